@@ -1,0 +1,298 @@
+/*
+ * Plain CPU oracle of the ReS2tAC dense SGM stereo path (Ruf et al., Sensors 2021).
+ *
+ * TEST INFRASTRUCTURE. This file is the checker of the CUDA library, not part of it: only the
+ * tests, the smoke check and the benchmark's CPU-baseline leg may load it. It shares no code,
+ * header, table or helper with the CUDA path. It is deliberately slow and literal: one pixel,
+ * one disparity, one direction at a time, int32 arithmetic, no SIMD, no threads, no blocking.
+ *
+ * What each function computes, with the passage it follows:
+ *   r2o_census          census transform, Sec. 2.1.1 and Sec. 2.2.1 (zero-valued margin), the
+ *                       centre pixel left out (Sec. 2.3.1).
+ *   r2o_cost            Hamming matching cost, Eq. (image_matching) in Sec. 2.1.1; cost 0xFF
+ *                       where the matching pixel lies left of the image (Sec. 2.3.2).
+ *   r2o_path            one SGM path, Eq. (sgm_path) in Sec. 2.1.2, in the normalised form
+ *                       L(p,d) = C(p,d) + min(L(q,d), L(q,d-1)+P1, L(q,d+1)+P1, m+P2) - m,
+ *                       q = p - r, m = min_k L(q,k); L = C where the path enters the image.
+ *   r2o_aggregate       S(p,d) = sum over paths of L_r(p,d), Eq. (sgm_path_aggr), saturated
+ *                       to 65535 (uint16 volume).
+ *   r2o_wta             D^L(p) = argmin_d S(p,d), Eq. (wta); the smallest d wins a tie.
+ *   r2o_right_disparity D^R(x,y) = argmin_d S((x+d,y),d), Eq. (right_disparity), over the d
+ *                       whose pixel x+d lies inside the image; the smallest d wins a tie.
+ *   r2o_lr_check        Eq. (LR_check), App. B: keep D^L(p) when x - D^L(p) >= 0 and
+ *                       |D^L(p) - D^R(x - D^L(p), y)| <= threshold, else the invalid value.
+ *   r2o_median3x3       3x3 median of the valid pixels, Sec. 2.1.3 / Sec. 2.2.4: pixels outside
+ *                       the image and invalid pixels count as 0xFFFF; the output is element [4]
+ *                       of the 9 sorted values (what five bubble-sort passes leave, App. D).
+ *   r2o_sgm             the whole chain above, in the order of Sec. 2.1.
+ *
+ * Conventions where the paper is silent (each is a reading, listed in the design doc):
+ *   - census bit = [neighbour < centre], row-major over the window (rows outer), LSB first;
+ *   - disparities d = 0 .. D-1;
+ *   - all volumes are [y][x][d] with the disparities of one pixel contiguous (Sec. 2.2.1).
+ *
+ * Return value of every function: 0 on success, -1 on an invalid argument.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define R2O_INVALID 0xFFFF
+#define R2O_COST_OUTSIDE 255
+
+/* Path directions r = (dx, dy), in the order LR, RL, TB, BT, TLBR, TRBL, BLTR, BRTL
+ * (Fig. neon_impl_paths, Sec. 2.3.3). Four-path SGM uses the first four (Sec. 3.2). */
+static const int R2O_DIRS[8][2] = {
+    {+1, 0}, {-1, 0}, {0, +1}, {0, -1}, {+1, +1}, {-1, +1}, {+1, -1}, {-1, -1}};
+
+static int popcount64(uint64_t v) {
+  int n = 0;
+  while (v) {
+    v &= v - 1;
+    n++;
+  }
+  return n;
+}
+
+/* Census transform. Bit k of the descriptor of pixel (x,y) is 1 when the k-th neighbour of the
+ * w x h window (visited row by row, left to right, centre skipped) is darker than the centre.
+ * Neighbours outside the image read 0 (zero-valued margin of Sec. 2.2.1). */
+int r2o_census(const uint8_t* img, int64_t pitch, int W, int H, int cw, int ch, uint64_t* out) {
+  if (!img || !out || W < 1 || H < 1 || cw < 1 || ch < 1) return -1;
+  if ((cw % 2) == 0 || (ch % 2) == 0 || cw * ch - 1 > 64 || pitch < W) return -1;
+  int rx = cw / 2, ry = ch / 2;
+  for (int y = 0; y < H; y++) {
+    for (int x = 0; x < W; x++) {
+      int centre = img[(int64_t)y * pitch + x];
+      uint64_t bits = 0;
+      int k = 0;
+      for (int j = -ry; j <= ry; j++) {
+        for (int i = -rx; i <= rx; i++) {
+          if (i == 0 && j == 0) continue;
+          int xx = x + i, yy = y + j;
+          int v = 0;
+          if (xx >= 0 && xx < W && yy >= 0 && yy < H) v = img[(int64_t)yy * pitch + xx];
+          if (v < centre) bits |= (uint64_t)1 << k;
+          k++;
+        }
+      }
+      out[(int64_t)y * W + x] = bits;
+    }
+  }
+  return 0;
+}
+
+/* Matching cost S(p,d) = Hamming distance between CT_L(x,y) and CT_R(x-d,y) (Eq. image_matching);
+ * 255 when x - d < 0. */
+int r2o_cost(const uint64_t* ctl, const uint64_t* ctr, int W, int H, int D, uint8_t* cost) {
+  if (!ctl || !ctr || !cost || W < 1 || H < 1 || D < 1 || D > 256) return -1;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++)
+      for (int d = 0; d < D; d++) {
+        int64_t i = ((int64_t)y * W + x) * D + d;
+        if (x - d < 0)
+          cost[i] = R2O_COST_OUTSIDE;
+        else
+          cost[i] = (uint8_t)popcount64(ctl[(int64_t)y * W + x] ^ ctr[(int64_t)y * W + (x - d)]);
+      }
+  return 0;
+}
+
+/* One SGM path L_r over the whole image for the direction r = (dx, dy) (Eq. sgm_path).
+ * Pixels are visited so that p - r is always visited before p; a pixel whose predecessor
+ * p - r lies outside the image starts its line: L(p,.) = C(p,.). L values never exceed
+ * 255 + P2, so uint16 holds them exactly. */
+int r2o_path(const uint8_t* cost, int W, int H, int D, int dx, int dy, int P1, int P2,
+             uint16_t* L) {
+  if (!cost || !L || W < 1 || H < 1 || D < 1 || D > 256) return -1;
+  if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || (dx == 0 && dy == 0)) return -1;
+  if (P1 < 0 || P2 < P1 || P2 > 16384) return -1;
+  for (int yi = 0; yi < H; yi++) {
+    int y = (dy >= 0) ? yi : H - 1 - yi;
+    for (int xi = 0; xi < W; xi++) {
+      int x = (dx >= 0) ? xi : W - 1 - xi;
+      int64_t p = ((int64_t)y * W + x) * D;
+      int qx = x - dx, qy = y - dy;
+      if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
+        for (int d = 0; d < D; d++) L[p + d] = cost[p + d];
+        continue;
+      }
+      int64_t q = ((int64_t)qy * W + qx) * D;
+      int m = L[q];
+      for (int k = 1; k < D; k++)
+        if (L[q + k] < m) m = L[q + k];
+      for (int d = 0; d < D; d++) {
+        int best = L[q + d];
+        if (d > 0 && L[q + d - 1] + P1 < best) best = L[q + d - 1] + P1;
+        if (d < D - 1 && L[q + d + 1] + P1 < best) best = L[q + d + 1] + P1;
+        if (m + P2 < best) best = m + P2;
+        L[p + d] = (uint16_t)(cost[p + d] + best - m);
+      }
+    }
+  }
+  return 0;
+}
+
+/* Aggregated volume S(p,d) = min(65535, sum_r L_r(p,d)) over the first R directions (R = 4 or 8). */
+int r2o_aggregate(const uint8_t* cost, int W, int H, int D, int R, int P1, int P2, uint16_t* S) {
+  if (!cost || !S || (R != 4 && R != 8) || W < 1 || H < 1 || D < 1 || D > 256) return -1;
+  int64_t n = (int64_t)W * H * D;
+  uint32_t* sum = (uint32_t*)calloc((size_t)n, sizeof(uint32_t));
+  uint16_t* L = (uint16_t*)malloc((size_t)n * sizeof(uint16_t));
+  if (!sum || !L) {
+    free(sum);
+    free(L);
+    return -1;
+  }
+  int rc = 0;
+  for (int r = 0; r < R && rc == 0; r++) {
+    rc = r2o_path(cost, W, H, D, R2O_DIRS[r][0], R2O_DIRS[r][1], P1, P2, L);
+    for (int64_t i = 0; i < n && rc == 0; i++) sum[i] += L[i];
+  }
+  for (int64_t i = 0; i < n && rc == 0; i++) S[i] = (uint16_t)(sum[i] > 65535 ? 65535 : sum[i]);
+  free(sum);
+  free(L);
+  return rc;
+}
+
+/* Winner-takes-all, Eq. (wta): the smallest d with the least S(p,d). */
+int r2o_wta(const uint16_t* S, int W, int H, int D, uint16_t* DL) {
+  if (!S || !DL || W < 1 || H < 1 || D < 1) return -1;
+  for (int64_t p = 0; p < (int64_t)W * H; p++) {
+    int best = S[p * D], bd = 0;
+    for (int d = 1; d < D; d++)
+      if (S[p * D + d] < best) {
+        best = S[p * D + d];
+        bd = d;
+      }
+    DL[p] = (uint16_t)bd;
+  }
+  return 0;
+}
+
+/* Approximate right disparity, Eq. (right_disparity): D^R(x,y) is the smallest d in
+ * [0, min(D-1, W-1-x)] with the least S((x+d,y),d). */
+int r2o_right_disparity(const uint16_t* S, int W, int H, int D, uint16_t* DR) {
+  if (!S || !DR || W < 1 || H < 1 || D < 1) return -1;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      int best = -1, bd = 0;
+      for (int d = 0; d < D && x + d < W; d++) {
+        int v = S[((int64_t)y * W + x + d) * D + d];
+        if (best < 0 || v < best) {
+          best = v;
+          bd = d;
+        }
+      }
+      DR[(int64_t)y * W + x] = (uint16_t)bd;
+    }
+  return 0;
+}
+
+/* Left-right consistency check, Eq. (LR_check). mask = 1 where the disparity is kept. */
+int r2o_lr_check(const uint16_t* DL, const uint16_t* DR, int W, int H, int threshold,
+                 uint16_t* Dout, uint8_t* mask) {
+  if (!DL || !DR || !Dout || W < 1 || H < 1 || threshold < 0) return -1;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      int64_t p = (int64_t)y * W + x;
+      int dl = DL[p];
+      int keep = 0;
+      if (x - dl >= 0) {
+        int dr = DR[(int64_t)y * W + (x - dl)];
+        int diff = dl - dr;
+        if (diff < 0) diff = -diff;
+        keep = diff <= threshold;
+      }
+      Dout[p] = keep ? (uint16_t)dl : (uint16_t)R2O_INVALID;
+      if (mask) mask[p] = (uint8_t)keep;
+    }
+  return 0;
+}
+
+/* 3x3 median: for each valid pixel, element [4] of its sorted 3x3 neighbourhood, where pixels
+ * outside the image and invalid pixels read 0xFFFF; invalid pixels stay invalid. */
+int r2o_median3x3(const uint16_t* Din, int W, int H, uint16_t* Dout) {
+  if (!Din || !Dout || W < 1 || H < 1 || Din == Dout) return -1;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      int64_t p = (int64_t)y * W + x;
+      if (Din[p] == R2O_INVALID) {
+        Dout[p] = R2O_INVALID;
+        continue;
+      }
+      int v[9], n = 0;
+      for (int j = -1; j <= 1; j++)
+        for (int i = -1; i <= 1; i++) {
+          int xx = x + i, yy = y + j;
+          v[n++] = (xx >= 0 && xx < W && yy >= 0 && yy < H) ? Din[(int64_t)yy * W + xx]
+                                                            : R2O_INVALID;
+        }
+      for (int a = 1; a < 9; a++) { /* insertion sort */
+        int t = v[a], b = a - 1;
+        while (b >= 0 && v[b] > t) {
+          v[b + 1] = v[b];
+          b--;
+        }
+        v[b + 1] = t;
+      }
+      Dout[p] = (uint16_t)v[4];
+    }
+  return 0;
+}
+
+/* Whole pipeline (Sec. 2.1). flags: bit 0 = left-right check, bit 1 = median.
+ * The optional outputs (may be NULL): cost [H][W][D] uint8, S [H][W][D] uint16, D^L, D^R,
+ * the left-right mask. disp receives the final map. */
+int r2o_sgm(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int H, int D,
+            int cw, int ch, int P1, int P2, int R, int flags, int lr_threshold, uint16_t* disp,
+            uint8_t* cost_out, uint16_t* S_out, uint16_t* DL_out, uint16_t* DR_out,
+            uint8_t* mask_out) {
+  if (!left || !right || !disp || W < 1 || H < 1 || D < 1 || D > 256) return -1;
+  int64_t npx = (int64_t)W * H, nde = npx * D;
+  uint64_t* ctl = (uint64_t*)malloc((size_t)npx * 8);
+  uint64_t* ctr = (uint64_t*)malloc((size_t)npx * 8);
+  uint8_t* cost = (uint8_t*)malloc((size_t)nde);
+  uint16_t* S = (uint16_t*)malloc((size_t)nde * 2);
+  uint16_t* DL = (uint16_t*)malloc((size_t)npx * 2);
+  uint16_t* DR = (uint16_t*)malloc((size_t)npx * 2);
+  uint16_t* Dlr = (uint16_t*)malloc((size_t)npx * 2);
+  uint8_t* mask = (uint8_t*)malloc((size_t)npx);
+  int rc = -1;
+  if (ctl && ctr && cost && S && DL && DR && Dlr && mask) {
+    rc = r2o_census(left, pitch, W, H, cw, ch, ctl);
+    if (!rc) rc = r2o_census(right, pitch, W, H, cw, ch, ctr);
+    if (!rc) rc = r2o_cost(ctl, ctr, W, H, D, cost);
+    if (!rc) rc = r2o_aggregate(cost, W, H, D, R, P1, P2, S);
+    if (!rc) rc = r2o_wta(S, W, H, D, DL);
+    if (!rc) rc = r2o_right_disparity(S, W, H, D, DR);
+    if (!rc) {
+      if (flags & 1) {
+        rc = r2o_lr_check(DL, DR, W, H, lr_threshold, Dlr, mask);
+      } else {
+        memcpy(Dlr, DL, (size_t)npx * 2);
+        memset(mask, 1, (size_t)npx);
+      }
+    }
+    if (!rc) {
+      if (flags & 2)
+        rc = r2o_median3x3(Dlr, W, H, disp);
+      else
+        memcpy(disp, Dlr, (size_t)npx * 2);
+    }
+    if (!rc && cost_out) memcpy(cost_out, cost, (size_t)nde);
+    if (!rc && S_out) memcpy(S_out, S, (size_t)nde * 2);
+    if (!rc && DL_out) memcpy(DL_out, DL, (size_t)npx * 2);
+    if (!rc && DR_out) memcpy(DR_out, DR, (size_t)npx * 2);
+    if (!rc && mask_out) memcpy(mask_out, mask, (size_t)npx);
+  }
+  free(ctl);
+  free(ctr);
+  free(cost);
+  free(S);
+  free(DL);
+  free(DR);
+  free(Dlr);
+  free(mask);
+  return rc;
+}

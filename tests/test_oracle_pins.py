@@ -1,0 +1,328 @@
+"""Pins of the CPU oracle to what the paper and the mathematics fix, independent of the oracle.
+
+Each test derives its expected values from something other than the oracle's own code: closed
+forms, brute-force enumeration over tiny inputs, the paper's worked examples (tests/golden/),
+invariants and independent numpy restatements. A dropped term, a flipped sign or direction, a
+transposed index or a wrong tie-break in the oracle fails at least one of them.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split(":", 1)
+            out[k.strip()] = v.split()
+    return out
+
+
+# ----------------------------------------------------------------------------- census (Sec. 2.1.1)
+@pytest.mark.parametrize("cw,ch", [(5, 5), (9, 7), (3, 3)])
+def test_census_raster_gradient_closed_form(cw, ch):
+    # Intensities rise strictly in raster order, so exactly the neighbours that precede the
+    # centre in row-major order are darker: the low B/2 bits are set, the high B/2 are clear.
+    img = (1 + np.arange(cw * ch)).reshape(ch, cw).astype(np.uint8)
+    ct = oracle.census(img, cw, ch)
+    B = cw * ch - 1
+    assert int(ct[ch // 2, cw // 2]) == (1 << (B // 2)) - 1
+    # reversed gradient: the complement within B bits
+    ct2 = oracle.census(img[::-1, ::-1].copy(), cw, ch)
+    assert int(ct2[ch // 2, cw // 2]) == ((1 << B) - 1) ^ ((1 << (B // 2)) - 1)
+
+
+@pytest.mark.parametrize("cw,ch", [(5, 5), (9, 7)])
+def test_census_zero_margin_at_corner(cw, ch):
+    # Constant image c > 0: inside neighbours are equal (bit 0); outside neighbours read 0 < c
+    # (bit 1). At the top-left corner (rx+1)(ry+1) window cells lie inside the image.
+    img = np.full((ch + 2, cw + 2), 77, np.uint8)
+    ct = oracle.census(img, cw, ch)
+    rx, ry = cw // 2, ch // 2
+    assert bin(int(ct[0, 0])).count("1") == cw * ch - (rx + 1) * (ry + 1)
+    # the bit of the neighbour at offset (-1, -1) (outside) is set, the one at (+1, +1) is not
+    k_out = (ry - 1) * cw + (rx - 1)
+    k_in = (ry + 1) * cw + (rx + 1) - 1  # minus one: the centre is skipped
+    assert (int(ct[0, 0]) >> k_out) & 1 == 1
+    assert (int(ct[0, 0]) >> k_in) & 1 == 0
+    assert int(oracle.census(np.zeros((9, 9), np.uint8), cw, ch).max()) == 0
+
+
+def test_census_invariant_under_monotone_map():
+    # The census is non-parametric (Zabih & Woodfill): a strictly increasing f with f(0) = 0
+    # leaves every descriptor unchanged, border pixels included (the margin stays 0).
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 81, (23, 31)).astype(np.uint8)
+    f = lambda v: 2 * v + (v * v) // 128  # strictly increasing on 0..80, f(0) = 0, max 210
+    img2 = f(img.astype(np.int64)).astype(np.uint8)
+    for cw, ch in ((5, 5), (9, 7)):
+        assert np.array_equal(oracle.census(img, cw, ch), oracle.census(img2, cw, ch))
+    # ... but not under a map with f(0) != 0 at the border
+    img3 = (img.astype(np.int64) + 10).astype(np.uint8)
+    assert not np.array_equal(oracle.census(img, 5, 5), oracle.census(img3, 5, 5))
+    # interior descriptors survive any strictly increasing map
+    assert np.array_equal(oracle.census(img, 5, 5)[2:-2, 2:-2],
+                          oracle.census(img3, 5, 5)[2:-2, 2:-2])
+
+
+@pytest.mark.parametrize("cw,ch", [(5, 5), (9, 7)])
+def test_census_bits_within_window(cw, ch):
+    rng = np.random.default_rng(4)
+    img = rng.integers(0, 256, (17, 19)).astype(np.uint8)
+    ct = oracle.census(img, cw, ch)
+    B = cw * ch - 1
+    if B < 64:
+        assert int(ct.max()) < (1 << B)
+    # the centre pixel is the strict maximum of a 1-hot image: every in-image bit is 0 except
+    # none; with the single bright pixel, all its (in-image) neighbours are darker
+    one = np.zeros((ch, cw), np.uint8)
+    one[ch // 2, cw // 2] = 9
+    assert int(oracle.census(one, cw, ch)[ch // 2, cw // 2]) == (1 << B) - 1
+
+
+# ------------------------------------------------------------------------- cost (Eq. image_matching)
+def test_cost_zero_at_true_shift_and_outside_value():
+    rng = np.random.default_rng(5)
+    W, H, D, s = 40, 12, 16, 6
+    L = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    R = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    R[:, :W - s] = L[:, s:]  # R(x) = L(x + s)  =>  L(x) = R(x - s)
+    for cw, ch in ((5, 5), (9, 7)):
+        rx, ry = cw // 2, ch // 2
+        C = oracle.cost(oracle.census(L, cw, ch), oracle.census(R, cw, ch), D)
+        inner = C[ry:H - ry, s + rx:W - rx, s]
+        assert inner.size > 0 and int(inner.max()) == 0
+        # Hamming distance of the descriptors, independently with numpy bit counting
+        ctl, ctr = oracle.census(L, cw, ch), oracle.census(R, cw, ch)
+        y, x, d = 3, 20, 9
+        assert C[y, x, d] == bin(int(ctl[y, x]) ^ int(ctr[y, x - d])).count("1")
+        # matching pixel left of the image: 0xFF
+        for x in range(D):
+            assert np.all(C[:, x, x + 1:] == 255)
+            assert np.all(C[:, x, :x + 1] <= cw * ch - 1)
+
+
+# ------------------------------------------------------------------------ SGM paths (Eq. sgm_path)
+def _V(a, b, P1, P2):
+    return 0 if a == b else (P1 if abs(a - b) == 1 else P2)
+
+
+def _chain_energy_min(costs, d_end, P1, P2):
+    """min over labelings l_0..l_k with l_k = d_end of sum C(p_i,l_i) + sum V(l_i, l_{i+1}):
+    the energy the 1-D dynamic programme minimises exactly, by exhaustive enumeration."""
+    k = len(costs)
+    D = len(costs[0])
+    best = None
+    for labels in itertools.product(range(D), repeat=k - 1):
+        lab = list(labels) + [d_end]
+        e = sum(int(costs[i][lab[i]]) for i in range(k))
+        e += sum(_V(lab[i], lab[i + 1], P1, P2) for i in range(k - 1))
+        best = e if best is None else min(best, e)
+    return best
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_path_equals_bruteforce_chain_energy(seed):
+    # Literal Eq. (sgm_path): L_eq(p,d) = C(p,d) + min_d' (L_eq(p-r,d') + V(d,d')) is the minimal
+    # chain energy of the path ending at p with label d. The normalised form subtracts
+    # m = min_k L_eq(p-r,k) at every step, so L(p,d) = L_eq(p,d) - min_k L_eq(p-r,k).
+    rng = np.random.default_rng(seed)
+    W, H, D = 5, 4, 3
+    cost_vol = rng.integers(0, 64, (H, W, D)).astype(np.uint8)
+    cost_vol[rng.random((H, W, D)) < 0.15] = 255
+    P1 = int(rng.integers(0, 20))
+    P2 = int(rng.integers(P1, 60))
+    for r in oracle.DIRECTIONS:
+        Lr = oracle.path(cost_vol, r, P1, P2)
+        for y in range(H):
+            for x in range(W):
+                chain = []
+                cx, cy = x, y
+                while 0 <= cx < W and 0 <= cy < H:
+                    chain.append(cost_vol[cy, cx])
+                    cx, cy = cx - r[0], cy - r[1]
+                chain = chain[::-1]  # from the line's entry pixel to p
+                eq_p = [_chain_energy_min(chain, d, P1, P2) for d in range(D)]
+                if len(chain) == 1:
+                    expect = eq_p
+                else:
+                    eq_q = [_chain_energy_min(chain[:-1], d, P1, P2) for d in range(D)]
+                    expect = [e - min(eq_q) for e in eq_p]
+                assert list(Lr[y, x]) == expect, (r, x, y)
+
+
+@pytest.mark.parametrize("R", [4, 8])
+def test_zero_penalties_reduce_to_cost_sum(R):
+    # P1 = P2 = 0: min(L(q,d), L(q,d+-1), m) - m = 0, so every L_r = C and S = R * C.
+    rng = np.random.default_rng(7)
+    cost_vol = rng.integers(0, 256, (9, 11, 8)).astype(np.uint8)
+    S = oracle.aggregate(cost_vol, R, 0, 0)
+    assert np.array_equal(S, np.minimum(R * cost_vol.astype(np.int64), 65535))
+
+
+def _steps_from_entry(W, H, r):
+    """Number of pixels on the path of direction r from its entry pixel to p, inclusive."""
+    n = np.zeros((H, W), np.int64)
+    for y in range(H):
+        for x in range(W):
+            k, cx, cy = 0, x, y
+            while 0 <= cx < W and 0 <= cy < H:
+                k += 1
+                cx, cy = cx - r[0], cy - r[1]
+            n[y, x] = k
+    return n
+
+
+@pytest.mark.parametrize("R,P2", [(4, 400), (8, 400), (8, 16384)])
+def test_aggregate_closed_form_and_saturation(R, P2):
+    # Cost 0 at d = 0 and 255 elsewhere, P1 = P2: along every path L(p,0) = 0 and, for d >= 1,
+    # L(p,d) = min(255 * n_r(p), 255 + P2) with n_r(p) the pixels walked from the entry.
+    # S = min(65535, sum_r L_r): with P2 = 16384 the centre saturates (8 * 16639 > 65535).
+    W, H, D = 80, 72, 4
+    cost_vol = np.full((H, W, D), 255, np.uint8)
+    cost_vol[:, :, 0] = 0
+    S = oracle.aggregate(cost_vol, R, P2, P2)
+    total = np.zeros((H, W), np.int64)
+    for r in oracle.DIRECTIONS[:R]:
+        total += np.minimum(255 * _steps_from_entry(W, H, r), 255 + P2)
+    expect = np.minimum(total, 65535)
+    assert np.all(S[:, :, 0] == 0)
+    for d in range(1, D):
+        assert np.array_equal(S[:, :, d].astype(np.int64), expect)
+    if P2 == 16384:
+        assert int(S[H // 2, W // 2, 1]) == 65535
+
+
+# ------------------------------------------------------------------------------- WTA (Eq. wta)
+def test_wta_map_reduce_worked_example():
+    g = _read_golden("map_reduce_min.txt")
+    costs = [int(v) for v in g["costs"]]
+    disps = [int(v) for v in g["disparities"]]
+    S = np.array(costs, np.uint16).reshape(1, 1, -1)
+    # the oracle's 0-based disparity of the minimum equals the figure's 1-based label 05
+    best = oracle.wta(S)[0, 0]
+    assert disps[best] == int(g["step3"][0].split("@")[1])
+    assert costs[best] == int(g["step3"][0].split("@")[0])
+    # the figure's halving pairing (i with i + n/2), restated here, reproduces every step
+    vals = list(zip(costs, disps))
+    for step in ("step1", "step2", "step3"):
+        n = len(vals) // 2
+        vals = [min(vals[i], vals[i + n]) for i in range(n)]
+        assert [f"{c}@{d}" for c, d in vals] == g[step]
+
+
+def test_wta_tie_takes_smallest_disparity():
+    S = np.array([[[9, 3, 7, 3, 3]]], np.uint16)
+    assert oracle.wta(S)[0, 0] == 1
+    rng = np.random.default_rng(8)
+    S = rng.integers(0, 6, (7, 9, 16)).astype(np.uint16)  # many ties
+    assert np.array_equal(oracle.wta(S), np.argmin(S, axis=2))
+
+
+# --------------------------------------------------------------- right disparity (Eq. right_disp.)
+def test_right_disparity_bruteforce():
+    rng = np.random.default_rng(9)
+    H, W, D = 6, 13, 8
+    S = rng.integers(0, 20, (H, W, D)).astype(np.uint16)
+    DR = oracle.right_disparity(S)
+    for y in range(H):
+        for x in range(W):
+            cand = [S[y, x + d, d] for d in range(min(D, W - x))]
+            assert DR[y, x] == int(np.argmin(cand))
+
+
+# ------------------------------------------------------------------------ LR check (Eq. LR_check)
+def test_lr_check_definition_cases():
+    DL = np.array([[0, 1, 3, 2, 2, 0]], np.uint16)
+    DR = np.array([[0, 1, 5, 0, 3, 1]], np.uint16)
+    D, mask = oracle.lr_check(DL, DR, 1)
+    # x=0: DR[0]=0 ok; x=1: DR[0]=0, |1-0|<=1 ok; x=2: 2-3<0 invalid;
+    # x=3: DR[1]=1, |2-1|=1 ok; x=4: DR[2]=5, |2-5|=3 invalid; x=5: DR[5]=1, |0-1|=1 ok
+    assert list(mask[0]) == [1, 1, 0, 1, 0, 1]
+    assert list(D[0]) == [0, 1, 0xFFFF, 2, 0xFFFF, 0]
+    D0, mask0 = oracle.lr_check(DL, DR, 0)
+    assert list(mask0[0]) == [1, 0, 0, 0, 0, 0]
+
+
+# ---------------------------------------------------------------------------- median (Sec. 2.1.3)
+def test_median_sorting_network_worked_example():
+    g = _read_golden("sorting_network_median.txt")
+    vals = [int(v) for v in g["input"]]
+    img = np.array(vals, np.uint16).reshape(3, 3)
+    out = oracle.median3x3(img)
+    assert out[1, 1] == int(g["median"][0])
+    assert sorted(vals) == [int(v) for v in g["sorted"]]
+    # a bubble-sort network of five passes, restated here: each pass carries the largest
+    # remaining value down to the lowest open wire (the smaller value stays on the upper wire),
+    # so after the fifth pass wires 8..4 hold the five largest values in order and wire 4 is
+    # the median
+    w = list(vals)
+    for p in range(5):
+        for i in range(0, 8 - p):
+            if w[i] > w[i + 1]:
+                w[i], w[i + 1] = w[i + 1], w[i]
+    assert w[4:] == [int(v) for v in g["sorted"]][4:]
+    assert w[4] == int(g["median"][0])
+
+
+def test_median_borders_and_invalid():
+    rng = np.random.default_rng(10)
+    Din = rng.integers(0, 50, (8, 9)).astype(np.uint16)
+    Din[rng.random(Din.shape) < 0.3] = 0xFFFF
+    out = oracle.median3x3(Din)
+    P = np.pad(Din.astype(np.int64), 1, constant_values=0xFFFF)
+    for y in range(8):
+        for x in range(9):
+            if Din[y, x] == 0xFFFF:
+                assert out[y, x] == 0xFFFF
+            else:
+                assert out[y, x] == np.sort(P[y:y + 3, x:x + 3].ravel())[4]
+
+
+# ----------------------------------------------------------------------------------- end to end
+@pytest.mark.parametrize("cw,ch,R", [(5, 5, 4), (9, 7, 8)])
+def test_constant_shift_recovered(cw, ch, R):
+    rng = np.random.default_rng(11)
+    W, H, D, s = 96, 40, 32, 7
+    from paper_2106_07927_gb300 import scenes
+    L = scenes._to_u8(scenes._blur(rng.random((H, W)), 1.0))
+    R_img = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    R_img[:, :W - s] = L[:, s:]
+    disp, dbg = oracle.sgm(L, R_img, D, cw, ch, 10, 120, R, oracle.FLAG_LR_CHECK, debug=True)
+    rx = cw // 2
+    inner = dbg["dl"][:, s + rx:W - D]
+    assert np.all(inner == s)
+    # the left-right check keeps the interior. Near the left border the approximate D^R of
+    # Eq. (right_disparity) is biased (paths entering there have summed fewer pixels), so the
+    # check is asserted from x = 3 s on.
+    assert np.all(disp[:, 3 * s:W - D] == s)
+
+
+def test_occluded_band_is_invalidated():
+    # Background at d = 4, a foreground box at d = 20: the background strip just left of the
+    # box is hidden in the right image (occlusion), so the LR check must drop most of it while
+    # keeping nearly all visible background pixels.
+    rng = np.random.default_rng(12)
+    W, H, D = 160, 48, 32
+    from paper_2106_07927_gb300 import scenes
+    L = scenes._to_u8(scenes._blur(rng.random((H, W)), 1.0))
+    disp = np.full((H, W), 4, np.int32)
+    x1, x2 = 90, 130
+    disp[:, x1:x2] = 20
+    R_img = scenes.forward_warp(rng, L, disp)
+    out, dbg = oracle.sgm(L, R_img, D, 9, 7, 10, 120, 8, oracle.FLAG_LR_CHECK, debug=True)
+    occl = dbg["mask"][8:H - 8, x1 - 14:x1 - 2]
+    vis = dbg["mask"][8:H - 8, 40:x1 - 20]
+    assert occl.mean() < 0.2
+    assert vis.mean() > 0.95
+    assert np.all(out[8:H - 8, 40:x1 - 20][vis.astype(bool)] == 4)
