@@ -1,0 +1,178 @@
+/*
+ * res2tac.h: C ABI of the GB300 SGM stereo library (census transform, Hamming matching cost,
+ * semi-global path aggregation, winner-takes-all, approximate left-right consistency check and
+ * 3x3 median) after Ruf et al., "ReS2tAC: UAV-borne real-time SGM stereo optimized for embedded
+ * ARM and CUDA devices", Sensors 2021.
+ *
+ * Every compute call runs all of its work in CUDA kernels for sm_103a on the caller's stream.
+ * No call falls back to the CPU. Types are plain C: image and output buffers are raw pointers
+ * (device memory unless a function says "host"), sizes are int32/int64, streams are passed as
+ * an opaque pointer that must be a cudaStream_t of the current device (NULL = legacy default).
+ *
+ * Data layout. Images are 8-bit grayscale, row-major with a pitch in bytes. The left image is
+ * the reference (Sec. 2.1.1). Disparity maps are uint16, row-major with a pitch in bytes, and
+ * hold d in [0, D-1] or RES2TAC_INVALID. Cost and aggregated volumes are [y][x][d] with the D
+ * disparities of one pixel contiguous (Sec. 2.2.1), d = 0 .. D-1.
+ *
+ * Errors. Functions return RES2TAC_OK (0) or a negative code; nothing is thrown across the
+ * ABI. res2tac_last_error() returns a message for the last failure on the calling thread.
+ * A context is not thread-safe: use one context per host thread / stream.
+ */
+#ifndef RES2TAC_H_
+#define RES2TAC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RES2TAC_OK 0
+#define RES2TAC_EINVAL (-1)   /* bad parameter, shape, pitch or NULL pointer */
+#define RES2TAC_ENOMEM (-2)   /* device memory for the scratch could not be allocated */
+#define RES2TAC_ECUDA (-3)    /* a CUDA runtime call or launch failed (message kept) */
+#define RES2TAC_ETIMEOUT (-4) /* a bounded device-side wait of the batch engine gave up */
+
+/* flags */
+#define RES2TAC_LR_CHECK 1 /* approximate left-right consistency check, Eq. (LR_check) */
+#define RES2TAC_MEDIAN 2   /* 3x3 median over the valid pixels, Sec. 2.1.3 */
+
+#define RES2TAC_INVALID 0xFFFF /* disparity of a pixel rejected by the left-right check */
+
+typedef struct res2tac_ctx* res2tac_t;
+typedef void* res2tac_stream_t; /* a cudaStream_t */
+
+/* Problem statement as the paper gives it.
+ *   width, height  image size W x H, 1 .. 16384 each.
+ *   max_disp       D, the number of disparities searched, d in [0, D-1] (the range Gamma of
+ *                  Sec. 2.1.1 with d_min = 0); 16 <= D <= 256, D % 16 == 0 (Sec. 3.1.2 caps D
+ *                  at 256).
+ *   census_w/_h    census window: 5 x 5 (24-bit descriptor) or 9 x 7 (62-bit), width first
+ *                  (Sec. 2.2.1).
+ *   p1, p2         SGM penalties of Eq. (sgm_path), 0 <= p1 <= p2 <= 16384.
+ *   num_paths      4 (LR, RL, TB, BT) or 8 (plus the four diagonals), Sec. 3.2.
+ *   flags          RES2TAC_LR_CHECK | RES2TAC_MEDIAN (0 = winner-takes-all only).
+ *   lr_threshold   largest accepted |D^L - D^R| of the left-right check (the paper uses 1). */
+typedef struct res2tac_params {
+  int32_t width, height;
+  int32_t max_disp;
+  int32_t census_w, census_h;
+  int32_t p1, p2;
+  int32_t num_paths;
+  int32_t flags;
+  int32_t lr_threshold;
+} res2tac_params;
+
+/* One stereo pair of a batch. Pointers are device memory owned by the caller. width, height
+ * and max_disp override the context's values for this pair (same limits as res2tac_params);
+ * the census window, penalties, path count, flags and threshold come from the context. */
+typedef struct res2tac_pair {
+  const uint8_t* left;
+  const uint8_t* right;
+  int64_t in_pitch; /* bytes, >= width */
+  uint16_t* disp;
+  int64_t out_pitch; /* bytes, >= 2 * width, even */
+  int32_t width, height, max_disp;
+  int32_t reserved; /* set to 0 */
+} res2tac_pair;
+
+/* Kernel configuration of a context. Every valid setting gives bit-identical results; only the
+ * speed differs. agg_dpl: disparities per lane of the aggregation kernel (0 = automatic, else
+ * 2, 4 or 8 with D / agg_dpl <= 32). agg_warps: warps per aggregation block (1..16).
+ * wta_chunk: pixels per chunk of the winner-takes-all / right-disparity kernel (32..256, a
+ * multiple of 32; 0 = automatic). */
+typedef struct res2tac_tuning {
+  int32_t agg_dpl;
+  int32_t agg_warps;
+  int32_t wta_chunk;
+  int32_t reserved;
+} res2tac_tuning;
+
+/* Validates *p, allocates the context's device scratch for a W x H x D pair on the current
+ * device, and returns the handle in *out. The scratch (census maps, cost volume, aggregated
+ * volume, intermediate maps, host staging) is owned by the context until res2tac_destroy.
+ * Returns RES2TAC_EINVAL for invalid parameters, RES2TAC_ENOMEM if the scratch does not fit. */
+int res2tac_create(const res2tac_params* p, res2tac_t* out);
+
+/* Runs the whole pipeline of Sec. 2.1 on one rectified pair, asynchronously on stream s:
+ * census (Sec. 2.2.1) -> Hamming cost, Eq. (image_matching) -> SGM aggregation over num_paths
+ * paths, Eqs. (sgm_path), (sgm_path_aggr) -> WTA, Eq. (wta) -> approximate D^R,
+ * Eq. (right_disparity) and left-right check, Eq. (LR_check) -> 3x3 median.
+ * left/right: device images of the context's W x H, in_pitch bytes per row. disp: device
+ * output, out_pitch bytes per row. The caller synchronises s before reading disp.
+ * Intermediates stay in the context until the next call (see res2tac_debug_outputs). */
+int res2tac_compute(res2tac_t h, const uint8_t* left, const uint8_t* right, int64_t in_pitch,
+                    uint16_t* disp, int64_t out_pitch, res2tac_stream_t s);
+
+/* Same pipeline on HOST buffers, end to end as the paper times it (upload, compute, download;
+ * Sec. 3.3): copies left/right (host, in_pitch bytes per row) into the context's device
+ * staging, runs res2tac_compute on s, copies the map back into disp (host, out_pitch bytes per
+ * row) and synchronises s before returning. Pinned host memory makes the copies faster. */
+int res2tac_compute_host(res2tac_t h, const uint8_t* left, const uint8_t* right,
+                         int64_t in_pitch, uint16_t* disp, int64_t out_pitch,
+                         res2tac_stream_t s);
+
+/* Runs n independent pairs of uneven sizes as one batch on stream s (the paper processes one
+ * pair at a time, Sec. 2.2; batching is this library's addition). The batch runs as persistent
+ * kernels fed by a device work queue over all pairs, recorded once into a CUDA graph and
+ * replayed while the batch layout (n and every pair's W, H, D) stays the same. The context
+ * grows its batch scratch when a larger batch arrives: that call allocates and must not be made
+ * during stream capture. pairs: host array of n descriptors with device pointers. Results are
+ * bit-identical to res2tac_compute on each pair alone. Returns RES2TAC_ETIMEOUT if a bounded
+ * device wait of the queue gave up (the outputs are then unspecified). */
+int res2tac_compute_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res2tac_stream_t s);
+
+/* Copies the intermediates of the last res2tac_compute on this context into caller buffers
+ * (device pointers; any may be NULL): cost [H][W][D] uint8 (Eq. image_matching, 255 where
+ * x - d < 0), agg [H][W][D] uint16 (S-bar of Eq. sgm_path_aggr, saturated at 65535),
+ * dl / dr [H][W] uint16 (Eqs. wta and right_disparity), mask [H][W] uint8 (1 where the
+ * left-right check kept the pixel, all 1 without RES2TAC_LR_CHECK). Asynchronous on s. */
+int res2tac_debug_outputs(res2tac_t h, uint8_t* cost, uint16_t* agg, uint16_t* dl, uint16_t* dr,
+                          uint8_t* mask, res2tac_stream_t s);
+
+/* Device bytes res2tac_create allocates for *p (0 if *p is invalid); for admission control. */
+size_t res2tac_workspace_bytes(const res2tac_params* p);
+
+/* Device bytes a batch of n pairs needs on top of the context (0 if a pair is invalid). */
+size_t res2tac_batch_workspace_bytes(const res2tac_params* p, const res2tac_pair* pairs,
+                                     int32_t n);
+
+/* Reads / sets the kernel configuration (RES2TAC_EINVAL for a setting the context's D cannot
+ * use). res2tac_autotune times every valid setting on the given device pair (left, right,
+ * in_pitch as for res2tac_compute, output into disp), keeps the fastest in the context and
+ * returns it in *best; it synchronises s. */
+int res2tac_get_tuning(res2tac_t h, res2tac_tuning* t);
+int res2tac_set_tuning(res2tac_t h, const res2tac_tuning* t);
+int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int64_t in_pitch,
+                     uint16_t* disp, int64_t out_pitch, res2tac_stream_t s,
+                     res2tac_tuning* best);
+
+/* Number of kernel launches the last res2tac_compute / res2tac_compute_batch issued. */
+int res2tac_last_launch_count(res2tac_t h);
+
+/* Per-stage timing. With profiling enabled, res2tac_compute records a CUDA event on the caller's
+ * stream before and after each stage. res2tac_stage_times waits for the last call and writes up
+ * to n durations in milliseconds: [0] census, [1] cost (+ clearing of the aggregated volume),
+ * [2] path aggregation, [3] WTA / right disparity / LR check, [4] median (0 when skipped). */
+int res2tac_set_profiling(res2tac_t h, int enable);
+int res2tac_stage_times(res2tac_t h, float* ms, int n);
+
+/* Integer-throughput probe (measurement aid, not part of the method): runs independent chains
+ * of packed u16x2 min and add instructions on every SM for about `iters` iterations on stream s
+ * and returns the sustained rate in 16-bit lane operations per second (one packed instruction
+ * counts two) through *lane_ops_per_s. Synchronises s. */
+int res2tac_probe_int_peak(int iters, res2tac_stream_t s, double* lane_ops_per_s);
+
+/* Frees the context and its scratch. NULL-safe. The caller makes sure no work on the context
+ * is still running. */
+void res2tac_destroy(res2tac_t h);
+
+const char* res2tac_strerror(int code);
+const char* res2tac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RES2TAC_H_ */

@@ -1,0 +1,417 @@
+// C ABI of the SGM stereo library: context management, validation, scratch layout, dispatch.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/res2tac.h"
+#include "batch.h"
+#include "launch.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int fail_cuda(cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky launch error of this thread
+  return fail(e == cudaErrorMemoryAllocation ? RES2TAC_ENOMEM : RES2TAC_ECUDA, "%s: %s (%s)", what,
+              cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool shape_ok(int W, int H, int D) {
+  return W >= 1 && W <= 16384 && H >= 1 && H <= 16384 && D >= 16 && D <= 256 && D % 16 == 0;
+}
+
+const char* params_error(const res2tac_params* p) {
+  if (!p) return "params is NULL";
+  if (!shape_ok(p->width, p->height, p->max_disp))
+    return "need 1 <= width, height <= 16384 and 16 <= max_disp <= 256, max_disp % 16 == 0";
+  if (!((p->census_w == 5 && p->census_h == 5) || (p->census_w == 9 && p->census_h == 7)))
+    return "census window must be 5x5 or 9x7";
+  if (p->p1 < 0 || p->p2 < p->p1 || p->p2 > 16384) return "need 0 <= p1 <= p2 <= 16384";
+  if (p->num_paths != 4 && p->num_paths != 8) return "num_paths must be 4 or 8";
+  if (p->flags & ~(RES2TAC_LR_CHECK | RES2TAC_MEDIAN)) return "unknown flag bits";
+  if (p->lr_threshold < 0 || p->lr_threshold > 255) return "lr_threshold must be in 0..255";
+  return nullptr;
+}
+
+bool needs_wide(const res2tac_params* p) { return p->num_paths * (255 + p->p2) > 65535; }
+
+// Byte offsets of the per-pair scratch buffers inside one allocation.
+struct Layout {
+  size_t ctl, ctr, cost, agg, dl, dr, dlr, mask, total;
+};
+
+Layout layout_for(int W, int H, int D, bool wide) {
+  const size_t npx = (size_t)W * H, nde = npx * D;
+  Layout l;
+  size_t o = 0;
+  l.ctl = o; o = align_up(o + npx * 8, 256);
+  l.ctr = o; o = align_up(o + npx * 8, 256);
+  l.cost = o; o = align_up(o + nde, 256);
+  l.agg = o; o = align_up(o + nde * (wide ? 4 : 2), 256);
+  l.dl = o; o = align_up(o + npx * 2, 256);
+  l.dr = o; o = align_up(o + npx * 2, 256);
+  l.dlr = o; o = align_up(o + npx * 2, 256);
+  l.mask = o; o = align_up(o + npx, 256);
+  l.total = o;
+  return l;
+}
+
+r2t::Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
+  r2t::Problem pb;
+  memset(&pb, 0, sizeof(pb));
+  pb.W = W;
+  pb.H = H;
+  pb.D = D;
+  pb.ctl = reinterpret_cast<uint64_t*>(base + l.ctl);
+  pb.ctr = reinterpret_cast<uint64_t*>(base + l.ctr);
+  pb.cost = reinterpret_cast<uint8_t*>(base + l.cost);
+  pb.agg = base + l.agg;
+  pb.dl = reinterpret_cast<uint16_t*>(base + l.dl);
+  pb.dr = reinterpret_cast<uint16_t*>(base + l.dr);
+  pb.dlr = reinterpret_cast<uint16_t*>(base + l.dlr);
+  pb.mask = reinterpret_cast<uint8_t*>(base + l.mask);
+  return pb;
+}
+
+r2t::Method method_of(const res2tac_params& p) {
+  r2t::Method m;
+  m.cw = p.census_w;
+  m.ch = p.census_h;
+  m.P1 = p.p1;
+  m.P2 = p.p2;
+  m.num_paths = p.num_paths;
+  m.flags = p.flags;
+  m.lr_threshold = p.lr_threshold;
+  m.wide = needs_wide(&p) ? 1 : 0;
+  return m;
+}
+
+}  // namespace
+
+struct res2tac_ctx {
+  res2tac_params p;
+  r2t::Method method;
+  r2t::Tuning tuning;
+  int device;
+  Layout lay;
+  char* scratch;       // per-pair scratch of the context's own shape
+  uint8_t* stage_in;   // device staging of res2tac_compute_host: left, right (pitch W)
+  uint16_t* stage_out; // device staging of the output map (pitch 2W bytes)
+  int last_launches;
+  r2t::BatchEngine* batch;
+  int profiling;
+  cudaEvent_t ev[6];  // stage boundaries of the last profiled compute
+};
+
+extern "C" {
+
+const char* res2tac_strerror(int code) {
+  switch (code) {
+    case RES2TAC_OK: return "ok";
+    case RES2TAC_EINVAL: return "invalid argument";
+    case RES2TAC_ENOMEM: return "out of device memory";
+    case RES2TAC_ECUDA: return "CUDA error";
+    case RES2TAC_ETIMEOUT: return "device-side wait timed out";
+    default: return "unknown error";
+  }
+}
+
+const char* res2tac_last_error(void) { return g_err; }
+
+size_t res2tac_workspace_bytes(const res2tac_params* p) {
+  if (params_error(p)) return 0;
+  const size_t npx = (size_t)p->width * p->height;
+  return layout_for(p->width, p->height, p->max_disp, needs_wide(p)).total + npx * 2 + npx * 2 +
+         1024;
+}
+
+int res2tac_create(const res2tac_params* p, res2tac_t* out) {
+  if (!out) return fail(RES2TAC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (const char* why = params_error(p)) return fail(RES2TAC_EINVAL, "res2tac_create: %s", why);
+  res2tac_ctx* h = new (std::nothrow) res2tac_ctx;
+  if (!h) return fail(RES2TAC_ENOMEM, "host allocation failed");
+  memset(h, 0, sizeof(*h));
+  h->p = *p;
+  h->method = method_of(*p);
+  h->tuning = r2t::default_tuning(p->max_disp);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail_cuda(e, "cudaGetDevice");
+  }
+  h->lay = layout_for(p->width, p->height, p->max_disp, h->method.wide != 0);
+  const size_t npx = (size_t)p->width * p->height;
+  e = cudaMalloc(&h->scratch, h->lay.total);
+  if (e == cudaSuccess) e = cudaMalloc(&h->stage_in, align_up(npx * 2, 256));
+  if (e == cudaSuccess) e = cudaMalloc(&h->stage_out, align_up(npx * 2, 256));
+  if (e != cudaSuccess) {
+    int rc = fail_cuda(e, "cudaMalloc of the context scratch");
+    res2tac_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return RES2TAC_OK;
+}
+
+void res2tac_destroy(res2tac_t h) {
+  if (!h) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (cur != h->device) cudaSetDevice(h->device);
+  r2t::batch_destroy(h->batch);
+  for (int i = 0; i < 6; i++)
+    if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+  cudaFree(h->scratch);
+  cudaFree(h->stage_in);
+  cudaFree(h->stage_out);
+  if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
+  delete h;
+}
+
+static int check_io(res2tac_t h, const void* left, const void* right, int64_t in_pitch,
+                    const void* disp, int64_t out_pitch) {
+  if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
+  if (!left || !right || !disp) return fail(RES2TAC_EINVAL, "NULL image or output pointer");
+  if (in_pitch < h->p.width) return fail(RES2TAC_EINVAL, "in_pitch < width");
+  if (out_pitch < 2 * (int64_t)h->p.width || (out_pitch & 1))
+    return fail(RES2TAC_EINVAL, "out_pitch must be even and >= 2 * width");
+  if ((reinterpret_cast<uintptr_t>(disp) & 1) != 0)
+    return fail(RES2TAC_EINVAL, "disp must be 2-byte aligned");
+  return RES2TAC_OK;
+}
+
+int res2tac_compute(res2tac_t h, const uint8_t* left, const uint8_t* right, int64_t in_pitch,
+                    uint16_t* disp, int64_t out_pitch, res2tac_stream_t s) {
+  int rc = check_io(h, left, right, in_pitch, disp, out_pitch);
+  if (rc) return rc;
+  r2t::Problem pb = problem_at(h->scratch, h->lay, h->p.width, h->p.height, h->p.max_disp);
+  pb.left = left;
+  pb.right = right;
+  pb.in_pitch = in_pitch;
+  pb.disp = disp;
+  pb.out_pitch = out_pitch;
+  int n = 0;
+  cudaError_t e = r2t::run_pipeline(pb, h->method, h->tuning, (cudaStream_t)s, &n,
+                                    h->profiling ? h->ev : nullptr);
+  h->last_launches = n;
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_compute launch");
+  return RES2TAC_OK;
+}
+
+int res2tac_compute_host(res2tac_t h, const uint8_t* left, const uint8_t* right,
+                         int64_t in_pitch, uint16_t* disp, int64_t out_pitch,
+                         res2tac_stream_t s) {
+  int rc = check_io(h, left, right, in_pitch, disp, out_pitch);
+  if (rc) return rc;
+  const int W = h->p.width, H = h->p.height;
+  cudaStream_t st = (cudaStream_t)s;
+  uint8_t* dl = h->stage_in;
+  uint8_t* dr = h->stage_in + (size_t)W * H;
+  cudaError_t e = cudaMemcpy2DAsync(dl, W, left, in_pitch, W, H, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(dr, W, right, in_pitch, W, H, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_compute_host upload");
+  rc = res2tac_compute(h, dl, dr, W, h->stage_out, 2 * (int64_t)W, s);
+  if (rc) return rc;
+  e = cudaMemcpy2DAsync(disp, out_pitch, h->stage_out, 2 * (size_t)W, 2 * (size_t)W, H,
+                        cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_compute_host download");
+  return RES2TAC_OK;
+}
+
+int res2tac_debug_outputs(res2tac_t h, uint8_t* cost, uint16_t* agg, uint16_t* dl, uint16_t* dr,
+                          uint8_t* mask, res2tac_stream_t s) {
+  if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
+  r2t::Problem pb = problem_at(h->scratch, h->lay, h->p.width, h->p.height, h->p.max_disp);
+  cudaStream_t st = (cudaStream_t)s;
+  const size_t npx = (size_t)pb.W * pb.H, nde = npx * pb.D;
+  cudaError_t e = cudaSuccess;
+  if (cost && e == cudaSuccess) e = cudaMemcpyAsync(cost, pb.cost, nde, cudaMemcpyDeviceToDevice, st);
+  if (agg && e == cudaSuccess) e = r2t::copy_agg_u16(pb, h->method.wide != 0, agg, st);
+  if (dl && e == cudaSuccess) e = cudaMemcpyAsync(dl, pb.dl, npx * 2, cudaMemcpyDeviceToDevice, st);
+  if (dr && e == cudaSuccess) e = cudaMemcpyAsync(dr, pb.dr, npx * 2, cudaMemcpyDeviceToDevice, st);
+  if (mask && e == cudaSuccess) e = cudaMemcpyAsync(mask, pb.mask, npx, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_debug_outputs");
+  return RES2TAC_OK;
+}
+
+int res2tac_get_tuning(res2tac_t h, res2tac_tuning* t) {
+  if (!h || !t) return fail(RES2TAC_EINVAL, "NULL argument");
+  t->agg_dpl = h->tuning.agg_dpl;
+  t->agg_warps = h->tuning.agg_warps;
+  t->wta_chunk = h->tuning.wta_chunk;
+  t->reserved = 0;
+  return RES2TAC_OK;
+}
+
+int res2tac_set_tuning(res2tac_t h, const res2tac_tuning* t) {
+  if (!h || !t) return fail(RES2TAC_EINVAL, "NULL argument");
+  r2t::Tuning n = r2t::default_tuning(h->p.max_disp);
+  if (t->agg_dpl) n.agg_dpl = t->agg_dpl;
+  if (t->agg_warps) n.agg_warps = t->agg_warps;
+  if (t->wta_chunk) n.wta_chunk = t->wta_chunk;
+  if (!r2t::tuning_valid(n, h->p.max_disp))
+    return fail(RES2TAC_EINVAL, "tuning (dpl %d, warps %d, chunk %d) invalid for D = %d",
+                n.agg_dpl, n.agg_warps, n.wta_chunk, h->p.max_disp);
+  h->tuning = n;
+  return RES2TAC_OK;
+}
+
+int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int64_t in_pitch,
+                     uint16_t* disp, int64_t out_pitch, res2tac_stream_t s,
+                     res2tac_tuning* best) {
+  int rc = check_io(h, left, right, in_pitch, disp, out_pitch);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)s;
+  std::vector<r2t::Tuning> cands;
+  const int dpls[3] = {2, 4, 8}, warps[3] = {2, 4, 8}, chunks[3] = {64, 128, 256};
+  for (int a : dpls)
+    for (int w : warps)
+      for (int c : chunks) {
+        r2t::Tuning t{a, w, c};
+        if (r2t::tuning_valid(t, h->p.max_disp)) cands.push_back(t);
+      }
+  if (cands.empty()) return fail(RES2TAC_EINVAL, "no valid tuning");
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(RES2TAC_ECUDA, "cudaEventCreate failed");
+  const r2t::Tuning keep = h->tuning;
+  float best_ms = 1e30f;
+  r2t::Tuning best_t = keep;
+  for (const r2t::Tuning& t : cands) {
+    h->tuning = t;
+    for (int rep = 0; rep < 2; rep++) {  // warm-up
+      rc = res2tac_compute(h, left, right, in_pitch, disp, out_pitch, s);
+      if (rc) break;
+    }
+    if (rc) break;
+    cudaEventRecord(e0, st);
+    const int reps = 5;
+    for (int rep = 0; rep < reps && !rc; rep++)
+      rc = res2tac_compute(h, left, right, in_pitch, disp, out_pitch, s);
+    cudaEventRecord(e1, st);
+    if (rc) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = fail(RES2TAC_ECUDA, "autotune synchronisation failed");
+      break;
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_t = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tuning = rc ? keep : best_t;
+  if (rc) return rc;
+  if (best) res2tac_get_tuning(h, best);
+  return RES2TAC_OK;
+}
+
+int res2tac_last_launch_count(res2tac_t h) { return h ? h->last_launches : 0; }
+
+int res2tac_set_profiling(res2tac_t h, int enable) {
+  if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
+  if (enable && !h->ev[0]) {
+    for (int i = 0; i < 6; i++) {
+      cudaError_t e = cudaEventCreate(&h->ev[i]);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaEventCreate");
+    }
+  }
+  h->profiling = enable ? 1 : 0;
+  return RES2TAC_OK;
+}
+
+int res2tac_stage_times(res2tac_t h, float* ms, int n) {
+  if (!h || !ms || n < 0) return fail(RES2TAC_EINVAL, "NULL argument");
+  if (!h->profiling || !h->ev[0]) return fail(RES2TAC_EINVAL, "profiling is not enabled");
+  cudaError_t e = cudaEventSynchronize(h->ev[5]);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaEventSynchronize");
+  for (int i = 0; i < n && i < 5; i++) {
+    float t = 0;
+    e = cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaEventElapsedTime");
+    ms[i] = t;
+  }
+  return RES2TAC_OK;
+}
+
+int res2tac_probe_int_peak(int iters, res2tac_stream_t s, double* lane_ops_per_s) {
+  if (iters < 1 || !lane_ops_per_s) return fail(RES2TAC_EINVAL, "bad probe arguments");
+  cudaError_t e = r2t::probe_int_peak(iters, (cudaStream_t)s, lane_ops_per_s);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_probe_int_peak");
+  return RES2TAC_OK;
+}
+
+size_t res2tac_batch_workspace_bytes(const res2tac_params* p, const res2tac_pair* pairs,
+                                     int32_t n) {
+  if (params_error(p) || !pairs || n < 1) return 0;
+  const bool wide = needs_wide(p);
+  size_t total = 0;
+  for (int i = 0; i < n; i++) {
+    if (!shape_ok(pairs[i].width, pairs[i].height, pairs[i].max_disp)) return 0;
+    total += layout_for(pairs[i].width, pairs[i].height, pairs[i].max_disp, wide).total;
+  }
+  return total + r2t::batch_fixed_bytes(n);
+}
+
+int res2tac_compute_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res2tac_stream_t s) {
+  if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
+  if (!pairs || n < 1) return fail(RES2TAC_EINVAL, "empty batch");
+  std::vector<r2t::Problem> probs((size_t)n);
+  std::vector<size_t> offs((size_t)n);
+  size_t total = 0;
+  const bool wide = h->method.wide != 0;
+  for (int i = 0; i < n; i++) {
+    const res2tac_pair& q = pairs[i];
+    if (!shape_ok(q.width, q.height, q.max_disp))
+      return fail(RES2TAC_EINVAL, "pair %d: invalid shape %dx%d D=%d", i, q.width, q.height,
+                  q.max_disp);
+    if (!q.left || !q.right || !q.disp) return fail(RES2TAC_EINVAL, "pair %d: NULL pointer", i);
+    if (q.in_pitch < q.width || q.out_pitch < 2 * (int64_t)q.width || (q.out_pitch & 1))
+      return fail(RES2TAC_EINVAL, "pair %d: bad pitch", i);
+    offs[i] = total;
+    total += layout_for(q.width, q.height, q.max_disp, wide).total;
+  }
+  int rc = r2t::batch_reserve(&h->batch, total, n);
+  if (rc == -2) return fail(RES2TAC_ENOMEM, "batch scratch of %zu bytes could not be allocated", total);
+  if (rc) return fail(RES2TAC_ECUDA, "batch engine setup failed: %s", r2t::batch_error(h->batch));
+  char* base = r2t::batch_scratch(h->batch);
+  for (int i = 0; i < n; i++) {
+    const res2tac_pair& q = pairs[i];
+    Layout l = layout_for(q.width, q.height, q.max_disp, wide);
+    r2t::Problem pb = problem_at(base + offs[i], l, q.width, q.height, q.max_disp);
+    pb.left = q.left;
+    pb.right = q.right;
+    pb.in_pitch = q.in_pitch;
+    pb.disp = q.disp;
+    pb.out_pitch = q.out_pitch;
+    probs[i] = pb;
+  }
+  int launches = 0;
+  rc = r2t::batch_run(h->batch, probs.data(), n, h->method, (cudaStream_t)s, &launches);
+  h->last_launches = launches;
+  if (rc == -4) return fail(RES2TAC_ETIMEOUT, "batch work queue wait timed out");
+  if (rc) return fail(RES2TAC_ECUDA, "batch run failed: %s", r2t::batch_error(h->batch));
+  return RES2TAC_OK;
+}
+
+}  // extern "C"

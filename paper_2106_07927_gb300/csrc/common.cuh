@@ -1,0 +1,57 @@
+// Shared device helpers and the per-pair problem descriptor of the GB300 SGM kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace r2t {
+
+constexpr uint16_t kInvalid = 0xFFFF;  // rejected disparity (Eq. LR_check "inv")
+constexpr uint8_t kCostOutside = 255;  // cost where the matching pixel x - d lies left of the image
+// Path-cost sentinel for disparities outside [0, D-1]. Any value v with v >= m + P2 - P1 for every
+// reachable minimum m never wins the min of Eq. (sgm_path); 0xBFFF does so because m <= 255 + P2
+// <= 16639 and P1, P2 <= 16384, and v + P1 still fits 16 bits.
+constexpr uint32_t kSent = 0xBFFFu;
+
+// Everything a kernel needs to know about one stereo pair. Volumes are [y][x][d], d contiguous.
+struct Problem {
+  const uint8_t* left;
+  const uint8_t* right;
+  int64_t in_pitch;   // bytes
+  uint16_t* disp;     // final map
+  int64_t out_pitch;  // bytes
+  int W, H, D;
+  uint64_t* ctl;      // census descriptors of the left / right image, [H][W]
+  uint64_t* ctr;
+  uint8_t* cost;      // [H][W][D]
+  void* agg;          // [H][W][D], uint16 (or uint32 when wide)
+  uint16_t* dl;       // [H][W] winner-takes-all map
+  uint16_t* dr;       // [H][W] approximate right map
+  uint16_t* dlr;      // [H][W] map after the left-right check (median input)
+  uint8_t* mask;      // [H][W] 1 = kept by the left-right check
+};
+
+// Method parameters shared by every pair of a call.
+struct Method {
+  int cw, ch;       // census window
+  int P1, P2;
+  int num_paths;    // 4 or 8
+  int flags;        // 1 = LR check, 2 = median
+  int lr_threshold;
+  int wide;         // aggregated sums kept in uint32 (needed when 8 (255 + P2) > 65535)
+};
+
+__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b) {
+  uint32_t r;
+  asm("min.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+  return r;
+}
+
+// Lanes per line and disparities per lane of the aggregation for a disparity count D.
+__host__ __device__ inline int agg_lanes_for(int D, int dpl) {
+  int need = (D + dpl - 1) / dpl;
+  int lpl = 8;
+  while (lpl < need) lpl *= 2;
+  return lpl;
+}
+
+}  // namespace r2t

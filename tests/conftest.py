@@ -10,7 +10,6 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
-    config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
 
 
 def pytest_collection_modifyitems(config, items):
@@ -25,3 +24,11 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def cuda_lib():
+    """Builds (if stale) and loads libres2tac.so."""
+    from paper_2106_07927_gb300 import binding, build
+    build.build()
+    return binding.load()

@@ -1,0 +1,150 @@
+"""GPU path vs the CPU oracle, bit-exact on every intermediate (cost, aggregated volume, D^L,
+D^R, LR mask) and on the final map. All arithmetic of the method is integer, so the bar is
+equality, not a tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_07927_gb300 import binding, scenes
+
+pytestmark = pytest.mark.gpu
+
+KEYS = ("cost", "agg", "dl", "dr", "mask")
+
+
+def _gpu(left, right, prm, in_pad=0, out_pad=0, tuning=None):
+    import torch
+    H, W = left.shape
+    st = binding.Stereo(prm)
+    if tuning is not None:
+        binding.res2tac_set_tuning(st.handle, tuning)
+    Lb = torch.zeros((H, W + in_pad), dtype=torch.uint8, device="cuda")
+    Rb = torch.zeros((H, W + in_pad), dtype=torch.uint8, device="cuda")
+    Lb[:, :W] = torch.from_numpy(left).cuda()
+    Rb[:, :W] = torch.from_numpy(right).cuda()
+    outb = torch.full((H, W + out_pad), 0x1234, dtype=torch.int16, device="cuda")
+    binding.res2tac_compute(st.handle, Lb.data_ptr(), Rb.data_ptr(), W + in_pad, outb.data_ptr(),
+                            2 * (W + out_pad), torch.cuda.current_stream().cuda_stream)
+    dbg = st.debug_outputs()
+    torch.cuda.synchronize()
+    out = binding.u16(outb)
+    if out_pad:
+        assert np.all(out[:, W:] == 0x1234), "wrote outside the row"
+    got = {"cost": dbg["cost"].cpu().numpy(), "agg": binding.u16(dbg["agg"]),
+           "dl": binding.u16(dbg["dl"]), "dr": binding.u16(dbg["dr"]),
+           "mask": dbg["mask"].cpu().numpy()}
+    st.close()
+    return out[:, :W], got
+
+
+def _oracle(left, right, prm):
+    return oracle.sgm(left, right, prm["max_disp"], prm["census_w"], prm["census_h"], prm["p1"],
+                      prm["p2"], prm["num_paths"], prm["flags"], prm["lr_threshold"], debug=True)
+
+
+def _assert_same(left, right, prm, **kw):
+    out, got = _gpu(left, right, prm, **kw)
+    ref, rdbg = _oracle(left, right, prm)
+    for k in KEYS:
+        if not np.array_equal(got[k], rdbg[k]):
+            bad = np.argwhere(got[k] != rdbg[k])
+            raise AssertionError(f"{k}: {len(bad)} mismatches, first at {bad[0].tolist()}: "
+                                 f"gpu {got[k][tuple(bad[0])]} oracle {rdbg[k][tuple(bad[0])]}")
+    assert np.array_equal(out, ref), "final map"
+    return out, ref
+
+
+@pytest.mark.parametrize("name", list(scenes.SINGLE))
+def test_single_pair_workloads_full_size(name):
+    left, right, _, prm = scenes.single_pair(name, 0)
+    _assert_same(left, right, prm)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_tiny_random_shapes(seed):
+    rng = np.random.default_rng(100 + seed)
+    W = int(rng.integers(1, 70))
+    H = int(rng.integers(1, 40))
+    D = int(rng.choice([16, 32, 48, 64, 80, 128, 144, 256]))
+    cw, ch = ((5, 5), (9, 7))[seed % 2]
+    R = (4, 8)[(seed // 2) % 2]
+    flags = seed % 4
+    left = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    right = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    P1 = int(rng.integers(0, 30))
+    P2 = int(rng.integers(P1, 300))
+    prm = scenes.params(W, H, D, cw, ch, P1, P2, R, flags, int(rng.integers(0, 3)))
+    _assert_same(left, right, prm)
+
+
+@pytest.mark.parametrize("W,H,D", [(200, 3, 64), (3, 150, 32), (97, 61, 128), (257, 33, 256)])
+def test_ragged_tiles(W, H, D):
+    left, right, _ = scenes.make_scene("road", W + H, W, H, D)
+    prm = scenes.params(W, H, D, 9, 7, 10, 120, 8, 3)
+    _assert_same(left, right, prm)
+
+
+def test_wide_sums_saturate_exactly():
+    # P2 = 16384 with 8 paths: sums can exceed 65535, so the library keeps uint32 sums and
+    # saturates them; the oracle saturates the exact sum.
+    rng = np.random.default_rng(5)
+    W, H, D = 150, 90, 32
+    left = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    right = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    prm = scenes.params(W, H, D, 5, 5, 100, 16384, 8, 3)
+    ref, rdbg = _oracle(left, right, prm)
+    assert (rdbg["agg"] == 65535).any(), "test input must reach saturation"
+    _assert_same(left, right, prm)
+
+
+def test_padded_pitches():
+    left, right, _ = scenes.make_scene("nadir", 3, 130, 70, 64)
+    prm = scenes.params(130, 70, 64, 9, 7, 8, 96, 8, 3)
+    _assert_same(left, right, prm, in_pad=14, out_pad=6)
+
+
+def test_every_tuning_is_bit_identical():
+    left, right, _ = scenes.make_scene("road", 11, 300, 120, 128)
+    prm = scenes.params(300, 120, 128, 9, 7, 10, 120, 8, 3)
+    ref, rdbg = _oracle(left, right, prm)
+    n = 0
+    for dpl in (4, 8):
+        for warps in (1, 4, 8):
+            for chunk in (32, 128, 256):
+                t = binding.res2tac_tuning(dpl, warps, chunk, 0)
+                out, got = _gpu(left, right, prm, tuning=t)
+                assert np.array_equal(out, ref), (dpl, warps, chunk)
+                assert np.array_equal(got["agg"], rdbg["agg"])
+                n += 1
+    assert n == 18
+
+
+def test_repeatable_and_host_path():
+    import torch
+    left, right, _, prm = scenes.single_pair("320x240_d64_ct5x5_r4", 3)
+    st = binding.Stereo(prm)
+    a = st.compute(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()).clone()
+    b = st.compute(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda())
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    host_out = np.zeros((prm["height"], prm["width"]), np.uint16)
+    binding.res2tac_compute_host(st.handle, left.ctypes.data, right.ctypes.data, prm["width"],
+                                 host_out.ctypes.data, 2 * prm["width"], 0)
+    assert np.array_equal(host_out, binding.u16(a))
+    assert binding.res2tac_last_launch_count(st.handle) == 4
+    st.close()
+
+
+def test_invalid_pointers_and_pitch_rejected():
+    import torch
+    prm = scenes.params(64, 32, 32, 5, 5, 10, 120, 4, 0)
+    st = binding.Stereo(prm)
+    x = torch.zeros((32, 64), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((32, 64), dtype=torch.int16, device="cuda")
+    with pytest.raises(binding.Res2tacError):
+        binding.res2tac_compute(st.handle, x.data_ptr(), x.data_ptr(), 63, out.data_ptr(), 128, 0)
+    with pytest.raises(binding.Res2tacError):
+        binding.res2tac_compute(st.handle, x.data_ptr(), 0, 64, out.data_ptr(), 128, 0)
+    with pytest.raises(binding.Res2tacError):
+        binding.res2tac_compute(st.handle, x.data_ptr(), x.data_ptr(), 64, out.data_ptr(), 127, 0)
+    st.close()
