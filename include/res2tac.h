@@ -138,6 +138,12 @@ size_t res2tac_workspace_bytes(const res2tac_params* p);
 size_t res2tac_batch_workspace_bytes(const res2tac_params* p, const res2tac_pair* pairs,
                                      int32_t n);
 
+/* Pre-allocates the context's batch engine for batches of at most max_pairs pairs whose
+ * res2tac_batch_workspace_bytes is at most scratch_bytes, so that such batches allocate nothing
+ * (a serving loop reserves once, then admits work by its own memory accounting). Grow-only;
+ * synchronises the device when it grows. RES2TAC_ENOMEM if the memory is not available. */
+int res2tac_batch_reserve(res2tac_t h, size_t scratch_bytes, int32_t max_pairs);
+
 /* Reads / sets the kernel configuration (RES2TAC_EINVAL for a setting the context's D cannot
  * use). res2tac_autotune times every valid setting on the given device pair (left, right,
  * in_pitch as for res2tac_compute, output into disp), keeps the fastest in the context and

@@ -27,7 +27,7 @@ EXPORTS = (
     "res2tac_debug_outputs", "res2tac_workspace_bytes", "res2tac_batch_workspace_bytes",
     "res2tac_get_tuning", "res2tac_set_tuning", "res2tac_autotune", "res2tac_last_launch_count",
     "res2tac_destroy", "res2tac_strerror", "res2tac_last_error", "res2tac_set_profiling",
-    "res2tac_stage_times", "res2tac_probe_int_peak",
+    "res2tac_stage_times", "res2tac_probe_int_peak", "res2tac_batch_reserve",
 )
 STAGES = ("census", "cost", "aggregate", "wta_lr", "median")
 
@@ -94,6 +94,7 @@ def load():
         "res2tac_stage_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
         "res2tac_probe_int_peak": (ctypes.c_int, [ctypes.c_int, P,
                                                   ctypes.POINTER(ctypes.c_double)]),
+        "res2tac_batch_reserve": (ctypes.c_int, [P, S, I32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -154,6 +155,10 @@ def res2tac_workspace_bytes(params: res2tac_params) -> int:
 def res2tac_batch_workspace_bytes(params: res2tac_params, pairs) -> int:
     arr = (res2tac_pair * len(pairs))(*pairs)
     return int(load().res2tac_batch_workspace_bytes(ctypes.byref(params), arr, len(pairs)))
+
+
+def res2tac_batch_reserve(h: int, scratch_bytes: int, max_pairs: int) -> None:
+    _check(load().res2tac_batch_reserve(h, scratch_bytes, max_pairs))
 
 
 def res2tac_get_tuning(h: int) -> res2tac_tuning:

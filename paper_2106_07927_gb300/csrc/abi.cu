@@ -373,6 +373,14 @@ size_t res2tac_batch_workspace_bytes(const res2tac_params* p, const res2tac_pair
   return total + r2t::batch_fixed_bytes(n);
 }
 
+int res2tac_batch_reserve(res2tac_t h, size_t scratch_bytes, int32_t max_pairs) {
+  if (!h || max_pairs < 1) return fail(RES2TAC_EINVAL, "bad batch reservation");
+  int rc = r2t::batch_reserve(&h->batch, scratch_bytes, max_pairs);
+  if (rc == -2) return fail(RES2TAC_ENOMEM, "batch reservation of %zu bytes failed", scratch_bytes);
+  if (rc) return fail(RES2TAC_ECUDA, "batch reservation: %s", r2t::batch_error(h->batch));
+  return RES2TAC_OK;
+}
+
 int res2tac_compute_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res2tac_stream_t s) {
   if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
   if (!pairs || n < 1) return fail(RES2TAC_EINVAL, "empty batch");

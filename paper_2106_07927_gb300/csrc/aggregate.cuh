@@ -69,18 +69,41 @@ __host__ __device__ inline int agg_num_lines(int W, int H, int num_paths) {
 struct LineGeom {
   int sx, sy, dx, dy, len;
 };
-__host__ __device__ inline LineGeom line_geom(int li, int W, int H, int num_paths) {
-  int nl[4] = {H, W, W + H - 1, W + H - 1};
-  int order[4];
+// Axis order of the line index space (the longer of rows / columns first, then the diagonals)
+// and the number of axes (2 or 4).
+__host__ __device__ inline int axis_order(int W, int H, int num_paths, int (&order)[4]) {
   if (W >= H) {
     order[0] = 0; order[1] = 2; order[2] = 3; order[3] = 1;
   } else {
     order[0] = 1; order[1] = 2; order[2] = 3; order[3] = 0;
   }
-  if (num_paths == 4) {
-    order[1] = order[3];
+  if (num_paths == 4) order[1] = order[3];
+  return num_paths == 8 ? 4 : 2;
+}
+
+// The axes as contiguous segments [begin, end) of the line index space, with the longest line
+// of each; returns the number of segments.
+__host__ __device__ inline int agg_segments(int W, int H, int num_paths, int* begin, int* end,
+                                            int* maxlen) {
+  const int nl[4] = {H, W, W + H - 1, W + H - 1};
+  const int mn = W < H ? W : H;
+  const int ml[4] = {W, H, mn, mn};
+  int order[4];
+  const int naxes = axis_order(W, H, num_paths, order);
+  int b = 0;
+  for (int a = 0; a < naxes; a++) {
+    begin[a] = b;
+    b += nl[order[a]];
+    end[a] = b;
+    maxlen[a] = ml[order[a]];
   }
-  const int naxes = num_paths == 8 ? 4 : 2;
+  return naxes;
+}
+
+__host__ __device__ inline LineGeom line_geom(int li, int W, int H, int num_paths) {
+  int nl[4] = {H, W, W + H - 1, W + H - 1};
+  int order[4];
+  const int naxes = axis_order(W, H, num_paths, order);
   int axis = -1, i = li;
   for (int a = 0; a < naxes; a++) {
     int n = nl[order[a]];
@@ -171,10 +194,11 @@ __device__ __forceinline__ void add_to_sum(void* aggp, const uint32_t (&L)[DPL /
   }
 }
 
-// Aggregates the lines [line0, line0 + 32 / LPL) of one pair with one warp: lane group g walks
-// line line0 + g in both directions and adds both chains into S.
+// Aggregates the lines [line0, min(line0 + 32 / LPL, line_end)) of one pair with one warp: lane
+// group g walks line line0 + g in both directions and adds both chains into S.
 template <int DPL, int LPL, bool WIDE>
-__device__ __forceinline__ void agg_warp_lines(const Problem& pb, const Method& mt, int line0) {
+__device__ __forceinline__ void agg_warp_lines(const Problem& pb, const Method& mt, int line0,
+                                               int line_end) {
   typedef RawCost<DPL> RC;
   typedef typename RC::T Raw;
   constexpr int NP = DPL / 2;
@@ -183,7 +207,7 @@ __device__ __forceinline__ void agg_warp_lines(const Problem& pb, const Method& 
   const int lig = lane % LPL;
   const int li = line0 + lane / LPL;
   const int W = pb.W, H = pb.H, D = pb.D;
-  const int nl = agg_num_lines(W, H, mt.num_paths);
+  const int nl = min(agg_num_lines(W, H, mt.num_paths), line_end);
   LineGeom g;
   if (li < nl) {
     g = line_geom(li, W, H, mt.num_paths);

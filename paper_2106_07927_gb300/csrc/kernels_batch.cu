@@ -2,8 +2,13 @@
 // batch. A block (or, in the aggregation, a warp) claims its next work item from a device queue
 // with one atomic increment and maps it to (pair, item of that pair) through per-stage prefix
 // tables; no block ever waits for another, so the queue needs no device-side spin. Stage order is
-// kept by the launch order on one stream. The descriptor upload, the queue reset and the five
-// stage kernels are recorded once into a CUDA graph and replayed while the capacities last.
+// kept by the launch order on one stream. The descriptor upload, the queue reset and the stage
+// kernels are recorded once into a CUDA graph and replayed while the capacities last.
+//
+// Aggregation work is described by segments: one per axis of every pair (rows, columns,
+// diagonals, anti-diagonals), a contiguous range of line indices. Segments are ordered by their
+// longest line across the whole batch (longest first), so the sequential chains that bound the
+// batch's duration start earliest; a warp claims one group of 32 / LPL lines of a segment.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -20,17 +25,22 @@ namespace r2t {
 
 enum { kStCensus = 0, kStCost = 1, kStAgg = 2, kStWta = 3, kStMedian = 4, kNumStages = 5 };
 
-// Header of the device descriptor block; followed by Problem[cap_pairs], int prefix[4][cap+1]
-// (census, cost, wta, median) and int2 agg_items[cap_items] (pair, first line).
+// Header of the device descriptor block. It is followed by Problem[cap_pairs],
+// int prefix[4][cap_pairs + 1] (census, cost, wta, median items), AggSeg[4 cap_pairs] and
+// int seg_prefix[4 cap_pairs + 1] (aggregation items).
 struct BatchHeader {
   int n;
+  int nseg;
   int total[kNumStages];
-  int wta_smem_max;
   int pad;
   signed char dpl_by_d16[17];  // aggregation disparities per lane, indexed by D / 16
 };
 
-__device__ __forceinline__ int find_pair(const int* prefix, int n, int item) {
+struct AggSeg {
+  int pair, begin, end, group;  // lines [begin, end) of one pair, `group` lines per warp item
+};
+
+__device__ __forceinline__ int find_slot(const int* prefix, int n, int item) {
   int lo = 0, hi = n - 1;  // largest p with prefix[p] <= item
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -59,7 +69,7 @@ __global__ void __launch_bounds__(256) batch_census_kernel(const BatchHeader* hd
   for (;;) {
     const int item = claim_block(&counters[kStCensus], &s_item);
     if (item >= total) break;
-    const int p = find_pair(prefix, n, item);
+    const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
     census_tile_dispatch(pb, mt, item - prefix[p], sm);
   }
@@ -74,7 +84,7 @@ __global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
   for (;;) {
     const int item = claim_block(&counters[kStCost], &s_item);
     if (item >= total) break;
-    const int p = find_pair(prefix, n, item);
+    const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
     cost_tile(pb, item - prefix[p], sm, mt.wide ? 4 : 2);
   }
@@ -82,36 +92,38 @@ __global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
 
 template <bool WIDE>
 __device__ __forceinline__ void agg_dispatch(const Problem& pb, const Method& mt, int line0,
-                                             int dpl) {
+                                             int line_end, int dpl) {
   const int lpl = agg_lanes_for(pb.D, dpl);
   switch (dpl * 100 + lpl) {
-    case 208: agg_warp_lines<2, 8, WIDE>(pb, mt, line0); break;
-    case 408: agg_warp_lines<4, 8, WIDE>(pb, mt, line0); break;
-    case 808: agg_warp_lines<8, 8, WIDE>(pb, mt, line0); break;
-    case 216: agg_warp_lines<2, 16, WIDE>(pb, mt, line0); break;
-    case 232: agg_warp_lines<2, 32, WIDE>(pb, mt, line0); break;
-    case 416: agg_warp_lines<4, 16, WIDE>(pb, mt, line0); break;
-    case 432: agg_warp_lines<4, 32, WIDE>(pb, mt, line0); break;
-    case 816: agg_warp_lines<8, 16, WIDE>(pb, mt, line0); break;
-    case 832: agg_warp_lines<8, 32, WIDE>(pb, mt, line0); break;
+    case 208: agg_warp_lines<2, 8, WIDE>(pb, mt, line0, line_end); break;
+    case 216: agg_warp_lines<2, 16, WIDE>(pb, mt, line0, line_end); break;
+    case 232: agg_warp_lines<2, 32, WIDE>(pb, mt, line0, line_end); break;
+    case 408: agg_warp_lines<4, 8, WIDE>(pb, mt, line0, line_end); break;
+    case 416: agg_warp_lines<4, 16, WIDE>(pb, mt, line0, line_end); break;
+    case 432: agg_warp_lines<4, 32, WIDE>(pb, mt, line0, line_end); break;
+    case 808: agg_warp_lines<8, 8, WIDE>(pb, mt, line0, line_end); break;
+    case 816: agg_warp_lines<8, 16, WIDE>(pb, mt, line0, line_end); break;
+    case 832: agg_warp_lines<8, 32, WIDE>(pb, mt, line0, line_end); break;
     default: break;
   }
 }
 
 template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_agg_kernel(const BatchHeader* hd, const Problem* probs,
-                                                        const int2* items, Method mt,
-                                                        unsigned* counters) {
-  const int total = hd->total[kStAgg];
+                                                        const AggSeg* segs, const int* seg_prefix,
+                                                        Method mt, unsigned* counters) {
+  const int total = hd->total[kStAgg], nseg = hd->nseg;
   const int lane = threadIdx.x & 31;
   for (;;) {
     int item = 0;
     if (lane == 0) item = (int)atomicAdd(&counters[kStAgg], 1u);
     item = __shfl_sync(0xffffffffu, item, 0);
     if (item >= total) break;
-    const int2 it = items[item];
-    const Problem pb = probs[it.x];
-    agg_dispatch<WIDE>(pb, mt, it.y, hd->dpl_by_d16[pb.D / 16]);
+    const int si = find_slot(seg_prefix, nseg, item);
+    const AggSeg sg = segs[si];
+    const Problem pb = probs[sg.pair];
+    const int line0 = sg.begin + (item - seg_prefix[si]) * sg.group;
+    agg_dispatch<WIDE>(pb, mt, line0, sg.end, hd->dpl_by_d16[pb.D / 16]);
   }
 }
 
@@ -125,7 +137,7 @@ __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, c
   for (;;) {
     const int item = claim_block(&counters[kStWta], &s_item);
     if (item >= total) break;
-    const int p = find_pair(prefix, n, item);
+    const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
     const int y = item - prefix[p];
     uint16_t* out_row = (mt.flags & 2) ? pb.dlr + (int64_t)y * pb.W
@@ -144,7 +156,7 @@ __global__ void __launch_bounds__(256) batch_median_kernel(const BatchHeader* hd
   for (;;) {
     const int item = claim_block(&counters[kStMedian], &s_item);
     if (item >= total) break;
-    const int p = find_pair(prefix, n, item);
+    const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
     median_tile(pb.dlr, pb.W, pb.W, pb.H, pb.disp, pb.out_pitch, item - prefix[p], sm);
   }
@@ -152,19 +164,13 @@ __global__ void __launch_bounds__(256) batch_median_kernel(const BatchHeader* hd
 
 static int default_dpl(int D) { return D <= 64 ? 2 : (D <= 128 ? 4 : 8); }
 
-struct BatchItem {
-  int pair, line0, len;
-};
-
 struct BatchEngine {
-  std::vector<int> shape_key;        // n, paths and every (W, H, D) of the cached layout
-  std::vector<BatchItem> agg_items;  // aggregation work list of that layout
   char* scratch = nullptr;
   size_t scratch_cap = 0;
   char* d_desc = nullptr;  // descriptor block (device)
   char* h_desc = nullptr;  // its pinned host image
   size_t desc_bytes = 0;
-  int cap_pairs = 0, cap_items = 0;
+  int cap_pairs = 0;
   unsigned* d_counters = nullptr;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -177,17 +183,15 @@ struct BatchEngine {
   char err[256];
 };
 
-static size_t prefix_offset(int cap_pairs) {
-  return (sizeof(BatchHeader) + 255) / 256 * 256 + (size_t)cap_pairs * sizeof(Problem);
+static size_t probs_offset() { return (sizeof(BatchHeader) + 255) / 256 * 256; }
+static size_t prefix_offset(int cap) { return probs_offset() + (size_t)cap * sizeof(Problem); }
+static size_t segs_offset(int cap) {
+  return (prefix_offset(cap) + 4 * sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
 }
-static size_t items_offset(int cap_pairs) {
-  return (prefix_offset(cap_pairs) + 4 * sizeof(int) * (size_t)(cap_pairs + 1) + 15) / 16 * 16;
-}
-static size_t desc_size(int cap_pairs, int cap_items) {
-  return items_offset(cap_pairs) + sizeof(int2) * (size_t)cap_items;
-}
+static size_t seg_prefix_offset(int cap) { return segs_offset(cap) + 4 * (size_t)cap * sizeof(AggSeg); }
+static size_t desc_size(int cap) { return seg_prefix_offset(cap) + sizeof(int) * (4 * (size_t)cap + 1); }
 
-size_t batch_fixed_bytes(int n) { return desc_size(n, 0) + 64 * 1024 * (size_t)n + 4096; }
+size_t batch_fixed_bytes(int n) { return desc_size(n) + 4096; }
 
 static int set_err(BatchEngine* e, cudaError_t c, const char* what) {
   cudaGetLastError();
@@ -195,22 +199,45 @@ static int set_err(BatchEngine* e, cudaError_t c, const char* what) {
   return c == cudaErrorMemoryAllocation ? -2 : -3;
 }
 
+static int grow_desc(BatchEngine* e, int n) {
+  if (n <= e->cap_pairs) return 0;
+  const int cap = std::max(n, 2 * e->cap_pairs);
+  if (e->copy_pending) cudaEventSynchronize(e->copied);
+  cudaDeviceSynchronize();  // the old descriptor block may still be read by a running batch
+  cudaFree(e->d_desc);
+  cudaFreeHost(e->h_desc);
+  e->d_desc = nullptr;
+  e->h_desc = nullptr;
+  e->desc_bytes = desc_size(cap);
+  cudaError_t c = cudaMalloc(&e->d_desc, e->desc_bytes);
+  if (c == cudaSuccess) c = cudaMallocHost(&e->h_desc, e->desc_bytes);
+  if (c != cudaSuccess) {
+    e->cap_pairs = 0;
+    return set_err(e, c, "descriptor allocation");
+  }
+  e->cap_pairs = cap;
+  e->copy_pending = false;
+  if (e->exec) {  // the graph holds the old descriptor addresses
+    cudaGraphExecDestroy(e->exec);
+    e->exec = nullptr;
+  }
+  return 0;
+}
+
 int batch_reserve(BatchEngine** pe, size_t scratch_bytes, int n) {
   if (!*pe) {
     BatchEngine* e = new BatchEngine();
     for (int i = 0; i < 17; i++) e->dpl_by_d16[i] = (signed char)default_dpl(i * 16);
     e->err[0] = 0;
+    memset(&e->graph_method, 0, sizeof(Method));
+    *pe = e;
     cudaError_t c = cudaMalloc(&e->d_counters, 64);
     if (c == cudaSuccess) c = cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking);
     if (c == cudaSuccess) c = cudaEventCreateWithFlags(&e->copied, cudaEventDisableTiming);
-    if (c != cudaSuccess) {
-      int rc = set_err(e, c, "batch engine setup");
-      *pe = e;
-      return rc;
-    }
-    *pe = e;
+    if (c != cudaSuccess) return set_err(e, c, "batch engine setup");
   }
   BatchEngine* e = *pe;
+  if (!e->d_counters) return set_err(e, cudaErrorInitializationError, "batch engine setup");
   if (scratch_bytes > e->scratch_cap) {
     // the previous batch may still run on its stream: wait before freeing its scratch
     cudaDeviceSynchronize();
@@ -221,8 +248,7 @@ int batch_reserve(BatchEngine** pe, size_t scratch_bytes, int n) {
     if (c != cudaSuccess) return set_err(e, c, "batch scratch allocation");
     e->scratch_cap = scratch_bytes;
   }
-  (void)n;
-  return 0;
+  return grow_desc(e, n);
 }
 
 char* batch_scratch(BatchEngine* e) { return e ? e->scratch : nullptr; }
@@ -245,13 +271,12 @@ void batch_destroy(BatchEngine* e) {
 }
 
 template <class K>
-static int persistent_grid(K kernel, size_t smem, int items) {
+static int persistent_grid(K kernel, size_t smem) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
   if (per_sm < 1) per_sm = 1;
-  (void)items;
   return sms * per_sm;
 }
 
@@ -260,25 +285,26 @@ static int capture(BatchEngine* e, const Method& mt, int wta_smem) {
     cudaGraphExecDestroy(e->exec);
     e->exec = nullptr;
   }
+  const int cap = e->cap_pairs;
   const BatchHeader* hd = reinterpret_cast<const BatchHeader*>(e->d_desc);
-  const Problem* probs =
-      reinterpret_cast<const Problem*>(e->d_desc + (sizeof(BatchHeader) + 255) / 256 * 256);
-  const int* prefix = reinterpret_cast<const int*>(e->d_desc + prefix_offset(e->cap_pairs));
-  const int stride = e->cap_pairs + 1;
-  const int2* items = reinterpret_cast<const int2*>(e->d_desc + items_offset(e->cap_pairs));
+  const Problem* probs = reinterpret_cast<const Problem*>(e->d_desc + probs_offset());
+  const int* prefix = reinterpret_cast<const int*>(e->d_desc + prefix_offset(cap));
+  const int stride = cap + 1;
+  const AggSeg* segs = reinterpret_cast<const AggSeg*>(e->d_desc + segs_offset(cap));
+  const int* seg_prefix = reinterpret_cast<const int*>(e->d_desc + seg_prefix_offset(cap));
   // launch shapes and attributes are settled before the capture starts
   const bool wide = mt.wide != 0;
   cudaFuncSetAttribute(batch_wta_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        wta_smem);
   cudaFuncSetAttribute(batch_wta_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        wta_smem);
-  const int g_census = persistent_grid(batch_census_kernel, 0, 0);
-  const int g_cost = persistent_grid(batch_cost_kernel, 0, 0);
-  const int g_agg = wide ? persistent_grid(batch_agg_kernel<true>, 0, 0)
-                         : persistent_grid(batch_agg_kernel<false>, 0, 0);
-  const int g_wta = wide ? persistent_grid(batch_wta_kernel<true>, wta_smem, 0)
-                         : persistent_grid(batch_wta_kernel<false>, wta_smem, 0);
-  const int g_med = persistent_grid(batch_median_kernel, 0, 0);
+  const int g_census = persistent_grid(batch_census_kernel, 0);
+  const int g_cost = persistent_grid(batch_cost_kernel, 0);
+  const int g_agg = wide ? persistent_grid(batch_agg_kernel<true>, 0)
+                         : persistent_grid(batch_agg_kernel<false>, 0);
+  const int g_wta = wide ? persistent_grid(batch_wta_kernel<true>, wta_smem)
+                         : persistent_grid(batch_wta_kernel<false>, wta_smem);
+  const int g_med = persistent_grid(batch_median_kernel, 0);
   cudaError_t c = cudaGetLastError();
   if (c != cudaSuccess) return set_err(e, c, "kernel attributes");
   cudaStream_t cs = e->cap_stream;
@@ -287,17 +313,20 @@ static int capture(BatchEngine* e, const Method& mt, int wta_smem) {
   if (c != cudaSuccess) return set_err(e, c, "begin capture");
   int launches = 0;
   cudaMemcpyAsync(e->d_desc, e->h_desc, e->desc_bytes, cudaMemcpyHostToDevice, cs);
-  cudaEventRecord(e->copied, cs);
+  // an external record node, so the host can wait for the upload of each replay
+  cudaEventRecordWithFlags(e->copied, cs, cudaEventRecordExternal);
   cudaMemsetAsync(e->d_counters, 0, 64, cs);
   batch_census_kernel<<<g_census, 256, 0, cs>>>(hd, probs, prefix + 0 * stride, mt,
                                                 e->d_counters);
   batch_cost_kernel<<<g_cost, 256, 0, cs>>>(hd, probs, prefix + 1 * stride, mt, e->d_counters);
   if (wide) {
-    batch_agg_kernel<true><<<g_agg, 256, 0, cs>>>(hd, probs, items, mt, e->d_counters);
+    batch_agg_kernel<true><<<g_agg, 256, 0, cs>>>(hd, probs, segs, seg_prefix, mt,
+                                                  e->d_counters);
     batch_wta_kernel<true><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 2 * stride, mt,
                                                          e->d_counters);
   } else {
-    batch_agg_kernel<false><<<g_agg, 256, 0, cs>>>(hd, probs, items, mt, e->d_counters);
+    batch_agg_kernel<false><<<g_agg, 256, 0, cs>>>(hd, probs, segs, seg_prefix, mt,
+                                                   e->d_counters);
     batch_wta_kernel<false><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 2 * stride, mt,
                                                           e->d_counters);
   }
@@ -319,75 +348,38 @@ static int capture(BatchEngine* e, const Method& mt, int wta_smem) {
 
 int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cudaStream_t s,
               int* launches) {
-  // aggregation items: groups of 32 / LPL lines, the longest lines first across all pairs
-  typedef BatchItem Item;
-  std::vector<int> shape_key;
-  shape_key.reserve(3 * n + 2);
-  shape_key.push_back(n);
-  shape_key.push_back(mt.num_paths);
-  for (int p = 0; p < n; p++) {
-    shape_key.push_back(probs[p].W);
-    shape_key.push_back(probs[p].H);
-    shape_key.push_back(probs[p].D);
-  }
-  std::vector<Item>& agg = e->agg_items;
-  int wta_smem = 0;
-  const bool same_layout = shape_key == e->shape_key;
-  if (!same_layout) agg.clear();
-  for (int p = 0; p < n; p++) {
-    const Problem& pb = probs[p];
-    const int dpl = e->dpl_by_d16[pb.D / 16];
-    const int G = 32 / agg_lanes_for(pb.D, dpl);
-    const int nl = agg_num_lines(pb.W, pb.H, mt.num_paths);
-    for (int l0 = 0; l0 < nl && !same_layout; l0 += G) {
-      int len = 0;
-      for (int j = l0; j < l0 + G && j < nl; j++)
-        len = std::max(len, line_geom(j, pb.W, pb.H, mt.num_paths).len);
-      agg.push_back(Item{p, l0, len});
-    }
-    wta_smem = std::max(wta_smem, (int)wta_smem_bytes(pb.D, wta_default_chunk(pb.D)));
-  }
-  if (!same_layout) {
-    std::stable_sort(agg.begin(), agg.end(),
-                     [](const BatchItem& a, const BatchItem& b) { return a.len > b.len; });
-    e->shape_key = shape_key;
-  }
-  const int nitems = (int)agg.size();
-  bool recapture = !e->exec;
-  if (n > e->cap_pairs || nitems > e->cap_items) {
-    const int cp = std::max(n, e->cap_pairs), ci = std::max(nitems, e->cap_items);
-    if (e->copy_pending) cudaEventSynchronize(e->copied);
-    cudaDeviceSynchronize();  // the old descriptor block may still be read by a running batch
-    cudaFree(e->d_desc);
-    cudaFreeHost(e->h_desc);
-    e->d_desc = nullptr;
-    e->h_desc = nullptr;
-    e->desc_bytes = desc_size(cp, ci);
-    cudaError_t c = cudaMalloc(&e->d_desc, e->desc_bytes);
-    if (c == cudaSuccess) c = cudaMallocHost(&e->h_desc, e->desc_bytes);
-    if (c != cudaSuccess) return set_err(e, c, "descriptor allocation");
-    e->cap_pairs = cp;
-    e->cap_items = ci;
-    e->copy_pending = false;
-    recapture = true;
-  }
-  if (memcmp(&e->graph_method, &mt, sizeof(Method)) != 0 || wta_smem > e->graph_wta_smem)
-    recapture = true;
+  int rc = grow_desc(e, n);
+  if (rc) return rc;
+  const int cap = e->cap_pairs;
   // the previous replay must have consumed the pinned descriptors before they are rewritten
   if (e->copy_pending) {
     cudaError_t c = cudaEventSynchronize(e->copied);
     if (c != cudaSuccess) return set_err(e, c, "descriptor upload wait");
+    e->copy_pending = false;
   }
   BatchHeader* hd = reinterpret_cast<BatchHeader*>(e->h_desc);
   memset(hd, 0, sizeof(BatchHeader));
-  hd->n = n;
-  Problem* hp = reinterpret_cast<Problem*>(e->h_desc + (sizeof(BatchHeader) + 255) / 256 * 256);
-  int* prefix = reinterpret_cast<int*>(e->h_desc + prefix_offset(e->cap_pairs));
-  const int stride = e->cap_pairs + 1;
+  Problem* hp = reinterpret_cast<Problem*>(e->h_desc + probs_offset());
+  int* prefix = reinterpret_cast<int*>(e->h_desc + prefix_offset(cap));
+  AggSeg* segs = reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap));
+  int* seg_prefix = reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap));
+  const int stride = cap + 1;
   int tot[4] = {0, 0, 0, 0};
+  int wta_smem = 0, nseg = 0;
+  struct Keyed {
+    AggSeg s;
+    int len;
+  };
+  Keyed keyed[4 * 64];
+  std::vector<Keyed> many;
+  Keyed* kv = keyed;
+  if (4 * n > 4 * 64) {
+    many.resize((size_t)4 * n);
+    kv = many.data();
+  }
   for (int p = 0; p < n; p++) {
-    hp[p] = probs[p];
     const Problem& pb = probs[p];
+    hp[p] = pb;
     prefix[0 * stride + p] = tot[0];
     prefix[1 * stride + p] = tot[1];
     prefix[2 * stride + p] = tot[2];
@@ -396,19 +388,32 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
     tot[1] += cost_items(pb.W, pb.H);
     tot[2] += pb.H;
     tot[3] += median_items(pb.W, pb.H);
+    wta_smem = std::max(wta_smem, (int)wta_smem_bytes(pb.D, wta_default_chunk(pb.D)));
+    int b[4], en[4], ml[4];
+    const int na = agg_segments(pb.W, pb.H, mt.num_paths, b, en, ml);
+    const int group = 32 / agg_lanes_for(pb.D, e->dpl_by_d16[pb.D / 16]);
+    for (int a = 0; a < na; a++) kv[nseg++] = Keyed{AggSeg{p, b[a], en[a], group}, ml[a]};
   }
   for (int k = 0; k < 4; k++) prefix[k * stride + n] = tot[k];
+  std::stable_sort(kv, kv + nseg, [](const Keyed& a, const Keyed& b) { return a.len > b.len; });
+  int items = 0;
+  for (int i = 0; i < nseg; i++) {
+    segs[i] = kv[i].s;
+    seg_prefix[i] = items;
+    items += (kv[i].s.end - kv[i].s.begin + kv[i].s.group - 1) / kv[i].s.group;
+  }
+  seg_prefix[nseg] = items;
+  hd->n = n;
+  hd->nseg = nseg;
   hd->total[kStCensus] = tot[0];
   hd->total[kStCost] = tot[1];
-  hd->total[kStAgg] = nitems;
+  hd->total[kStAgg] = items;
   hd->total[kStWta] = tot[2];
   hd->total[kStMedian] = tot[3];
-  hd->wta_smem_max = std::max(wta_smem, e->graph_wta_smem);
   memcpy(hd->dpl_by_d16, e->dpl_by_d16, sizeof(hd->dpl_by_d16));
-  int2* hi = reinterpret_cast<int2*>(e->h_desc + items_offset(e->cap_pairs));
-  for (int i = 0; i < nitems; i++) hi[i] = make_int2(agg[i].pair, agg[i].line0);
-  if (recapture) {
-    int rc = capture(e, mt, std::max(wta_smem, e->graph_wta_smem));
+  if (!e->exec || memcmp(&e->graph_method, &mt, sizeof(Method)) != 0 ||
+      wta_smem > e->graph_wta_smem) {
+    rc = capture(e, mt, std::max(wta_smem, e->graph_wta_smem));
     if (rc) return rc;
   }
   cudaError_t c = cudaGraphLaunch(e->exec, s);

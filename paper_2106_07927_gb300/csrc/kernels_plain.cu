@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(256) cost_kernel(Problem pb, int agg_bytes_per
 template <int DPL, int LPL, bool WIDE>
 __global__ void __launch_bounds__(512) aggregate_kernel(Problem pb, Method mt) {
   const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  agg_warp_lines<DPL, LPL, WIDE>(pb, mt, warp * (32 / LPL));
+  agg_warp_lines<DPL, LPL, WIDE>(pb, mt, warp * (32 / LPL), 0x7FFFFFFF);
 }
 
 template <bool WIDE>

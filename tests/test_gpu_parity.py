@@ -87,8 +87,10 @@ def test_ragged_tiles(W, H, D):
 def test_wide_sums_saturate_exactly():
     # P2 = 16384 with 8 paths: sums can exceed 65535, so the library keeps uint32 sums and
     # saturates them; the oracle saturates the exact sum.
+    # Near the left border, large d cost 255 at every step of the vertical paths and of the paths
+    # arriving from the right, so their L reach 255 + P2 and the sum passes 65535.
     rng = np.random.default_rng(5)
-    W, H, D = 150, 90, 32
+    W, H, D = 300, 200, 128
     left = rng.integers(0, 256, (H, W)).astype(np.uint8)
     right = rng.integers(0, 256, (H, W)).astype(np.uint8)
     prm = scenes.params(W, H, D, 5, 5, 100, 16384, 8, 3)
