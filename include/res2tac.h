@@ -170,6 +170,31 @@ int res2tac_stage_times(res2tac_t h, float* ms, int n);
  * counts two) through *lane_ops_per_s. Synchronises s. */
 int res2tac_probe_int_peak(int iters, res2tac_stream_t s, double* lane_ops_per_s);
 
+/* No-allocation variant of res2tac_compute. The paper has no counterpart: it is an addition for
+ * callers that must not allocate device memory while they run, for example an onboard stereo loop
+ * that is only allowed to allocate at start-up, a plugin whose host framework owns every byte of
+ * device memory, or a latency-critical loop that cannot take the device-wide synchronisation a
+ * cudaMalloc / cudaFree may cause. It needs no context and calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ * It runs the same pipeline as res2tac_compute on stream s, for the problem *p, with left /
+ * right / disp and the pitches as in res2tac_compute. Its scratch (census maps, cost volume,
+ * aggregated volume, intermediate maps) is one fixed device array of
+ * RES2TAC_STATIC_SCRATCH_BYTES compiled into the library; every GPU that loads the library holds
+ * that array until the process exits.
+ * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 23 B per pixel,
+ * 5 B per W*H*D when num_paths * (255 + p2) > 65535) is rejected with RES2TAC_ENOMEM and a
+ * message giving both sizes; 640 x 480 with D = 64 fits.
+ * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Sharing: every call in the process uses the same array, which keeps the contents of the last
+ * call; each call clears what must start at zero (the aggregated volume) itself. Calls that
+ * overlap on the GPU (on other streams, or from other host threads) race on the array, so the
+ * caller must serialise them. */
+#define RES2TAC_STATIC_SCRATCH_BYTES ((size_t)80 << 20)
+int res2tac_compute_static(const res2tac_params* p, const uint8_t* left, const uint8_t* right,
+                           int64_t in_pitch, uint16_t* disp, int64_t out_pitch,
+                           res2tac_stream_t s);
+
 /* Frees the context and its scratch. NULL-safe. The caller makes sure no work on the context
  * is still running. */
 void res2tac_destroy(res2tac_t h);

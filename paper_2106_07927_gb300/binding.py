@@ -28,7 +28,9 @@ EXPORTS = (
     "res2tac_get_tuning", "res2tac_set_tuning", "res2tac_autotune", "res2tac_last_launch_count",
     "res2tac_destroy", "res2tac_strerror", "res2tac_last_error", "res2tac_set_profiling",
     "res2tac_stage_times", "res2tac_probe_int_peak", "res2tac_batch_reserve",
+    "res2tac_compute_static",
 )
+RES2TAC_STATIC_SCRATCH_BYTES = 80 << 20
 STAGES = ("census", "cost", "aggregate", "wta_lr", "median")
 
 
@@ -95,6 +97,7 @@ def load():
         "res2tac_probe_int_peak": (ctypes.c_int, [ctypes.c_int, P,
                                                   ctypes.POINTER(ctypes.c_double)]),
         "res2tac_batch_reserve": (ctypes.c_int, [P, S, I32]),
+        "res2tac_compute_static": (ctypes.c_int, [PP, P, P, I64, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -136,6 +139,14 @@ def res2tac_compute(h: int, left: int, right: int, in_pitch: int, disp: int, out
 def res2tac_compute_host(h: int, left: int, right: int, in_pitch: int, disp: int, out_pitch: int,
                          stream: int = 0) -> None:
     _check(load().res2tac_compute_host(h, left, right, in_pitch, disp, out_pitch, stream))
+
+
+def res2tac_compute_static(params: res2tac_params, left: int, right: int, in_pitch: int,
+                           disp: int, out_pitch: int, stream: int = 0) -> None:
+    """No-allocation variant of res2tac_compute: no context; scratch is the library's fixed
+    device array (RES2TAC_STATIC_SCRATCH_BYTES), shared by every call."""
+    _check(load().res2tac_compute_static(ctypes.byref(params), left, right, in_pitch, disp,
+                                         out_pitch, stream))
 
 
 def res2tac_compute_batch(h: int, pairs, stream: int = 0) -> None:

@@ -102,6 +102,11 @@ r2t::Method method_of(const res2tac_params& p) {
 
 }  // namespace
 
+namespace r2t {
+// Records msg as the calling thread's last error (read by res2tac_last_error) and returns code.
+int report_error(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace r2t
+
 struct res2tac_ctx {
   res2tac_params p;
   r2t::Method method;

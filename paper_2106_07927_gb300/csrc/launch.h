@@ -26,6 +26,9 @@ bool tuning_valid(const Tuning& t, int D);
 cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
                          int* launches, cudaEvent_t* ev = nullptr);
 
+// Sets the calling thread's res2tac_last_error message; returns code.
+int report_error(int code, const char* msg);
+
 // Packed-u16 integer throughput probe: lane operations per second.
 cudaError_t probe_int_peak(int iters, cudaStream_t s, double* lane_ops_per_s);
 
