@@ -80,8 +80,8 @@ typedef struct res2tac_pair {
 /* Kernel configuration of a context. Every valid setting gives bit-identical results; only the
  * speed differs. agg_dpl: disparities per lane of the aggregation kernel (0 = automatic, else
  * 2, 4 or 8 with D / agg_dpl <= 32). agg_warps: warps per aggregation block (1..16).
- * wta_chunk: pixels per chunk of the winner-takes-all / right-disparity kernel (32..256, a
- * multiple of 32; 0 = automatic). */
+ * wta_chunk: pixels per block of the winner-takes-all / right-disparity kernel (32, 64, 128 or
+ * 256 with wta_chunk * D * 2 <= 96 KiB; 0 = automatic). */
 typedef struct res2tac_tuning {
   int32_t agg_dpl;
   int32_t agg_warps;
@@ -160,7 +160,7 @@ int res2tac_last_launch_count(res2tac_t h);
 /* Per-stage timing. With profiling enabled, res2tac_compute records a CUDA event on the caller's
  * stream before and after each stage. res2tac_stage_times waits for the last call and writes up
  * to n durations in milliseconds: [0] census, [1] cost (+ clearing of the aggregated volume),
- * [2] path aggregation, [3] WTA / right disparity / LR check, [4] median (0 when skipped). */
+ * [2] path aggregation, [3] WTA + right-disparity keys, [4] LR check + median. */
 int res2tac_set_profiling(res2tac_t h, int enable);
 int res2tac_stage_times(res2tac_t h, float* ms, int n);
 
@@ -181,7 +181,7 @@ int res2tac_probe_int_peak(int iters, res2tac_stream_t s, double* lane_ops_per_s
  * aggregated volume, intermediate maps) is one fixed device array of
  * RES2TAC_STATIC_SCRATCH_BYTES compiled into the library; every GPU that loads the library holds
  * that array until the process exits.
- * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 23 B per pixel,
+ * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 25 B per pixel,
  * 5 B per W*H*D when num_paths * (255 + p2) > 65535) is rejected with RES2TAC_ENOMEM and a
  * message giving both sizes; 640 x 480 with D = 64 fits.
  * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)

@@ -31,7 +31,7 @@ EXPORTS = (
     "res2tac_compute_static",
 )
 RES2TAC_STATIC_SCRATCH_BYTES = 80 << 20
-STAGES = ("census", "cost", "aggregate", "wta_lr", "median")
+STAGES = ("census", "cost", "aggregate", "wta_dr", "lr_median")
 
 
 class res2tac_params(ctypes.Structure):

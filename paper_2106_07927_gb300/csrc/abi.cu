@@ -9,6 +9,7 @@
 #include "../../include/res2tac.h"
 #include "batch.h"
 #include "launch.h"
+#include "layout.h"
 
 namespace {
 
@@ -49,43 +50,9 @@ const char* params_error(const res2tac_params* p) {
 
 bool needs_wide(const res2tac_params* p) { return p->num_paths * (255 + p->p2) > 65535; }
 
-// Byte offsets of the per-pair scratch buffers inside one allocation.
-struct Layout {
-  size_t ctl, ctr, cost, agg, dl, dr, dlr, mask, total;
-};
-
-Layout layout_for(int W, int H, int D, bool wide) {
-  const size_t npx = (size_t)W * H, nde = npx * D;
-  Layout l;
-  size_t o = 0;
-  l.ctl = o; o = align_up(o + npx * 8, 256);
-  l.ctr = o; o = align_up(o + npx * 8, 256);
-  l.cost = o; o = align_up(o + nde, 256);
-  l.agg = o; o = align_up(o + nde * (wide ? 4 : 2), 256);
-  l.dl = o; o = align_up(o + npx * 2, 256);
-  l.dr = o; o = align_up(o + npx * 2, 256);
-  l.dlr = o; o = align_up(o + npx * 2, 256);
-  l.mask = o; o = align_up(o + npx, 256);
-  l.total = o;
-  return l;
-}
-
-r2t::Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
-  r2t::Problem pb;
-  memset(&pb, 0, sizeof(pb));
-  pb.W = W;
-  pb.H = H;
-  pb.D = D;
-  pb.ctl = reinterpret_cast<uint64_t*>(base + l.ctl);
-  pb.ctr = reinterpret_cast<uint64_t*>(base + l.ctr);
-  pb.cost = reinterpret_cast<uint8_t*>(base + l.cost);
-  pb.agg = base + l.agg;
-  pb.dl = reinterpret_cast<uint16_t*>(base + l.dl);
-  pb.dr = reinterpret_cast<uint16_t*>(base + l.dr);
-  pb.dlr = reinterpret_cast<uint16_t*>(base + l.dlr);
-  pb.mask = reinterpret_cast<uint8_t*>(base + l.mask);
-  return pb;
-}
+using r2t::Layout;
+using r2t::layout_for;
+using r2t::problem_at;
 
 r2t::Method method_of(const res2tac_params& p) {
   r2t::Method m;
@@ -120,6 +87,7 @@ struct res2tac_ctx {
   r2t::BatchEngine* batch;
   int profiling;
   cudaEvent_t ev[6];  // stage boundaries of the last profiled compute
+  r2t::Fork fork;     // second stream for the concurrent aggregation kernels
 };
 
 extern "C" {
@@ -164,6 +132,7 @@ int res2tac_create(const res2tac_params* p, res2tac_t* out) {
   e = cudaMalloc(&h->scratch, h->lay.total);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_in, align_up(npx * 2, 256));
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_out, align_up(npx * 2, 256));
+  if (e == cudaSuccess) e = r2t::fork_create(&h->fork);
   if (e != cudaSuccess) {
     int rc = fail_cuda(e, "cudaMalloc of the context scratch");
     res2tac_destroy(h);
@@ -179,6 +148,7 @@ void res2tac_destroy(res2tac_t h) {
   cudaGetDevice(&cur);
   if (cur != h->device) cudaSetDevice(h->device);
   r2t::batch_destroy(h->batch);
+  r2t::fork_destroy(&h->fork);
   for (int i = 0; i < 6; i++)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   cudaFree(h->scratch);
@@ -212,7 +182,7 @@ int res2tac_compute(res2tac_t h, const uint8_t* left, const uint8_t* right, int6
   pb.out_pitch = out_pitch;
   int n = 0;
   cudaError_t e = r2t::run_pipeline(pb, h->method, h->tuning, (cudaStream_t)s, &n,
-                                    h->profiling ? h->ev : nullptr);
+                                    h->profiling ? h->ev : nullptr, &h->fork);
   h->last_launches = n;
   if (e != cudaSuccess) return fail_cuda(e, "res2tac_compute launch");
   return RES2TAC_OK;
@@ -245,9 +215,9 @@ int res2tac_debug_outputs(res2tac_t h, uint8_t* cost, uint16_t* agg, uint16_t* d
   if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
   r2t::Problem pb = problem_at(h->scratch, h->lay, h->p.width, h->p.height, h->p.max_disp);
   cudaStream_t st = (cudaStream_t)s;
-  const size_t npx = (size_t)pb.W * pb.H, nde = npx * pb.D;
+  const size_t npx = (size_t)pb.W * pb.H;
   cudaError_t e = cudaSuccess;
-  if (cost && e == cudaSuccess) e = cudaMemcpyAsync(cost, pb.cost, nde, cudaMemcpyDeviceToDevice, st);
+  if (cost && e == cudaSuccess) e = r2t::copy_cost(pb, cost, st);
   if (agg && e == cudaSuccess) e = r2t::copy_agg_u16(pb, h->method.wide != 0, agg, st);
   if (dl && e == cudaSuccess) e = cudaMemcpyAsync(dl, pb.dl, npx * 2, cudaMemcpyDeviceToDevice, st);
   if (dr && e == cudaSuccess) e = cudaMemcpyAsync(dr, pb.dr, npx * 2, cudaMemcpyDeviceToDevice, st);

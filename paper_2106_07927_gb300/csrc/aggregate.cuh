@@ -1,25 +1,105 @@
 // SGM path aggregation, Eq. (sgm_path) and Eq. (sgm_path_aggr) of Sec. 2.1.2.
 //
 // For one direction r and a pixel p with predecessor q = p - r inside the image,
-//   L_r(p,d) = C(p,d) + min(L_r(q,d), L_r(q,d-1) + P1, L_r(q,d+1) + P1, m + P2) - m,
-//   m = min_k L_r(q,k),
+//   L_r(p,d) = C(p,d) + min(L_r(q,d), L_r(q,d-1) + P1, L_r(q,d+1) + P1, m(q) + P2) - m(q),
+//   m(q) = min_k L_r(q,k),
 // and L_r(p,d) = C(p,d) where the path enters the image. With P1 <= P2 the four-term min equals
 // the paper's min over d' of L_r(q,d') + V(d,d'); subtracting m keeps L_r <= 255 + P2 so every
 // value fits 16 bits. S(p,d) = sum_r L_r(p,d), saturated at 65535.
 //
-// GB300 mapping (not the paper's): every path line is a sequential chain, so one group of LPL
-// lanes walks one line with the D disparities spread over the lanes, DPL per lane, held as
-// packed u16x2 registers. Both directions of a line (LR/RL, TB/BT, TLBR/BRTL, TRBL/BLTR) run in
-// the same group as two independent chains, which doubles the instruction-level parallelism of
-// the latency-bound recurrence. Neighbouring disparities cross lanes by one shuffle each way;
-// the group minimum m is one redux.sync. Path costs are added into S with 64-bit atomic adds of
-// four packed u16 lanes (no carry can cross a lane while 8 (255 + P2) <= 65535; above that the
-// sums are kept as uint32, "wide"). Integer addition is associative, so the result does not
-// depend on the order in which the eight directions arrive.
+// GB300 mapping (not the paper's). Every path line is a sequential chain; a group of lanes walks
+// one line with the D disparities spread over its lanes, held as packed u16x2 registers.
+// Neighbouring disparities cross lanes by one shuffle each way; the line's costs are added into
+// S with 64-bit atomic adds of four packed u16 lanes (no carry can cross a lane while
+// num_paths (255 + P2) <= 65535; above that the sums are uint32, "wide"). Integer addition is
+// associative, so the order in which directions arrive does not change S.
+// Two kernels split the lines:
+//  - the long axis (rows when W >= H, else columns) holds the longest chains, which bound the
+//    kernel's duration. One warp walks a line in both directions (two chains for ILP) with few
+//    disparities per lane, and forms m with a pipelined reduction: writing
+//    g(q,d) = min(L(q,d), L(q,d-1) + P1, L(q,d+1) + P1) and h(p,d) = C(p,d) + g(q,d),
+//      L(p,d) = min(h(p,d) - m(q), C(p,d) + P2),
+//      m(p)   = min(min_d h(p,d) - m(q), min_d C(p,d) + P2),
+//    so the group minimum of h (one redux.sync) does not wait for m(q) and overlaps the next
+//    step; min_d C comes precomputed from the cost stage.
+//  - the other axes (short lines, many of them) run one chain per small lane group with 16 or 32
+//    disparities per lane, which amortises shuffles and reductions over much more arithmetic.
+// The cost and S vectors use a blocked disparity order (VolOrder) matched to the second kernel,
+// so each lane group's loads and atomic adds touch contiguous memory in both kernels.
 #pragma once
 #include "common.cuh"
 
 namespace r2t {
+
+struct LineGeom {
+  int sx, sy, dx, dy, len;
+};
+
+// Axes: 0 rows (LR/RL), 1 columns (TB/BT), 2 diagonals x - y = const (TLBR/BRTL),
+// 3 anti-diagonals x + y = const (TRBL/BLTR). Line i of an axis, walked forward.
+__host__ __device__ inline int axis_lines(int axis, int W, int H) {
+  return axis == 0 ? H : (axis == 1 ? W : W + H - 1);
+}
+__host__ __device__ inline LineGeom axis_line(int axis, int i, int W, int H) {
+  LineGeom g;
+  if (axis == 0) {
+    g.sx = 0; g.sy = i; g.dx = 1; g.dy = 0; g.len = W;
+  } else if (axis == 1) {
+    g.sx = i; g.sy = 0; g.dx = 0; g.dy = 1; g.len = H;
+  } else if (axis == 2) {
+    const int k = i - (H - 1);
+    g.sx = k > 0 ? k : 0;
+    g.sy = k < 0 ? -k : 0;
+    g.dx = 1; g.dy = 1;
+    g.len = (W - g.sx) < (H - g.sy) ? (W - g.sx) : (H - g.sy);
+  } else {
+    g.sy = i - (W - 1) > 0 ? i - (W - 1) : 0;
+    g.sx = i - g.sy;
+    g.dx = -1; g.dy = 1;
+    g.len = (g.sx + 1) < (H - g.sy) ? (g.sx + 1) : (H - g.sy);
+  }
+  return g;
+}
+__host__ __device__ inline int long_axis(int W, int H) { return W >= H ? 0 : 1; }
+// Axes of the second kernel: the other straight axis, plus both diagonals with 8 paths.
+__host__ __device__ inline int bulk_axes(int W, int H, int num_paths, int (&axes)[3]) {
+  axes[0] = 1 - long_axis(W, H);
+  if (num_paths == 8) {
+    axes[1] = 2;
+    axes[2] = 3;
+    return 3;
+  }
+  return 1;
+}
+__host__ __device__ inline int bulk_num_lines(int W, int H, int num_paths) {
+  int axes[3];
+  const int na = bulk_axes(W, H, num_paths, axes);
+  int n = 0;
+  for (int a = 0; a < na; a++) n += axis_lines(axes[a], W, H);
+  return n;
+}
+__host__ __device__ inline LineGeom bulk_line(int li, int W, int H, int num_paths) {
+  int axes[3];
+  const int na = bulk_axes(W, H, num_paths, axes);
+  for (int a = 0; a < na; a++) {
+    const int n = axis_lines(axes[a], W, H);
+    if (li < n) return axis_line(axes[a], li, W, H);
+    li -= n;
+  }
+  LineGeom g;
+  g.sx = g.sy = g.dx = g.dy = g.len = 0;
+  return g;
+}
+
+// Kernel configurations for D disparities. Long axis: dpl in {2, 4, 8} (smallest with
+// D / dpl <= 32), lanes = next power of two >= D / dpl. Other axes: 32 disparities per lane when
+// D % 32 == 0, else 16; group width = next power of two >= D / dpl.
+__host__ __device__ inline int long_dpl_default(int D) { return D <= 64 ? 2 : (D <= 128 ? 4 : 8); }
+__host__ __device__ inline int long_lanes(int D, int dpl) {
+  const int l = pow2ceil((D + dpl - 1) / dpl);
+  return l < 8 ? 8 : l;
+}
+__host__ __device__ inline int bulk_width(int D) { return pow2ceil(D / bulk_dpl(D)); }
 
 template <int DPL>
 struct RawCost;
@@ -58,146 +138,89 @@ struct RawCost<8> {
   }
 };
 
-// Number of path lines of a pair: rows (+ columns) (+ 2 (W + H - 1) diagonals).
-__host__ __device__ inline int agg_num_lines(int W, int H, int num_paths) {
-  return num_paths == 8 ? H + W + 2 * (W + H - 1) : H + W;
+// Both halves of the result hold min(lo(v), hi(v)).
+__device__ __forceinline__ uint32_t halves_min(uint32_t v) {
+  return vmin2(v, __byte_perm(v, v, 0x1032));
 }
 
-// Line li (0 .. agg_num_lines - 1) -> entry pixel, unit step and length. The longest axis comes
-// first so its chains start earliest. Axes: 0 rows (LR/RL), 1 columns (TB/BT), 2 diagonals
-// x - y = const (TLBR/BRTL), 3 anti-diagonals x + y = const (TRBL/BLTR).
-struct LineGeom {
-  int sx, sy, dx, dy, len;
-};
-// Axis order of the line index space (the longer of rows / columns first, then the diagonals)
-// and the number of axes (2 or 4).
-__host__ __device__ inline int axis_order(int W, int H, int num_paths, int (&order)[4]) {
-  if (W >= H) {
-    order[0] = 0; order[1] = 2; order[2] = 3; order[3] = 1;
-  } else {
-    order[0] = 1; order[1] = 2; order[2] = 3; order[3] = 0;
-  }
-  if (num_paths == 4) order[1] = order[3];
-  return num_paths == 8 ? 4 : 2;
+// Minimum over a group of LPL lanes of a value whose halves are equal.
+template <int LPL>
+__device__ __forceinline__ uint32_t group_min(uint32_t v) {
+  if (LPL == 32) return __reduce_min_sync(0xffffffffu, v);
+#pragma unroll
+  for (int o = LPL / 2; o >= 1; o >>= 1) v = vmin2(v, __shfl_xor_sync(0xffffffffu, v, o, LPL));
+  return v;
 }
 
-// The axes as contiguous segments [begin, end) of the line index space, with the longest line
-// of each; returns the number of segments.
-__host__ __device__ inline int agg_segments(int W, int H, int num_paths, int* begin, int* end,
-                                            int* maxlen) {
-  const int nl[4] = {H, W, W + H - 1, W + H - 1};
-  const int mn = W < H ? W : H;
-  const int ml[4] = {W, H, mn, mn};
-  int order[4];
-  const int naxes = axis_order(W, H, num_paths, order);
-  int b = 0;
-  for (int a = 0; a < naxes; a++) {
-    begin[a] = b;
-    b += nl[order[a]];
-    end[a] = b;
-    maxlen[a] = ml[order[a]];
+// (L(d0 - 1), L(d0)) for every pair k of a lane, from the lane's registers and its neighbours.
+template <int NP, int LPL>
+__device__ __forceinline__ void neighbours(const uint32_t (&L)[NP], int lig, uint32_t (&X)[NP + 1]) {
+  uint32_t up = kSent << 16, dn = kSent;
+  if (LPL > 1) {
+    const uint32_t u = __shfl_up_sync(0xffffffffu, L[NP - 1], 1, LPL);   // hi half: d0 - 1
+    const uint32_t w = __shfl_down_sync(0xffffffffu, L[0], 1, LPL);      // lo half: last + 1
+    up = lig == 0 ? up : u;
+    dn = lig == LPL - 1 ? dn : w;
   }
-  return naxes;
-}
-
-__host__ __device__ inline LineGeom line_geom(int li, int W, int H, int num_paths) {
-  int nl[4] = {H, W, W + H - 1, W + H - 1};
-  int order[4];
-  const int naxes = axis_order(W, H, num_paths, order);
-  int axis = -1, i = li;
-  for (int a = 0; a < naxes; a++) {
-    int n = nl[order[a]];
-    if (i < n) {
-      axis = order[a];
-      break;
-    }
-    i -= n;
-  }
-  LineGeom g;
-  g.len = 0;
-  g.sx = g.sy = g.dx = g.dy = 0;
-  if (axis == 0) {
-    g.sx = 0; g.sy = i; g.dx = 1; g.dy = 0; g.len = W;
-  } else if (axis == 1) {
-    g.sx = i; g.sy = 0; g.dx = 0; g.dy = 1; g.len = H;
-  } else if (axis == 2) {
-    int k = i - (H - 1);
-    g.sx = k > 0 ? k : 0;
-    g.sy = k < 0 ? -k : 0;
-    g.dx = 1; g.dy = 1;
-    g.len = (W - g.sx) < (H - g.sy) ? (W - g.sx) : (H - g.sy);
-  } else if (axis == 3) {
-    int k = i;
-    g.sy = k - (W - 1) > 0 ? k - (W - 1) : 0;
-    g.sx = k - g.sy;
-    g.dx = -1; g.dy = 1;
-    g.len = (g.sx + 1) < (H - g.sy) ? (g.sx + 1) : (H - g.sy);
-  }
-  return g;
-}
-
-// One step of one chain: L <- L_r(p, .) from L = L_r(q, .), m = min_k L_r(q, k), c = C(p, .).
-template <int DPL, int LPL>
-__device__ __forceinline__ void chain_step(uint32_t (&L)[DPL / 2], uint32_t& m,
-                                           const uint32_t (&c)[DPL / 2], bool active, int lig,
-                                           uint32_t P1P1, uint32_t P2P2) {
-  constexpr int NP = DPL / 2;
-  uint32_t up = __shfl_up_sync(0xffffffffu, L[NP - 1], 1, LPL);  // hi half: d = first - 1
-  uint32_t dn = __shfl_down_sync(0xffffffffu, L[0], 1, LPL);     // lo half: d = last + 1
-  if (lig == 0) up = kSent << 16;
-  if (lig == LPL - 1) dn = kSent;
-  // X[k] = (L(d0 - 1), L(d0)) for pair k starting at d0; X[k + 1] = (L(d0 + 1), L(d0 + 2)).
-  uint32_t X[NP + 1];
   X[0] = __byte_perm(up, L[0], 0x5432);
 #pragma unroll
   for (int k = 1; k < NP; k++) X[k] = __byte_perm(L[k - 1], L[k], 0x5432);
   X[NP] = __byte_perm(L[NP - 1], dn, 0x5432);
-  const uint32_t mm = m * 0x10001u;
-  const uint32_t mP2 = mm + P2P2;
-  uint32_t lmin = 0xFFFFFFFFu;
+}
+
+// Adds 4 packed u16 sums (2 registers) into S at element e (uint16 or, when wide, uint32).
+template <bool WIDE>
+__device__ __forceinline__ void add4(void* agg, int64_t e, uint32_t a, uint32_t b) {
+  if (!WIDE) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(reinterpret_cast<uint16_t*>(agg) + e),
+              (unsigned long long)a | ((unsigned long long)b << 32));
+  } else {
+    unsigned long long* p =
+        reinterpret_cast<unsigned long long*>(reinterpret_cast<uint32_t*>(agg) + e);
+    atomicAdd(p, (unsigned long long)(a & 0xFFFFu) | ((unsigned long long)(a >> 16) << 32));
+    atomicAdd(p + 1, (unsigned long long)(b & 0xFFFFu) | ((unsigned long long)(b >> 16) << 32));
+  }
+}
+template <bool WIDE>
+__device__ __forceinline__ void add2(void* agg, int64_t e, uint32_t a) {
+  if (!WIDE)
+    atomicAdd(reinterpret_cast<unsigned int*>(reinterpret_cast<uint16_t*>(agg) + e), a);
+  else
+    atomicAdd(reinterpret_cast<unsigned long long*>(reinterpret_cast<uint32_t*>(agg) + e),
+              (unsigned long long)(a & 0xFFFFu) | ((unsigned long long)(a >> 16) << 32));
+}
+
+// ------------------------------------------------------------------------------- long axis
+// One pipelined step. In: L = L(q, .), mm = m(q) in both halves, c = C(p, .),
+// cp2 = C(p, .) + P2, cminp2 = (min_d C(p, d) + P2) in both halves.
+template <int DPL, int LPL>
+__device__ __forceinline__ void long_step(uint32_t (&L)[DPL / 2], uint32_t& mm,
+                                          const uint32_t (&c)[DPL / 2], uint32_t cminp2,
+                                          bool active, int lig, uint32_t P1P1, uint32_t P2P2) {
+  constexpr int NP = DPL / 2;
+  uint32_t X[NP + 1];
+  neighbours<NP, LPL>(L, lig, X);
+  uint32_t h[NP];
+  uint32_t hmin = 0xFFFFFFFFu;
 #pragma unroll
   for (int k = 0; k < NP; k++) {
-    uint32_t t = vmin2(X[k], X[k + 1]) + P1P1;   // min(L(d-1), L(d+1)) + P1, no lane carry
-    uint32_t u = vmin2(vmin2(L[k], t), mP2);     // >= m in both halves
-    uint32_t ln = u + c[k] - mm;                 // each half in [0, 255 + P2]
-    ln = active ? ln : (kSent * 0x10001u);
-    L[k] = ln;
-    lmin = vmin2(lmin, ln);
+    const uint32_t g = vmin2(L[k], vmin2(X[k], X[k + 1]) + P1P1);  // <= L(q,d), no lane carry
+    h[k] = g + c[k];
+    hmin = vmin2(hmin, h[k]);
   }
-  uint32_t lm = min(lmin & 0xFFFFu, lmin >> 16);
-  if (LPL == 32) {
-    lm = __reduce_min_sync(0xffffffffu, lm);
-  } else {
+  hmin = active ? halves_min(hmin) : 0xFFFFFFFFu;
+  const uint32_t aa = group_min<LPL>(hmin);  // min_d h(p, d), both halves
 #pragma unroll
-    for (int o = LPL / 2; o >= 1; o >>= 1) lm = min(lm, __shfl_xor_sync(0xffffffffu, lm, o, LPL));
+  for (int k = 0; k < NP; k++) {
+    const uint32_t ln = vmin2(h[k] - mm, c[k] + P2P2);  // h >= m(q) in both halves
+    L[k] = active ? ln : kSent * 0x10001u;
   }
-  m = lm;
+  mm = vmin2(aa - mm, cminp2);
 }
 
-template <int DPL, bool WIDE>
-__device__ __forceinline__ void add_to_sum(void* aggp, const uint32_t (&L)[DPL / 2]) {
-  constexpr int NP = DPL / 2;
-  if (!WIDE) {
-    if (DPL == 2) {
-      atomicAdd(reinterpret_cast<unsigned int*>(aggp), L[0]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < NP; k += 2)
-        atomicAdd(reinterpret_cast<unsigned long long*>(aggp) + k / 2,
-                  (unsigned long long)L[k] | ((unsigned long long)L[k + 1] << 32));
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < NP; k++)
-      atomicAdd(reinterpret_cast<unsigned long long*>(aggp) + k,
-                (unsigned long long)(L[k] & 0xFFFFu) | ((unsigned long long)(L[k] >> 16) << 32));
-  }
-}
-
-// Aggregates the lines [line0, min(line0 + 32 / LPL, line_end)) of one pair with one warp: lane
-// group g walks line line0 + g in both directions and adds both chains into S.
+// Lines [line0, min(line0 + 32 / LPL, line_end)) of the long axis, both directions each.
 template <int DPL, int LPL, bool WIDE>
-__device__ __forceinline__ void agg_warp_lines(const Problem& pb, const Method& mt, int line0,
+__device__ __forceinline__ void agg_long_lines(const Problem& pb, const Method& mt, int line0,
                                                int line_end) {
   typedef RawCost<DPL> RC;
   typedef typename RC::T Raw;
@@ -205,25 +228,24 @@ __device__ __forceinline__ void agg_warp_lines(const Problem& pb, const Method& 
   constexpr int U = 4;  // steps loaded ahead
   const int lane = threadIdx.x & 31;
   const int lig = lane % LPL;
-  const int li = line0 + lane / LPL;
   const int W = pb.W, H = pb.H, D = pb.D;
-  const int nl = min(agg_num_lines(W, H, mt.num_paths), line_end);
-  LineGeom g;
-  if (li < nl) {
-    g = line_geom(li, W, H, mt.num_paths);
-  } else {
-    g.sx = g.sy = g.dx = g.dy = 0;
-    g.len = 0;
-  }
-  const int maxlen = __reduce_max_sync(0xffffffffu, (unsigned)g.len);
-  if (maxlen == 0) return;
-  const bool active = lig * DPL < D;
-  const int64_t stride = ((int64_t)g.dy * W + g.dx) * D;  // elements per step
-  const int64_t off_f = ((int64_t)g.sy * W + g.sx) * D + lig * DPL;
-  const int64_t off_b = off_f + (int64_t)(g.len > 0 ? g.len - 1 : 0) * stride;
-  const uint8_t* cf = pb.cost + off_f;
-  const uint8_t* cb = pb.cost + off_b;
+  const int la = long_axis(W, H);
+  const int nl = min(axis_lines(la, W, H), line_end);
+  const int li = line0 + lane / LPL;
+  const bool valid = li < nl;
+  const LineGeom g = axis_line(la, valid ? li : 0, W, H);  // every line of the axis has len
+  const int len = g.len;
+  const bool active = valid && lig * DPL < D;
+  const int d0 = active ? lig * DPL : 0;
+  const int coff = vol_pos(d0, pb.ord, 16);      // DPL consecutive bytes
+  const int soff0 = vol_pos(d0, pb.ord, 4);      // first 4 (or 2) sums
+  const int soff1 = DPL == 8 ? vol_pos(d0 + 4, pb.ord, 4) : 0;
+  const int64_t pstride = (int64_t)g.dy * W + g.dx;  // pixels per step
+  const int64_t pf = (int64_t)g.sy * W + g.sx;
+  const int64_t pbk = pf + (int64_t)(len - 1) * pstride;
   const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
+  const uint8_t* cost = pb.cost;
+  const uint8_t* cmin = pb.cmin;
 
   uint32_t Lf[NP], Lb[NP];
 #pragma unroll
@@ -231,39 +253,50 @@ __device__ __forceinline__ void agg_warp_lines(const Problem& pb, const Method& 
   uint32_t mf = 0, mb = 0;
 
   Raw rf[U], rb[U];
+  uint32_t qf[U], qb[U];  // min_d C of the step's pixels
 #pragma unroll
   for (int u = 0; u < U; u++) {
-    const bool live = active && u < g.len;
-    rf[u] = live ? RC::load(cf + (int64_t)u * stride) : Raw();
-    rb[u] = live ? RC::load(cb - (int64_t)u * stride) : Raw();
+    const int64_t xf = pf + u * pstride, xb = pbk - u * pstride;
+    const bool ok = valid && u < len;
+    rf[u] = (active && ok) ? RC::load(cost + xf * D + coff) : Raw();
+    rb[u] = (active && ok) ? RC::load(cost + xb * D + coff) : Raw();
+    qf[u] = ok ? (uint32_t)__ldg(cmin + xf) : 0u;
+    qb[u] = ok ? (uint32_t)__ldg(cmin + xb) : 0u;
   }
-  for (int t0 = 0; t0 < maxlen; t0 += U) {
+  for (int t0 = 0; t0 < len; t0 += U) {
     Raw nf[U], nb[U];
+    uint32_t nqf[U], nqb[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int t = t0 + U + u;
-      const bool live = active && t < g.len;
-      nf[u] = live ? RC::load(cf + (int64_t)t * stride) : Raw();
-      nb[u] = live ? RC::load(cb - (int64_t)t * stride) : Raw();
+      const int64_t xf = pf + t * pstride, xb = pbk - t * pstride;
+      const bool ok = valid && t < len;
+      nf[u] = (active && ok) ? RC::load(cost + xf * D + coff) : Raw();
+      nb[u] = (active && ok) ? RC::load(cost + xb * D + coff) : Raw();
+      nqf[u] = ok ? (uint32_t)__ldg(cmin + xf) : 0u;
+      nqb[u] = ok ? (uint32_t)__ldg(cmin + xb) : 0u;
     }
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int t = t0 + u;
-      if (t < maxlen) {
+      if (t < len) {
         uint32_t c[NP];
         RC::unpack(rf[u], c);
-        chain_step<DPL, LPL>(Lf, mf, c, active, lig, P1P1, P2P2);
+        long_step<DPL, LPL>(Lf, mf, c, (qf[u] * 0x10001u) + P2P2, active, lig, P1P1, P2P2);
         RC::unpack(rb[u], c);
-        chain_step<DPL, LPL>(Lb, mb, c, active, lig, P1P1, P2P2);
-        if (active && t < g.len) {
-          const int64_t ef = off_f + (int64_t)t * stride;
-          const int64_t eb = off_b - (int64_t)t * stride;
-          if (WIDE) {
-            add_to_sum<DPL, true>(reinterpret_cast<uint32_t*>(pb.agg) + ef, Lf);
-            add_to_sum<DPL, true>(reinterpret_cast<uint32_t*>(pb.agg) + eb, Lb);
+        long_step<DPL, LPL>(Lb, mb, c, (qb[u] * 0x10001u) + P2P2, active, lig, P1P1, P2P2);
+        if (active && valid) {
+          const int64_t ef = (pf + t * pstride) * D, eb = (pbk - t * pstride) * D;
+          if (DPL == 2) {
+            add2<WIDE>(pb.agg, ef + soff0, Lf[0]);
+            add2<WIDE>(pb.agg, eb + soff0, Lb[0]);
           } else {
-            add_to_sum<DPL, false>(reinterpret_cast<uint16_t*>(pb.agg) + ef, Lf);
-            add_to_sum<DPL, false>(reinterpret_cast<uint16_t*>(pb.agg) + eb, Lb);
+            add4<WIDE>(pb.agg, ef + soff0, Lf[0], Lf[1]);
+            add4<WIDE>(pb.agg, eb + soff0, Lb[0], Lb[1]);
+            if (DPL == 8) {
+              add4<WIDE>(pb.agg, ef + soff1, Lf[NP - 2], Lf[NP - 1]);
+              add4<WIDE>(pb.agg, eb + soff1, Lb[NP - 2], Lb[NP - 1]);
+            }
           }
         }
       }
@@ -272,7 +305,104 @@ __device__ __forceinline__ void agg_warp_lines(const Problem& pb, const Method& 
     for (int u = 0; u < U; u++) {
       rf[u] = nf[u];
       rb[u] = nb[u];
+      qf[u] = nqf[u];
+      qb[u] = nqb[u];
     }
+  }
+}
+
+// ------------------------------------------------------------------------------- other axes
+// Chains [chain0, min(chain0 + 32 / WD, chain_end)): chain c walks line c / 2 of the other axes,
+// forward when c is even, backward when odd. WD lanes per chain, DPL disparities per lane.
+template <int DPL, int WD, bool WIDE>
+__device__ __forceinline__ void agg_bulk_chains(const Problem& pb, const Method& mt, int chain0,
+                                                int chain_end) {
+  constexpr int NP = DPL / 2;
+  constexpr int NV = DPL / 16;  // 16-byte cost vectors per lane
+  const int lane = threadIdx.x & 31;
+  const int lig = lane % WD;
+  const int W = pb.W, H = pb.H, D = pb.D;
+  const int nc = min(2 * bulk_num_lines(W, H, mt.num_paths), chain_end);
+  const int ci = chain0 + lane / WD;
+  const bool valid = ci < nc;
+  LineGeom g = bulk_line(valid ? ci >> 1 : 0, W, H, mt.num_paths);
+  if (!valid) g.len = 0;
+  const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)g.len);
+  if (maxlen == 0) return;
+  const bool back = (ci & 1) != 0;
+  const bool active = valid && lig * DPL < D;
+  int64_t pstride = (int64_t)g.dy * W + g.dx;
+  int64_t px = (int64_t)g.sy * W + g.sx;
+  if (back) {
+    px += (int64_t)(g.len - 1) * pstride;
+    pstride = -pstride;
+  }
+  // lane member lig owns disparities [d0, d0 + DPL): cost chunk h at (h * lpl + lig) * 16,
+  // sum chunk k at (k * lpl + lig) * 4 (VolOrder blocked, lpl = D / DPL)
+  const int lpl = D / DPL;
+  const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
+
+  uint32_t L[NP];
+#pragma unroll
+  for (int k = 0; k < NP; k++) L[k] = active ? 0u : kSent * 0x10001u;
+  uint32_t mm = 0;
+
+  uint4 ra[NV], rb[NV];  // costs of the next two steps
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    ra[v] = (active && 0 < g.len)
+                ? __ldg(reinterpret_cast<const uint4*>(pb.cost + px * D + (v * lpl + lig) * 16))
+                : make_uint4(0, 0, 0, 0);
+    rb[v] = (active && 1 < g.len) ? __ldg(reinterpret_cast<const uint4*>(
+                                        pb.cost + (px + pstride) * D + (v * lpl + lig) * 16))
+                                  : make_uint4(0, 0, 0, 0);
+  }
+  for (int t = 0; t < maxlen; t++) {
+    uint32_t c[NP];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      const uint4 r = (t & 1) ? rb[v] : ra[v];
+      c[8 * v + 0] = __byte_perm(r.x, 0u, 0x4140);
+      c[8 * v + 1] = __byte_perm(r.x, 0u, 0x4342);
+      c[8 * v + 2] = __byte_perm(r.y, 0u, 0x4140);
+      c[8 * v + 3] = __byte_perm(r.y, 0u, 0x4342);
+      c[8 * v + 4] = __byte_perm(r.z, 0u, 0x4140);
+      c[8 * v + 5] = __byte_perm(r.z, 0u, 0x4342);
+      c[8 * v + 6] = __byte_perm(r.w, 0u, 0x4140);
+      c[8 * v + 7] = __byte_perm(r.w, 0u, 0x4342);
+    }
+    {  // load step t + 2 into the buffer just consumed
+      const bool ok = active && t + 2 < g.len;
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        const uint4 n = ok ? __ldg(reinterpret_cast<const uint4*>(
+                                 pb.cost + (px + 2 * pstride) * D + (v * lpl + lig) * 16))
+                           : make_uint4(0, 0, 0, 0);
+        if (t & 1)
+          rb[v] = n;
+        else
+          ra[v] = n;
+      }
+    }
+    uint32_t X[NP + 1];
+    neighbours<NP, WD>(L, lig, X);
+    const uint32_t mP2 = mm + P2P2;
+    uint32_t lmin = 0xFFFFFFFFu;
+#pragma unroll
+    for (int k = 0; k < NP; k++) {
+      const uint32_t tt = vmin2(X[k], X[k + 1]) + P1P1;
+      const uint32_t u = vmin2(vmin2(L[k], tt), mP2);  // >= m(q) in both halves
+      const uint32_t ln = u + c[k] - mm;                // each half in [0, 255 + P2]
+      L[k] = active ? ln : kSent * 0x10001u;
+      lmin = vmin2(lmin, L[k]);
+    }
+    mm = group_min<WD>(halves_min(lmin));
+    if (active && t < g.len) {
+      const int64_t e = px * D;
+#pragma unroll
+      for (int k = 0; k < NP / 2; k++) add4<WIDE>(pb.agg, e + (k * lpl + lig) * 4, L[2 * k], L[2 * k + 1]);
+    }
+    px += pstride;
   }
 }
 

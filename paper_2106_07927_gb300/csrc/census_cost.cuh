@@ -76,11 +76,13 @@ __device__ __forceinline__ void census_tile_dispatch(const Problem& pb, const Me
 struct CostSmem {
   uint64_t r[kCostTX + 256];  // CT_R(x0 - D + 1 .. x0 + 31)
   uint64_t l[kCostTX];
+  unsigned int cmin[kCostTX];  // min_d C of each pixel of the tile
 };
 
 // One row segment of 32 pixels, all disparities, written as 4-byte words (coalesced along d).
-// The same tile of the aggregated volume is cleared here (16-byte stores), so the aggregation
-// can add into it without a separate memset pass; agg_bytes_per_de is 2, or 4 when wide.
+// The same tile of the aggregated volume is cleared here (16-byte stores) and the tile's
+// right-disparity keys are set to their maximum, so the later stages can add / atomicMin into
+// them without separate memset passes; agg_bytes_per_de is 2, or 4 when wide.
 __device__ __forceinline__ void cost_tile(const Problem& pb, int item, CostSmem& sm,
                                           int agg_bytes_per_de) {
   const int ntx = (pb.W + kCostTX - 1) / kCostTX;
@@ -93,8 +95,10 @@ __device__ __forceinline__ void cost_tile(const Problem& pb, int item, CostSmem&
     int xr = x0 - (D - 1) + i;
     sm.r[i] = (xr >= 0 && xr < pb.W) ? rowr[xr] : 0ull;
   }
-  for (int i = threadIdx.x; i < kCostTX; i += blockDim.x)
+  for (int i = threadIdx.x; i < kCostTX; i += blockDim.x) {
     sm.l[i] = (x0 + i < pb.W) ? rowl[x0 + i] : 0ull;
+    sm.cmin[i] = 0xFFu;
+  }
   __syncthreads();
   const int nq = D / 4;
   for (int it = threadIdx.x; it < kCostTX * nq; it += blockDim.x) {
@@ -102,22 +106,31 @@ __device__ __forceinline__ void cost_tile(const Problem& pb, int item, CostSmem&
     const int x = x0 + px;
     if (x >= pb.W) continue;
     const uint64_t cl = sm.l[px];
-    uint32_t word = 0;
+    uint32_t word = 0, mn = 0xFFu;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       const int d = 4 * q + j;
       uint32_t v = kCostOutside;
       if (x >= d) v = (uint32_t)__popcll(cl ^ sm.r[px + D - 1 - d]);
       word |= v << (8 * j);
+      mn = min(mn, v);
     }
-    *reinterpret_cast<uint32_t*>(pb.cost + ((int64_t)y * pb.W + x) * D + 4 * q) = word;
+    // 4 consecutive disparities stay consecutive in the volume's order (chunks of 16)
+    *reinterpret_cast<uint32_t*>(pb.cost + ((int64_t)y * pb.W + x) * D + vol_pos(4 * q, pb.ord, 16)) =
+        word;
+    atomicMin(&sm.cmin[px], mn);
   }
+  __syncthreads();
   {
     const int npx = min(kCostTX, pb.W - x0);
+    for (int i = threadIdx.x; i < npx; i += blockDim.x)
+      pb.cmin[(int64_t)y * pb.W + x0 + i] = (uint8_t)sm.cmin[i];
     const int64_t bytes = (int64_t)npx * D * agg_bytes_per_de;  // multiple of 32
     uint4* z = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(pb.agg) +
                                         ((int64_t)y * pb.W + x0) * D * agg_bytes_per_de);
     for (int64_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) z[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < npx; i += blockDim.x)
+      pb.kr[(int64_t)y * pb.W + x0 + i] = 0xFFFFFFFFu;
   }
   __syncthreads();
 }

@@ -12,7 +12,43 @@ constexpr uint8_t kCostOutside = 255;  // cost where the matching pixel x - d li
 // <= 16639 and P1, P2 <= 16384, and v + P1 still fits 16 bits.
 constexpr uint32_t kSent = 0xBFFFu;
 
-// Everything a kernel needs to know about one stereo pair. Volumes are [y][x][d], d contiguous.
+// Order of the D disparities inside one pixel's cost (uint8) and aggregated (uint16 / uint32)
+// vectors. blocked == 0: disparity d sits at position d. blocked == 1: the disparities are owned
+// by the lpl members of a lane group, dpl consecutive ones each, and are cut into chunks of
+// `chunk` disparities; chunk c of member l sits at chunk slot c * lpl + l, so the members'
+// accesses to chunk c are contiguous in memory (chunk = 16 for the cost, 4 for the sums).
+struct VolOrder {
+  int blocked, dpl, lpl;
+};
+__host__ __device__ inline int vol_pos(int d, VolOrder o, int chunk) {
+  if (!o.blocked) return d;
+  const int l = d / o.dpl, w = d - l * o.dpl;
+  return ((w / chunk) * o.lpl + l) * chunk + (w % chunk);
+}
+// Inverse of vol_pos: the disparity stored at position p.
+__host__ __device__ inline int vol_index(int p, VolOrder o, int chunk) {
+  if (!o.blocked) return p;
+  const int c = p / chunk, k = c / o.lpl, l = c - k * o.lpl;
+  return l * o.dpl + k * chunk + (p - c * chunk);
+}
+
+__host__ __device__ inline int pow2ceil(int v) {
+  int p = 1;
+  while (p < v) p *= 2;
+  return p;
+}
+// Disparities per lane of the short-line aggregation kernel, which fixes the volumes' order.
+__host__ __device__ inline int bulk_dpl(int D) { return D % 32 == 0 ? 32 : 16; }
+__host__ __device__ inline VolOrder vol_order_for(int D) {
+  VolOrder o;
+  o.blocked = 1;
+  o.dpl = bulk_dpl(D);
+  o.lpl = D / o.dpl;
+  return o;
+}
+
+// Everything a kernel needs to know about one stereo pair. Volumes are [y][x][d] with the D
+// disparities of a pixel contiguous, in the order `ord`.
 struct Problem {
   const uint8_t* left;
   const uint8_t* right;
@@ -20,13 +56,15 @@ struct Problem {
   uint16_t* disp;     // final map
   int64_t out_pitch;  // bytes
   int W, H, D;
+  VolOrder ord;       // disparity order inside the cost and aggregated vectors
   uint64_t* ctl;      // census descriptors of the left / right image, [H][W]
   uint64_t* ctr;
   uint8_t* cost;      // [H][W][D]
+  uint8_t* cmin;      // [H][W] min_d C(x, y, d)
   void* agg;          // [H][W][D], uint16 (or uint32 when wide)
   uint16_t* dl;       // [H][W] winner-takes-all map
   uint16_t* dr;       // [H][W] approximate right map
-  uint16_t* dlr;      // [H][W] map after the left-right check (median input)
+  uint32_t* kr;       // [H][W] right-disparity keys S << 8 | d, reduced with atomicMin
   uint8_t* mask;      // [H][W] 1 = kept by the left-right check
 };
 

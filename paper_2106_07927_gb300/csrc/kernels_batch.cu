@@ -1,14 +1,16 @@
-// Batch engine: every stage of the pipeline runs as one persistent kernel over all pairs of the
+// Batch engine: every stage of the pipeline runs as a persistent kernel over all pairs of the
 // batch. A block (or, in the aggregation, a warp) claims its next work item from a device queue
-// with one atomic increment and maps it to (pair, item of that pair) through per-stage prefix
-// tables; no block ever waits for another, so the queue needs no device-side spin. Stage order is
-// kept by the launch order on one stream. The descriptor upload, the queue reset and the stage
-// kernels are recorded once into a CUDA graph and replayed while the capacities last.
+// with one atomic increment and maps it to (pair, item of that pair) through prefix tables; no
+// block ever waits for another, so the queues need no device-side spin. Stage order is kept by
+// the launch order on one stream; the two aggregation kernels (long-axis lines and the other
+// lines) run concurrently on a forked stream inside the graph. The descriptor upload, the queue
+// reset and the stage kernels are recorded once into a CUDA graph and replayed while the
+// capacities last.
 //
-// Aggregation work is described by segments: one per axis of every pair (rows, columns,
-// diagonals, anti-diagonals), a contiguous range of line indices. Segments are ordered by their
-// longest line across the whole batch (longest first), so the sequential chains that bound the
-// batch's duration start earliest; a warp claims one group of 32 / LPL lines of a segment.
+// Aggregation work is described by segments, two per pair: its long-axis lines (one warp item
+// per group of lines) and its other lines (one item per group of chains). Each queue is ordered
+// by the longest line of its segments across the whole batch (longest first), so the sequential
+// chains that bound the batch's duration start earliest.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -19,25 +21,28 @@
 #include "aggregate.cuh"
 #include "batch.h"
 #include "census_cost.cuh"
+#include "launch.h"
 #include "post.cuh"
 
 namespace r2t {
 
-enum { kStCensus = 0, kStCost = 1, kStAgg = 2, kStWta = 3, kStMedian = 4, kNumStages = 5 };
+enum {
+  kStCensus = 0, kStCost = 1, kStLong = 2, kStBulk = 3, kStWta = 4, kStMedian = 5,
+  kNumCounters = 6
+};
 
-// Header of the device descriptor block. It is followed by Problem[cap_pairs],
-// int prefix[4][cap_pairs + 1] (census, cost, wta, median items), AggSeg[4 cap_pairs] and
-// int seg_prefix[4 cap_pairs + 1] (aggregation items).
+// Header of the device descriptor block. It is followed by Problem[cap], int prefix[4][cap + 1]
+// (census, cost, wta, median items), then for the long and the bulk queue each AggSeg[cap] and
+// int seg_prefix[cap + 1].
 struct BatchHeader {
   int n;
-  int nseg;
-  int total[kNumStages];
+  int total[kNumCounters];
   int pad;
-  signed char dpl_by_d16[17];  // aggregation disparities per lane, indexed by D / 16
+  signed char dpl_by_d16[17];  // long-axis disparities per lane, indexed by D / 16
 };
 
 struct AggSeg {
-  int pair, begin, end, group;  // lines [begin, end) of one pair, `group` lines per warp item
+  int pair, begin, end, group;  // lines / chains [begin, end) of one pair, `group` per warp item
 };
 
 __device__ __forceinline__ int find_slot(const int* prefix, int n, int item) {
@@ -58,6 +63,12 @@ __device__ __forceinline__ int claim_block(unsigned* counter, int* s_item) {
   const int item = *s_item;
   __syncthreads();
   return item;
+}
+
+__device__ __forceinline__ int claim_warp(unsigned* counter) {
+  int item = 0;
+  if ((threadIdx.x & 31) == 0) item = (int)atomicAdd(counter, 1u);
+  return __shfl_sync(0xffffffffu, item, 0);
 }
 
 __global__ void __launch_bounds__(256) batch_census_kernel(const BatchHeader* hd,
@@ -91,46 +102,72 @@ __global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
 }
 
 template <bool WIDE>
-__device__ __forceinline__ void agg_dispatch(const Problem& pb, const Method& mt, int line0,
-                                             int line_end, int dpl) {
-  const int lpl = agg_lanes_for(pb.D, dpl);
-  switch (dpl * 100 + lpl) {
-    case 208: agg_warp_lines<2, 8, WIDE>(pb, mt, line0, line_end); break;
-    case 216: agg_warp_lines<2, 16, WIDE>(pb, mt, line0, line_end); break;
-    case 232: agg_warp_lines<2, 32, WIDE>(pb, mt, line0, line_end); break;
-    case 408: agg_warp_lines<4, 8, WIDE>(pb, mt, line0, line_end); break;
-    case 416: agg_warp_lines<4, 16, WIDE>(pb, mt, line0, line_end); break;
-    case 432: agg_warp_lines<4, 32, WIDE>(pb, mt, line0, line_end); break;
-    case 808: agg_warp_lines<8, 8, WIDE>(pb, mt, line0, line_end); break;
-    case 816: agg_warp_lines<8, 16, WIDE>(pb, mt, line0, line_end); break;
-    case 832: agg_warp_lines<8, 32, WIDE>(pb, mt, line0, line_end); break;
+__device__ __forceinline__ void long_dispatch(const Problem& pb, const Method& mt, int line0,
+                                              int line_end, int dpl) {
+  switch (dpl * 100 + long_lanes(pb.D, dpl)) {
+    case 208: agg_long_lines<2, 8, WIDE>(pb, mt, line0, line_end); break;
+    case 216: agg_long_lines<2, 16, WIDE>(pb, mt, line0, line_end); break;
+    case 232: agg_long_lines<2, 32, WIDE>(pb, mt, line0, line_end); break;
+    case 408: agg_long_lines<4, 8, WIDE>(pb, mt, line0, line_end); break;
+    case 416: agg_long_lines<4, 16, WIDE>(pb, mt, line0, line_end); break;
+    case 432: agg_long_lines<4, 32, WIDE>(pb, mt, line0, line_end); break;
+    case 808: agg_long_lines<8, 8, WIDE>(pb, mt, line0, line_end); break;
+    case 816: agg_long_lines<8, 16, WIDE>(pb, mt, line0, line_end); break;
+    case 832: agg_long_lines<8, 32, WIDE>(pb, mt, line0, line_end); break;
     default: break;
   }
 }
 
 template <bool WIDE>
-__global__ void __launch_bounds__(256) batch_agg_kernel(const BatchHeader* hd, const Problem* probs,
-                                                        const AggSeg* segs, const int* seg_prefix,
-                                                        Method mt, unsigned* counters) {
-  const int total = hd->total[kStAgg], nseg = hd->nseg;
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void bulk_dispatch(const Problem& pb, const Method& mt, int chain0,
+                                              int chain_end) {
+  switch (bulk_dpl(pb.D) * 100 + bulk_width(pb.D)) {
+    case 1601: agg_bulk_chains<16, 1, WIDE>(pb, mt, chain0, chain_end); break;
+    case 1604: agg_bulk_chains<16, 4, WIDE>(pb, mt, chain0, chain_end); break;
+    case 1608: agg_bulk_chains<16, 8, WIDE>(pb, mt, chain0, chain_end); break;
+    case 1616: agg_bulk_chains<16, 16, WIDE>(pb, mt, chain0, chain_end); break;
+    case 3201: agg_bulk_chains<32, 1, WIDE>(pb, mt, chain0, chain_end); break;
+    case 3202: agg_bulk_chains<32, 2, WIDE>(pb, mt, chain0, chain_end); break;
+    case 3204: agg_bulk_chains<32, 4, WIDE>(pb, mt, chain0, chain_end); break;
+    case 3208: agg_bulk_chains<32, 8, WIDE>(pb, mt, chain0, chain_end); break;
+    default: break;
+  }
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(256) batch_long_kernel(const BatchHeader* hd, const Problem* probs,
+                                                         const AggSeg* segs, const int* seg_prefix,
+                                                         int nseg, Method mt, unsigned* counters) {
+  const int total = hd->total[kStLong];
   for (;;) {
-    int item = 0;
-    if (lane == 0) item = (int)atomicAdd(&counters[kStAgg], 1u);
-    item = __shfl_sync(0xffffffffu, item, 0);
+    const int item = claim_warp(&counters[kStLong]);
     if (item >= total) break;
     const int si = find_slot(seg_prefix, nseg, item);
     const AggSeg sg = segs[si];
     const Problem pb = probs[sg.pair];
-    const int line0 = sg.begin + (item - seg_prefix[si]) * sg.group;
-    agg_dispatch<WIDE>(pb, mt, line0, sg.end, hd->dpl_by_d16[pb.D / 16]);
+    long_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, sg.end,
+                        hd->dpl_by_d16[pb.D / 16]);
+  }
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(256) batch_bulk_kernel(const BatchHeader* hd, const Problem* probs,
+                                                         const AggSeg* segs, const int* seg_prefix,
+                                                         int nseg, Method mt, unsigned* counters) {
+  const int total = hd->total[kStBulk];
+  for (;;) {
+    const int item = claim_warp(&counters[kStBulk]);
+    if (item >= total) break;
+    const int si = find_slot(seg_prefix, nseg, item);
+    const AggSeg sg = segs[si];
+    const Problem pb = probs[sg.pair];
+    bulk_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, sg.end);
   }
 }
 
 template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, const Problem* probs,
-                                                        const int* prefix, Method mt,
-                                                        unsigned* counters) {
+                                                        const int* prefix, unsigned* counters) {
   extern __shared__ __align__(16) uint16_t wsm[];
   __shared__ int s_item;
   const int total = hd->total[kStWta], n = hd->n;
@@ -139,17 +176,13 @@ __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, c
     if (item >= total) break;
     const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
-    const int y = item - prefix[p];
-    uint16_t* out_row = (mt.flags & 2) ? pb.dlr + (int64_t)y * pb.W
-                                       : reinterpret_cast<uint16_t*>(
-                                             reinterpret_cast<uint8_t*>(pb.disp) + y * pb.out_pitch);
-    wta_lr_row<WIDE>(pb, mt, y, wta_default_chunk(pb.D), wsm, out_row);
+    wta_dr_tile<WIDE>(pb, item - prefix[p], wsm, wta_tile_px(pb.D));
   }
 }
 
 __global__ void __launch_bounds__(256) batch_median_kernel(const BatchHeader* hd,
                                                            const Problem* probs, const int* prefix,
-                                                           unsigned* counters) {
+                                                           Method mt, unsigned* counters) {
   __shared__ MedianSmem sm;
   __shared__ int s_item;
   const int total = hd->total[kStMedian], n = hd->n;
@@ -158,11 +191,9 @@ __global__ void __launch_bounds__(256) batch_median_kernel(const BatchHeader* hd
     if (item >= total) break;
     const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
-    median_tile(pb.dlr, pb.W, pb.W, pb.H, pb.disp, pb.out_pitch, item - prefix[p], sm);
+    lr_median_tile(pb, mt, item - prefix[p], sm);
   }
 }
-
-static int default_dpl(int D) { return D <= 64 ? 2 : (D <= 128 ? 4 : 8); }
 
 struct BatchEngine {
   char* scratch = nullptr;
@@ -173,6 +204,7 @@ struct BatchEngine {
   int cap_pairs = 0;
   unsigned* d_counters = nullptr;
   cudaStream_t cap_stream = nullptr;
+  Fork fork = {nullptr, nullptr, nullptr};
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t copied = nullptr;  // recorded in the graph after the descriptor upload
   bool copy_pending = false;
@@ -185,11 +217,13 @@ struct BatchEngine {
 
 static size_t probs_offset() { return (sizeof(BatchHeader) + 255) / 256 * 256; }
 static size_t prefix_offset(int cap) { return probs_offset() + (size_t)cap * sizeof(Problem); }
-static size_t segs_offset(int cap) {
-  return (prefix_offset(cap) + 4 * sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
+static size_t segs_offset(int cap, int q) {  // q = 0 long, 1 bulk
+  const size_t base = (prefix_offset(cap) + 4 * sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
+  const size_t per = ((size_t)cap * sizeof(AggSeg) + sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
+  return base + q * per;
 }
-static size_t seg_prefix_offset(int cap) { return segs_offset(cap) + 4 * (size_t)cap * sizeof(AggSeg); }
-static size_t desc_size(int cap) { return seg_prefix_offset(cap) + sizeof(int) * (4 * (size_t)cap + 1); }
+static size_t seg_prefix_offset(int cap, int q) { return segs_offset(cap, q) + (size_t)cap * sizeof(AggSeg); }
+static size_t desc_size(int cap) { return segs_offset(cap, 2); }
 
 size_t batch_fixed_bytes(int n) { return desc_size(n) + 4096; }
 
@@ -227,17 +261,19 @@ static int grow_desc(BatchEngine* e, int n) {
 int batch_reserve(BatchEngine** pe, size_t scratch_bytes, int n) {
   if (!*pe) {
     BatchEngine* e = new BatchEngine();
-    for (int i = 0; i < 17; i++) e->dpl_by_d16[i] = (signed char)default_dpl(i * 16);
+    for (int i = 0; i < 17; i++) e->dpl_by_d16[i] = (signed char)long_dpl_default(i * 16);
     e->err[0] = 0;
     memset(&e->graph_method, 0, sizeof(Method));
     *pe = e;
     cudaError_t c = cudaMalloc(&e->d_counters, 64);
     if (c == cudaSuccess) c = cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking);
     if (c == cudaSuccess) c = cudaEventCreateWithFlags(&e->copied, cudaEventDisableTiming);
+    if (c == cudaSuccess) c = fork_create(&e->fork);
     if (c != cudaSuccess) return set_err(e, c, "batch engine setup");
   }
   BatchEngine* e = *pe;
-  if (!e->d_counters) return set_err(e, cudaErrorInitializationError, "batch engine setup");
+  if (!e->d_counters || !e->fork.aux)
+    return set_err(e, cudaErrorInitializationError, "batch engine setup");
   if (scratch_bytes > e->scratch_cap) {
     // the previous batch may still run on its stream: wait before freeing its scratch
     cudaDeviceSynchronize();
@@ -255,7 +291,8 @@ char* batch_scratch(BatchEngine* e) { return e ? e->scratch : nullptr; }
 const char* batch_error(BatchEngine* e) { return e ? e->err : "no batch engine"; }
 
 void batch_set_dpl(BatchEngine* e, int D, int dpl) {
-  if (e && D >= 0 && D <= 256) e->dpl_by_d16[D / 16] = (signed char)(dpl ? dpl : default_dpl(D));
+  if (e && D >= 0 && D <= 256)
+    e->dpl_by_d16[D / 16] = (signed char)(dpl ? dpl : long_dpl_default(D));
 }
 
 void batch_destroy(BatchEngine* e) {
@@ -263,6 +300,7 @@ void batch_destroy(BatchEngine* e) {
   if (e->exec) cudaGraphExecDestroy(e->exec);
   if (e->copied) cudaEventDestroy(e->copied);
   if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
+  fork_destroy(&e->fork);
   cudaFree(e->scratch);
   cudaFree(e->d_desc);
   cudaFreeHost(e->h_desc);
@@ -280,30 +318,25 @@ static int persistent_grid(K kernel, size_t smem) {
   return sms * per_sm;
 }
 
-static int capture(BatchEngine* e, const Method& mt, int wta_smem) {
-  if (e->exec) {
-    cudaGraphExecDestroy(e->exec);
-    e->exec = nullptr;
-  }
+template <bool WIDE>
+static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   const int cap = e->cap_pairs;
   const BatchHeader* hd = reinterpret_cast<const BatchHeader*>(e->d_desc);
   const Problem* probs = reinterpret_cast<const Problem*>(e->d_desc + probs_offset());
   const int* prefix = reinterpret_cast<const int*>(e->d_desc + prefix_offset(cap));
   const int stride = cap + 1;
-  const AggSeg* segs = reinterpret_cast<const AggSeg*>(e->d_desc + segs_offset(cap));
-  const int* seg_prefix = reinterpret_cast<const int*>(e->d_desc + seg_prefix_offset(cap));
+  const AggSeg* lsegs = reinterpret_cast<const AggSeg*>(e->d_desc + segs_offset(cap, 0));
+  const int* lpre = reinterpret_cast<const int*>(e->d_desc + seg_prefix_offset(cap, 0));
+  const AggSeg* bsegs = reinterpret_cast<const AggSeg*>(e->d_desc + segs_offset(cap, 1));
+  const int* bpre = reinterpret_cast<const int*>(e->d_desc + seg_prefix_offset(cap, 1));
   // launch shapes and attributes are settled before the capture starts
-  const bool wide = mt.wide != 0;
-  cudaFuncSetAttribute(batch_wta_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       wta_smem);
-  cudaFuncSetAttribute(batch_wta_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(batch_wta_kernel<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        wta_smem);
   const int g_census = persistent_grid(batch_census_kernel, 0);
   const int g_cost = persistent_grid(batch_cost_kernel, 0);
-  const int g_agg = wide ? persistent_grid(batch_agg_kernel<true>, 0)
-                         : persistent_grid(batch_agg_kernel<false>, 0);
-  const int g_wta = wide ? persistent_grid(batch_wta_kernel<true>, wta_smem)
-                         : persistent_grid(batch_wta_kernel<false>, wta_smem);
+  const int g_long = persistent_grid(batch_long_kernel<WIDE>, 0);
+  const int g_bulk = persistent_grid(batch_bulk_kernel<WIDE>, 0);
+  const int g_wta = persistent_grid(batch_wta_kernel<WIDE>, wta_smem);
   const int g_med = persistent_grid(batch_median_kernel, 0);
   cudaError_t c = cudaGetLastError();
   if (c != cudaSuccess) return set_err(e, c, "kernel attributes");
@@ -311,7 +344,6 @@ static int capture(BatchEngine* e, const Method& mt, int wta_smem) {
   cudaGraph_t g = nullptr;
   c = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (c != cudaSuccess) return set_err(e, c, "begin capture");
-  int launches = 0;
   cudaMemcpyAsync(e->d_desc, e->h_desc, e->desc_bytes, cudaMemcpyHostToDevice, cs);
   // an external record node, so the host can wait for the upload of each replay
   cudaEventRecordWithFlags(e->copied, cs, cudaEventRecordExternal);
@@ -319,22 +351,16 @@ static int capture(BatchEngine* e, const Method& mt, int wta_smem) {
   batch_census_kernel<<<g_census, 256, 0, cs>>>(hd, probs, prefix + 0 * stride, mt,
                                                 e->d_counters);
   batch_cost_kernel<<<g_cost, 256, 0, cs>>>(hd, probs, prefix + 1 * stride, mt, e->d_counters);
-  if (wide) {
-    batch_agg_kernel<true><<<g_agg, 256, 0, cs>>>(hd, probs, segs, seg_prefix, mt,
-                                                  e->d_counters);
-    batch_wta_kernel<true><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 2 * stride, mt,
-                                                         e->d_counters);
-  } else {
-    batch_agg_kernel<false><<<g_agg, 256, 0, cs>>>(hd, probs, segs, seg_prefix, mt,
-                                                   e->d_counters);
-    batch_wta_kernel<false><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 2 * stride, mt,
-                                                          e->d_counters);
-  }
-  launches += 4;
-  if (mt.flags & 2) {
-    batch_median_kernel<<<g_med, 256, 0, cs>>>(hd, probs, prefix + 3 * stride, e->d_counters);
-    launches += 1;
-  }
+  cudaEventRecord(e->fork.fork, cs);
+  cudaStreamWaitEvent(e->fork.aux, e->fork.fork, 0);
+  batch_long_kernel<WIDE><<<g_long, 256, 0, e->fork.aux>>>(hd, probs, lsegs, lpre, cap, mt,
+                                                           e->d_counters);
+  batch_bulk_kernel<WIDE><<<g_bulk, 256, 0, cs>>>(hd, probs, bsegs, bpre, cap, mt, e->d_counters);
+  cudaEventRecord(e->fork.join, e->fork.aux);
+  cudaStreamWaitEvent(cs, e->fork.join, 0);
+  batch_wta_kernel<WIDE><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 2 * stride,
+                                                       e->d_counters);
+  batch_median_kernel<<<g_med, 256, 0, cs>>>(hd, probs, prefix + 3 * stride, mt, e->d_counters);
   c = cudaStreamEndCapture(cs, &g);
   if (c != cudaSuccess) return set_err(e, c, "end capture");
   c = cudaGraphInstantiate(&e->exec, g, 0);
@@ -342,8 +368,35 @@ static int capture(BatchEngine* e, const Method& mt, int wta_smem) {
   if (c != cudaSuccess) return set_err(e, c, "graph instantiate");
   e->graph_method = mt;
   e->graph_wta_smem = wta_smem;
-  e->graph_launches = launches;
+  e->graph_launches = 6;
   return 0;
+}
+
+static int capture(BatchEngine* e, const Method& mt, int wta_smem) {
+  if (e->exec) {
+    cudaGraphExecDestroy(e->exec);
+    e->exec = nullptr;
+  }
+  return mt.wide ? capture_t<true>(e, mt, wta_smem) : capture_t<false>(e, mt, wta_smem);
+}
+
+struct Keyed {
+  AggSeg s;
+  int len;
+};
+
+// Writes one queue's segments, sorted by their longest line, and its prefix table.
+static int write_queue(std::vector<Keyed>& kv, AggSeg* segs, int* pre, int cap) {
+  std::stable_sort(kv.begin(), kv.end(), [](const Keyed& a, const Keyed& b) { return a.len > b.len; });
+  int items = 0;
+  const int n = (int)kv.size();
+  for (int i = 0; i < n; i++) {
+    segs[i] = kv[i].s;
+    pre[i] = items;
+    items += (kv[i].s.end - kv[i].s.begin + kv[i].s.group - 1) / kv[i].s.group;
+  }
+  for (int i = n; i <= cap; i++) pre[i] = items;  // padding slots never match an item
+  return items;
 }
 
 int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cudaStream_t s,
@@ -361,22 +414,12 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
   memset(hd, 0, sizeof(BatchHeader));
   Problem* hp = reinterpret_cast<Problem*>(e->h_desc + probs_offset());
   int* prefix = reinterpret_cast<int*>(e->h_desc + prefix_offset(cap));
-  AggSeg* segs = reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap));
-  int* seg_prefix = reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap));
   const int stride = cap + 1;
   int tot[4] = {0, 0, 0, 0};
-  int wta_smem = 0, nseg = 0;
-  struct Keyed {
-    AggSeg s;
-    int len;
-  };
-  Keyed keyed[4 * 64];
-  std::vector<Keyed> many;
-  Keyed* kv = keyed;
-  if (4 * n > 4 * 64) {
-    many.resize((size_t)4 * n);
-    kv = many.data();
-  }
+  int wta_smem = 0;
+  std::vector<Keyed> lk, bk;
+  lk.reserve(n);
+  bk.reserve(n);
   for (int p = 0; p < n; p++) {
     const Problem& pb = probs[p];
     hp[p] = pb;
@@ -386,28 +429,27 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
     prefix[3 * stride + p] = tot[3];
     tot[0] += census_items(pb.W, pb.H);
     tot[1] += cost_items(pb.W, pb.H);
-    tot[2] += pb.H;
+    tot[2] += wta_items(pb.W, pb.H, wta_tile_px(pb.D));
     tot[3] += median_items(pb.W, pb.H);
-    wta_smem = std::max(wta_smem, (int)wta_smem_bytes(pb.D, wta_default_chunk(pb.D)));
-    int b[4], en[4], ml[4];
-    const int na = agg_segments(pb.W, pb.H, mt.num_paths, b, en, ml);
-    const int group = 32 / agg_lanes_for(pb.D, e->dpl_by_d16[pb.D / 16]);
-    for (int a = 0; a < na; a++) kv[nseg++] = Keyed{AggSeg{p, b[a], en[a], group}, ml[a]};
+    wta_smem = std::max(wta_smem, (int)wta_smem_bytes(pb.D, wta_tile_px(pb.D)));
+    const int dpl = e->dpl_by_d16[pb.D / 16];
+    const int la = long_axis(pb.W, pb.H);
+    lk.push_back(Keyed{AggSeg{p, 0, axis_lines(la, pb.W, pb.H), 32 / long_lanes(pb.D, dpl)},
+                       std::max(pb.W, pb.H)});
+    bk.push_back(Keyed{AggSeg{p, 0, 2 * bulk_num_lines(pb.W, pb.H, mt.num_paths),
+                              32 / bulk_width(pb.D)},
+                       std::min(pb.W, pb.H)});
   }
   for (int k = 0; k < 4; k++) prefix[k * stride + n] = tot[k];
-  std::stable_sort(kv, kv + nseg, [](const Keyed& a, const Keyed& b) { return a.len > b.len; });
-  int items = 0;
-  for (int i = 0; i < nseg; i++) {
-    segs[i] = kv[i].s;
-    seg_prefix[i] = items;
-    items += (kv[i].s.end - kv[i].s.begin + kv[i].s.group - 1) / kv[i].s.group;
-  }
-  seg_prefix[nseg] = items;
+  const int nlong = write_queue(lk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 0)),
+                                reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 0)), cap);
+  const int nbulk = write_queue(bk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 1)),
+                                reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 1)), cap);
   hd->n = n;
-  hd->nseg = nseg;
   hd->total[kStCensus] = tot[0];
   hd->total[kStCost] = tot[1];
-  hd->total[kStAgg] = items;
+  hd->total[kStLong] = nlong;
+  hd->total[kStBulk] = nbulk;
   hd->total[kStWta] = tot[2];
   hd->total[kStMedian] = tot[3];
   memcpy(hd->dpl_by_d16, e->dpl_by_d16, sizeof(hd->dpl_by_d16));

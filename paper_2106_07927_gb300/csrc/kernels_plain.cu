@@ -17,37 +17,54 @@ __global__ void __launch_bounds__(256) cost_kernel(Problem pb, int agg_bytes_per
 }
 
 template <int DPL, int LPL, bool WIDE>
-__global__ void __launch_bounds__(512) aggregate_kernel(Problem pb, Method mt) {
+__global__ void __launch_bounds__(512) agg_long_kernel(Problem pb, Method mt) {
   const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  agg_warp_lines<DPL, LPL, WIDE>(pb, mt, warp * (32 / LPL), 0x7FFFFFFF);
+  agg_long_lines<DPL, LPL, WIDE>(pb, mt, warp * (32 / LPL), 0x7FFFFFFF);
+}
+
+template <int DPL, int WD, bool WIDE>
+__global__ void __launch_bounds__(512) agg_bulk_kernel(Problem pb, Method mt) {
+  const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  agg_bulk_chains<DPL, WD, WIDE>(pb, mt, warp * (32 / WD), 0x7FFFFFFF);
 }
 
 template <bool WIDE>
-__global__ void __launch_bounds__(256) wta_lr_kernel(Problem pb, Method mt, int T) {
+__global__ void __launch_bounds__(256) wta_dr_kernel(Problem pb, int T) {
   extern __shared__ __align__(16) uint16_t wsm[];
-  const int y = blockIdx.x;
-  uint16_t* out_row = (mt.flags & 2) ? pb.dlr + (int64_t)y * pb.W
-                                     : reinterpret_cast<uint16_t*>(
-                                           reinterpret_cast<uint8_t*>(pb.disp) + y * pb.out_pitch);
-  wta_lr_row<WIDE>(pb, mt, y, T, wsm, out_row);
+  wta_dr_tile<WIDE>(pb, blockIdx.x, wsm, T);
 }
 
-__global__ void __launch_bounds__(256) median_kernel(Problem pb) {
+__global__ void __launch_bounds__(256) lr_median_kernel(Problem pb, Method mt) {
   __shared__ MedianSmem sm;
-  median_tile(pb.dlr, pb.W, pb.W, pb.H, pb.disp, pb.out_pitch, blockIdx.x, sm);
+  lr_median_tile(pb, mt, blockIdx.x, sm);
 }
 
-__global__ void agg_to_u16_kernel(const uint32_t* src, uint16_t* dst, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (uint16_t)min(src[i], 65535u);
+// Debug copies in natural disparity order: sums saturated to uint16, costs as they are.
+template <bool WIDE>
+__global__ void agg_copy_kernel(const void* src, uint16_t* dst, int64_t npx, int D, VolOrder o) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx * D;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / D;
+    const int pos = (int)(i - p * D);
+    const uint32_t v = WIDE ? min(reinterpret_cast<const uint32_t*>(src)[i], 65535u)
+                            : reinterpret_cast<const uint16_t*>(src)[i];
+    dst[p * D + vol_index(pos - pos % 4, o, 4) + pos % 4] = (uint16_t)v;
+  }
+}
+__global__ void cost_copy_kernel(const uint8_t* src, uint8_t* dst, int64_t npx, int D, VolOrder o) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx * D;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / D;
+    const int pos = (int)(i - p * D);
+    dst[p * D + vol_index(pos - pos % 16, o, 16) + pos % 16] = src[i];
+  }
 }
 
 Tuning default_tuning(int D) {
   Tuning t;
-  t.agg_dpl = D <= 64 ? 2 : (D <= 128 ? 4 : 8);
+  t.agg_dpl = long_dpl_default(D);
   t.agg_warps = 4;
-  t.wta_chunk = wta_default_chunk(D);
+  t.wta_chunk = wta_tile_px(D);
   return t;
 }
 
@@ -56,46 +73,99 @@ bool tuning_valid(const Tuning& t, int D) {
   if (D % t.agg_dpl != 0) return false;
   if ((D + t.agg_dpl - 1) / t.agg_dpl > 32) return false;
   if (t.agg_warps < 1 || t.agg_warps > 16) return false;
-  if (t.wta_chunk < 32 || t.wta_chunk > 256 || t.wta_chunk % 32 != 0) return false;
-  if (wta_smem_bytes(D, t.wta_chunk) > 200 * 1024) return false;
+  if (t.wta_chunk != 32 && t.wta_chunk != 64 && t.wta_chunk != 128 && t.wta_chunk != 256)
+    return false;
+  if (wta_smem_bytes(D, t.wta_chunk) > 96 * 1024) return false;
   return true;
 }
 
+cudaError_t fork_create(Fork* f) {
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaError_t e = cudaStreamCreateWithPriority(&f->aux, cudaStreamNonBlocking, hi);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->join, cudaEventDisableTiming);
+  return e;
+}
+
+void fork_destroy(Fork* f) {
+  if (f->aux) cudaStreamDestroy(f->aux);
+  if (f->fork) cudaEventDestroy(f->fork);
+  if (f->join) cudaEventDestroy(f->join);
+  f->aux = nullptr;
+  f->fork = f->join = nullptr;
+}
+
 template <int DPL, int LPL, bool WIDE>
-static cudaError_t launch_agg_t(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
-  const int nl = agg_num_lines(pb.W, pb.H, mt.num_paths);
-  const int lines_per_warp = 32 / LPL;
-  const int nwarp = (nl + lines_per_warp - 1) / lines_per_warp;
-  const int grid = (nwarp + warps - 1) / warps;
-  aggregate_kernel<DPL, LPL, WIDE><<<grid, warps * 32, 0, s>>>(pb, mt);
+static cudaError_t launch_long_t(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
+  const int nl = axis_lines(long_axis(pb.W, pb.H), pb.W, pb.H);
+  const int nwarp = (nl + 32 / LPL - 1) / (32 / LPL);
+  agg_long_kernel<DPL, LPL, WIDE><<<(nwarp + warps - 1) / warps, warps * 32, 0, s>>>(pb, mt);
   return cudaGetLastError();
 }
 
 template <bool WIDE>
-static cudaError_t launch_agg_w(const Problem& pb, const Method& mt, const Tuning& tn,
-                                cudaStream_t s) {
-  const int lpl = agg_lanes_for(pb.D, tn.agg_dpl);
-  switch (tn.agg_dpl * 100 + lpl) {
-    case 208: return launch_agg_t<2, 8, WIDE>(pb, mt, tn.agg_warps, s);
-    case 216: return launch_agg_t<2, 16, WIDE>(pb, mt, tn.agg_warps, s);
-    case 232: return launch_agg_t<2, 32, WIDE>(pb, mt, tn.agg_warps, s);
-    case 408: return launch_agg_t<4, 8, WIDE>(pb, mt, tn.agg_warps, s);
-    case 416: return launch_agg_t<4, 16, WIDE>(pb, mt, tn.agg_warps, s);
-    case 432: return launch_agg_t<4, 32, WIDE>(pb, mt, tn.agg_warps, s);
-    case 808: return launch_agg_t<8, 8, WIDE>(pb, mt, tn.agg_warps, s);
-    case 816: return launch_agg_t<8, 16, WIDE>(pb, mt, tn.agg_warps, s);
-    case 832: return launch_agg_t<8, 32, WIDE>(pb, mt, tn.agg_warps, s);
+static cudaError_t launch_long(const Problem& pb, const Method& mt, const Tuning& tn,
+                               cudaStream_t s) {
+  switch (tn.agg_dpl * 100 + long_lanes(pb.D, tn.agg_dpl)) {
+    case 208: return launch_long_t<2, 8, WIDE>(pb, mt, tn.agg_warps, s);
+    case 216: return launch_long_t<2, 16, WIDE>(pb, mt, tn.agg_warps, s);
+    case 232: return launch_long_t<2, 32, WIDE>(pb, mt, tn.agg_warps, s);
+    case 408: return launch_long_t<4, 8, WIDE>(pb, mt, tn.agg_warps, s);
+    case 416: return launch_long_t<4, 16, WIDE>(pb, mt, tn.agg_warps, s);
+    case 432: return launch_long_t<4, 32, WIDE>(pb, mt, tn.agg_warps, s);
+    case 808: return launch_long_t<8, 8, WIDE>(pb, mt, tn.agg_warps, s);
+    case 816: return launch_long_t<8, 16, WIDE>(pb, mt, tn.agg_warps, s);
+    case 832: return launch_long_t<8, 32, WIDE>(pb, mt, tn.agg_warps, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int DPL, int WD, bool WIDE>
+static cudaError_t launch_bulk_t(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
+  const int nc = 2 * bulk_num_lines(pb.W, pb.H, mt.num_paths);
+  const int nwarp = (nc + 32 / WD - 1) / (32 / WD);
+  agg_bulk_kernel<DPL, WD, WIDE><<<(nwarp + warps - 1) / warps, warps * 32, 0, s>>>(pb, mt);
+  return cudaGetLastError();
+}
+
+template <bool WIDE>
+static cudaError_t launch_bulk(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
+  switch (bulk_dpl(pb.D) * 100 + bulk_width(pb.D)) {
+    case 1601: return launch_bulk_t<16, 1, WIDE>(pb, mt, warps, s);
+    case 1604: return launch_bulk_t<16, 4, WIDE>(pb, mt, warps, s);
+    case 1608: return launch_bulk_t<16, 8, WIDE>(pb, mt, warps, s);
+    case 1616: return launch_bulk_t<16, 16, WIDE>(pb, mt, warps, s);
+    case 3201: return launch_bulk_t<32, 1, WIDE>(pb, mt, warps, s);
+    case 3202: return launch_bulk_t<32, 2, WIDE>(pb, mt, warps, s);
+    case 3204: return launch_bulk_t<32, 4, WIDE>(pb, mt, warps, s);
+    case 3208: return launch_bulk_t<32, 8, WIDE>(pb, mt, warps, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 static cudaError_t launch_aggregate(const Problem& pb, const Method& mt, const Tuning& tn,
-                                    cudaStream_t s) {
-  return mt.wide ? launch_agg_w<true>(pb, mt, tn, s) : launch_agg_w<false>(pb, mt, tn, s);
+                                    cudaStream_t s, const Fork* fork) {
+  cudaStream_t ls = s;
+  if (fork) {
+    cudaEventRecord(fork->fork, s);
+    cudaStreamWaitEvent(fork->aux, fork->fork, 0);
+    ls = fork->aux;
+  }
+  cudaError_t e = mt.wide ? launch_long<true>(pb, mt, tn, ls) : launch_long<false>(pb, mt, tn, ls);
+  if (e != cudaSuccess) return e;
+  e = mt.wide ? launch_bulk<true>(pb, mt, tn.agg_warps, s)
+              : launch_bulk<false>(pb, mt, tn.agg_warps, s);
+  if (e != cudaSuccess) return e;
+  if (fork) {
+    cudaEventRecord(fork->join, fork->aux);
+    cudaStreamWaitEvent(s, fork->join, 0);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
-                         int* launches, cudaEvent_t* ev) {
+                         int* launches, cudaEvent_t* ev, const Fork* fork) {
   int n = 0;
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], s);
@@ -107,36 +177,41 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
-  if ((e = launch_aggregate(pb, mt, tn, s)) != cudaSuccess) return e;
-  n++;
+  if ((e = launch_aggregate(pb, mt, tn, s, fork)) != cudaSuccess) return e;
+  n += 2;
   if (ev) cudaEventRecord(ev[3], s);
-  const size_t smem = wta_smem_bytes(pb.D, tn.wta_chunk);
+  const int T = tn.wta_chunk;
+  const size_t smem = wta_smem_bytes(pb.D, T);
   if (mt.wide) {
-    cudaFuncSetAttribute(wta_lr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    wta_lr_kernel<true><<<pb.H, 256, smem, s>>>(pb, mt, tn.wta_chunk);
+    cudaFuncSetAttribute(wta_dr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    wta_dr_kernel<true><<<wta_items(pb.W, pb.H, T), 256, smem, s>>>(pb, T);
   } else {
-    cudaFuncSetAttribute(wta_lr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    wta_lr_kernel<false><<<pb.H, 256, smem, s>>>(pb, mt, tn.wta_chunk);
+    cudaFuncSetAttribute(wta_dr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    wta_dr_kernel<false><<<wta_items(pb.W, pb.H, T), 256, smem, s>>>(pb, T);
   }
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[4], s);
-  if (mt.flags & 2) {
-    median_kernel<<<median_items(pb.W, pb.H), 256, 0, s>>>(pb);
-    n++;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  lr_median_kernel<<<median_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
+  n++;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[5], s);
   if (launches) *launches = n;
   return cudaSuccess;
 }
 
 cudaError_t copy_agg_u16(const Problem& pb, bool wide, uint16_t* dst, cudaStream_t s) {
-  const int64_t nde = (int64_t)pb.W * pb.H * pb.D;
-  if (!wide) return cudaMemcpyAsync(dst, pb.agg, (size_t)nde * 2, cudaMemcpyDeviceToDevice, s);
-  agg_to_u16_kernel<<<1216, 256, 0, s>>>(reinterpret_cast<const uint32_t*>(pb.agg), dst, nde);
+  const int64_t npx = (int64_t)pb.W * pb.H;
+  if (wide)
+    agg_copy_kernel<true><<<1216, 256, 0, s>>>(pb.agg, dst, npx, pb.D, pb.ord);
+  else
+    agg_copy_kernel<false><<<1216, 256, 0, s>>>(pb.agg, dst, npx, pb.D, pb.ord);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_cost(const Problem& pb, uint8_t* dst, cudaStream_t s) {
+  const int64_t npx = (int64_t)pb.W * pb.H;
+  cost_copy_kernel<<<1216, 256, 0, s>>>(pb.cost, dst, npx, pb.D, pb.ord);
   return cudaGetLastError();
 }
 

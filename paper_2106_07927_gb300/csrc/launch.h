@@ -8,23 +8,32 @@
 namespace r2t {
 
 struct Tuning {
-  int agg_dpl;    // disparities per lane (2, 4 or 8)
+  int agg_dpl;    // disparities per lane of the long-axis aggregation (2, 4 or 8)
   int agg_warps;  // warps per aggregation block
-  int wta_chunk;  // pixels per chunk of the row walk
+  int wta_chunk;  // pixels per block of the WTA / right-disparity stage
 };
+
+// A second stream and two events that let the two aggregation kernels run concurrently: the
+// long-axis kernel goes to `aux` (forked from and joined back to the caller's stream).
+struct Fork {
+  cudaStream_t aux;
+  cudaEvent_t fork, join;
+};
+cudaError_t fork_create(Fork* f);
+void fork_destroy(Fork* f);
 
 // Default configuration for a disparity count D.
 Tuning default_tuning(int D);
 // True when the configuration can run a pair with D disparities.
 bool tuning_valid(const Tuning& t, int D);
 
-// Plain single-pair pipeline: 4 or 5 kernel launches on stream s (census, cost + clearing of
-// the aggregated volume, aggregation, WTA / right disparity / LR check, median). Returns the
+// Plain single-pair pipeline: 5 kernel launches on stream s (census; cost + clearing of the
+// aggregated volume; aggregation; WTA + right-disparity keys; LR check + median). Returns the
 // number of launches through *launches.
-// ev: NULL, or 6 events recorded around the stages (before census, after each of the five
-// stages; the median slot is recorded even when the median is skipped).
+// ev: NULL, or 6 events recorded around the stages (before census, after each of the five).
+// fork: NULL runs the two aggregation kernels one after the other on s.
 cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
-                         int* launches, cudaEvent_t* ev = nullptr);
+                         int* launches, cudaEvent_t* ev = nullptr, const Fork* fork = nullptr);
 
 // Sets the calling thread's res2tac_last_error message; returns code.
 int report_error(int code, const char* msg);
@@ -32,7 +41,8 @@ int report_error(int code, const char* msg);
 // Packed-u16 integer throughput probe: lane operations per second.
 cudaError_t probe_int_peak(int iters, cudaStream_t s, double* lane_ops_per_s);
 
-// Converts the aggregated volume to saturated uint16 (identity copy when not wide).
+// Copies the aggregated volume as saturated uint16 / the cost volume, both in natural order.
 cudaError_t copy_agg_u16(const Problem& pb, bool wide, uint16_t* dst, cudaStream_t s);
+cudaError_t copy_cost(const Problem& pb, uint8_t* dst, cudaStream_t s);
 
 }  // namespace r2t

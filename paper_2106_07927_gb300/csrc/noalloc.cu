@@ -10,6 +10,7 @@
 
 #include "../../include/res2tac.h"
 #include "launch.h"
+#include "layout.h"
 
 namespace {
 
@@ -20,8 +21,6 @@ static __device__ __align__(256) unsigned char g_static_scratch[RES2TAC_STATIC_S
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mu;
 void* g_scratch_addr[kMaxDevices];  // device address of g_static_scratch on each device
-
-size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 int reject(int code, const char* fmt, ...) {
   char msg[384];
@@ -46,22 +45,13 @@ extern "C" int res2tac_compute_static(const res2tac_params* p, const uint8_t* le
     return reject(RES2TAC_EINVAL, "res2tac_compute_static: bad pitch or output alignment");
   const int W = p->width, H = p->height, D = p->max_disp;
   const bool wide = p->num_paths * (255 + p->p2) > 65535;
-  const size_t npx = (size_t)W * H, nde = npx * D;
-  // offsets of the buffers inside the array (the same buffers a context allocates)
-  size_t o = 0;
-  const size_t o_ctl = o; o = up256(o + npx * 8);
-  const size_t o_ctr = o; o = up256(o + npx * 8);
-  const size_t o_cost = o; o = up256(o + nde);
-  const size_t o_agg = o; o = up256(o + nde * (wide ? 4 : 2));
-  const size_t o_dl = o; o = up256(o + npx * 2);
-  const size_t o_dr = o; o = up256(o + npx * 2);
-  const size_t o_dlr = o; o = up256(o + npx * 2);
-  const size_t o_mask = o; o = up256(o + npx);
-  if (o > RES2TAC_STATIC_SCRATCH_BYTES)
+  // the same buffers a context allocates, at their offsets inside the array
+  const r2t::Layout lay = r2t::layout_for(W, H, D, wide);
+  if (lay.total > RES2TAC_STATIC_SCRATCH_BYTES)
     return reject(RES2TAC_ENOMEM,
                   "res2tac_compute_static: %dx%d with D=%d needs %zu bytes of scratch, more than "
                   "the fixed array of %zu bytes",
-                  W, H, D, o, (size_t)RES2TAC_STATIC_SCRATCH_BYTES);
+                  W, H, D, lay.total, (size_t)RES2TAC_STATIC_SCRATCH_BYTES);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
@@ -82,24 +72,13 @@ extern "C" int res2tac_compute_static(const res2tac_params* p, const uint8_t* le
     }
     base = static_cast<char*>(g_scratch_addr[dev]);
   }
-  r2t::Problem pb;
-  memset(&pb, 0, sizeof(pb));
+  // the aggregated volume and the right-disparity keys are reset by the cost stage of each call
+  r2t::Problem pb = r2t::problem_at(base, lay, W, H, D);
   pb.left = left;
   pb.right = right;
   pb.in_pitch = in_pitch;
   pb.disp = disp;
   pb.out_pitch = out_pitch;
-  pb.W = W;
-  pb.H = H;
-  pb.D = D;
-  pb.ctl = reinterpret_cast<uint64_t*>(base + o_ctl);
-  pb.ctr = reinterpret_cast<uint64_t*>(base + o_ctr);
-  pb.cost = reinterpret_cast<uint8_t*>(base + o_cost);
-  pb.agg = base + o_agg;  // cleared by the cost stage before the paths add into it
-  pb.dl = reinterpret_cast<uint16_t*>(base + o_dl);
-  pb.dr = reinterpret_cast<uint16_t*>(base + o_dr);
-  pb.dlr = reinterpret_cast<uint16_t*>(base + o_dlr);
-  pb.mask = reinterpret_cast<uint8_t*>(base + o_mask);
   r2t::Method mt;
   mt.cw = p->census_w;
   mt.ch = p->census_h;
