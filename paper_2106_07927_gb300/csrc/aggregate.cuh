@@ -20,12 +20,14 @@
 //    g(q,d) = min(L(q,d), L(q,d-1) + P1, L(q,d+1) + P1) and h(p,d) = C(p,d) + g(q,d),
 //      L(p,d) = min(h(p,d) - m(q), C(p,d) + P2),
 //      m(p)   = min(min_d h(p,d) - m(q), min_d C(p,d) + P2),
-//    so the group minimum of h (one redux.sync) does not wait for m(q) and overlaps the next
-//    step; min_d C comes precomputed from the cost stage.
-//  - the other axes (short lines, many of them) run one chain per small lane group with 16 or 32
+//    so the group minima of h and of C (redux.sync) do not wait for m(q) and overlap the next
+//    step.
+//  - the other axes (short lines, many of them) run one chain per small lane group with 32
 //    disparities per lane, which amortises shuffles and reductions over much more arithmetic.
-// The cost and S vectors use a blocked disparity order (VolOrder) matched to the second kernel,
-// so each lane group's loads and atomic adds touch contiguous memory in both kernels.
+// Costs are fetched several steps ahead (registers in the first kernel, a per-lane cp.async ring
+// in shared memory in the second). The cost and S vectors use a blocked disparity order
+// (VolOrder) matched to the second kernel, so each lane group's copies and atomic adds touch
+// contiguous memory in both kernels.
 #pragma once
 #include "common.cuh"
 
@@ -91,15 +93,42 @@ __host__ __device__ inline LineGeom bulk_line(int li, int W, int H, int num_path
   return g;
 }
 
-// Kernel configurations for D disparities. Long axis: dpl in {2, 4, 8} (smallest with
-// D / dpl <= 32), lanes = next power of two >= D / dpl. Other axes: 32 disparities per lane when
-// D % 32 == 0, else 16; group width = next power of two >= D / dpl.
+// Kernel configurations for D disparities. Long axis: dpl in {2, 4, 8}, lanes = next power of
+// two >= D / dpl (at least 8). Other axes: bulk_dpl(D) disparities per lane, group width = next
+// power of two >= D / dpl.
 __host__ __device__ inline int long_dpl_default(int D) { return D <= 64 ? 2 : (D <= 128 ? 4 : 8); }
 __host__ __device__ inline int long_lanes(int D, int dpl) {
   const int l = pow2ceil((D + dpl - 1) / dpl);
   return l < 8 ? 8 : l;
 }
 __host__ __device__ inline int bulk_width(int D) { return pow2ceil(D / bulk_dpl(D)); }
+
+// Steps of register prefetch in the long-axis kernel, and of the per-lane cp.async ring in the
+// other-axes kernel (one commit group per step, waited with cp.async.wait_group 3).
+constexpr int kBulkRing = 4;
+__host__ __device__ inline int bulk_ring_bytes(int dpl) { return kBulkRing * (dpl / 16) * 32 * 16; }
+
+// Adds 4 packed u16 sums (2 registers) into S at element e (uint16 or, when wide, uint32).
+template <bool WIDE>
+__device__ __forceinline__ void add4(void* agg, int64_t e, uint32_t a, uint32_t b) {
+  if (!WIDE) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(reinterpret_cast<uint16_t*>(agg) + e),
+              (unsigned long long)a | ((unsigned long long)b << 32));
+  } else {
+    unsigned long long* p =
+        reinterpret_cast<unsigned long long*>(reinterpret_cast<uint32_t*>(agg) + e);
+    atomicAdd(p, (unsigned long long)(a & 0xFFFFu) | ((unsigned long long)(a >> 16) << 32));
+    atomicAdd(p + 1, (unsigned long long)(b & 0xFFFFu) | ((unsigned long long)(b >> 16) << 32));
+  }
+}
+template <bool WIDE>
+__device__ __forceinline__ void add2(void* agg, int64_t e, uint32_t a) {
+  if (!WIDE)
+    atomicAdd(reinterpret_cast<unsigned int*>(reinterpret_cast<uint16_t*>(agg) + e), a);
+  else
+    atomicAdd(reinterpret_cast<unsigned long long*>(reinterpret_cast<uint32_t*>(agg) + e),
+              (unsigned long long)(a & 0xFFFFu) | ((unsigned long long)(a >> 16) << 32));
+}
 
 template <int DPL>
 struct RawCost;
@@ -138,6 +167,11 @@ struct RawCost<8> {
   }
 };
 
+__device__ __forceinline__ void unpack4(uint32_t r, uint32_t& lo, uint32_t& hi) {
+  lo = __byte_perm(r, 0u, 0x4140);
+  hi = __byte_perm(r, 0u, 0x4342);
+}
+
 // Both halves of the result hold min(lo(v), hi(v)).
 __device__ __forceinline__ uint32_t halves_min(uint32_t v) {
   return vmin2(v, __byte_perm(v, v, 0x1032));
@@ -168,84 +202,74 @@ __device__ __forceinline__ void neighbours(const uint32_t (&L)[NP], int lig, uin
   X[NP] = __byte_perm(L[NP - 1], dn, 0x5432);
 }
 
-// Adds 4 packed u16 sums (2 registers) into S at element e (uint16 or, when wide, uint32).
-template <bool WIDE>
-__device__ __forceinline__ void add4(void* agg, int64_t e, uint32_t a, uint32_t b) {
-  if (!WIDE) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(reinterpret_cast<uint16_t*>(agg) + e),
-              (unsigned long long)a | ((unsigned long long)b << 32));
-  } else {
-    unsigned long long* p =
-        reinterpret_cast<unsigned long long*>(reinterpret_cast<uint32_t*>(agg) + e);
-    atomicAdd(p, (unsigned long long)(a & 0xFFFFu) | ((unsigned long long)(a >> 16) << 32));
-    atomicAdd(p + 1, (unsigned long long)(b & 0xFFFFu) | ((unsigned long long)(b >> 16) << 32));
-  }
-}
-template <bool WIDE>
-__device__ __forceinline__ void add2(void* agg, int64_t e, uint32_t a) {
-  if (!WIDE)
-    atomicAdd(reinterpret_cast<unsigned int*>(reinterpret_cast<uint16_t*>(agg) + e), a);
-  else
-    atomicAdd(reinterpret_cast<unsigned long long*>(reinterpret_cast<uint32_t*>(agg) + e),
-              (unsigned long long)(a & 0xFFFFu) | ((unsigned long long)(a >> 16) << 32));
-}
-
 // ------------------------------------------------------------------------------- long axis
-// One pipelined step. In: L = L(q, .), mm = m(q) in both halves, c = C(p, .),
-// cp2 = C(p, .) + P2, cminp2 = (min_d C(p, d) + P2) in both halves.
-template <int DPL, int LPL>
+// One pipelined step. In: L = L(q, .), mm = m(q) in both halves, c = C(p, .). Out: L(p, .),
+// m(p) in both halves.
+template <int DPL, int LPL, bool FULL>
 __device__ __forceinline__ void long_step(uint32_t (&L)[DPL / 2], uint32_t& mm,
-                                          const uint32_t (&c)[DPL / 2], uint32_t cminp2,
-                                          bool active, int lig, uint32_t P1P1, uint32_t P2P2) {
+                                          const uint32_t (&c)[DPL / 2], bool active, int lig,
+                                          uint32_t P1P1, uint32_t P2P2) {
   constexpr int NP = DPL / 2;
   uint32_t X[NP + 1];
   neighbours<NP, LPL>(L, lig, X);
   uint32_t h[NP];
-  uint32_t hmin = 0xFFFFFFFFu;
+  uint32_t hmin = 0xFFFFFFFFu, cmin = 0xFFFFFFFFu;
 #pragma unroll
   for (int k = 0; k < NP; k++) {
     const uint32_t g = vmin2(L[k], vmin2(X[k], X[k + 1]) + P1P1);  // <= L(q,d), no lane carry
     h[k] = g + c[k];
     hmin = vmin2(hmin, h[k]);
+    cmin = vmin2(cmin, c[k]);
   }
-  hmin = active ? halves_min(hmin) : 0xFFFFFFFFu;
+  hmin = halves_min(hmin);
+  cmin = halves_min(cmin);
+  if (!FULL) {
+    hmin = active ? hmin : 0xFFFFFFFFu;
+    cmin = active ? cmin : 0xFFFFFFFFu;
+  }
   const uint32_t aa = group_min<LPL>(hmin);  // min_d h(p, d), both halves
+  const uint32_t cc = group_min<LPL>(cmin);  // min_d C(p, d), both halves
 #pragma unroll
   for (int k = 0; k < NP; k++) {
     const uint32_t ln = vmin2(h[k] - mm, c[k] + P2P2);  // h >= m(q) in both halves
-    L[k] = active ? ln : kSent * 0x10001u;
+    L[k] = (FULL || active) ? ln : kSent * 0x10001u;
   }
-  mm = vmin2(aa - mm, cminp2);
+  mm = vmin2(aa - mm, cc + P2P2);
 }
 
 // Lines [line0, min(line0 + 32 / LPL, line_end)) of the long axis, both directions each.
-template <int DPL, int LPL, bool WIDE>
+// FULL: every lane of a group owns disparities (D == LPL * DPL). Costs are loaded U steps ahead
+// into a register ring that each step refills in place.
+template <int DPL, int LPL, bool WIDE, bool FULL>
 __device__ __forceinline__ void agg_long_lines(const Problem& pb, const Method& mt, int line0,
                                                int line_end) {
   typedef RawCost<DPL> RC;
   typedef typename RC::T Raw;
   constexpr int NP = DPL / 2;
-  constexpr int U = 4;  // steps loaded ahead
+  constexpr int U = DPL == 8 ? 8 : 16;  // steps loaded ahead
   const int lane = threadIdx.x & 31;
   const int lig = lane % LPL;
   const int W = pb.W, H = pb.H, D = pb.D;
   const int la = long_axis(W, H);
   const int nl = min(axis_lines(la, W, H), line_end);
   const int li = line0 + lane / LPL;
+  if (LPL == 32 && li >= nl) return;  // one line per warp: uniform
   const bool valid = li < nl;
   const LineGeom g = axis_line(la, valid ? li : 0, W, H);  // every line of the axis has len
   const int len = g.len;
-  const bool active = valid && lig * DPL < D;
+  const bool active = FULL ? valid : (valid && lig * DPL < D);
   const int d0 = active ? lig * DPL : 0;
-  const int coff = vol_pos(d0, pb.ord, 16);      // DPL consecutive bytes
-  const int soff0 = vol_pos(d0, pb.ord, 4);      // first 4 (or 2) sums
-  const int soff1 = DPL == 8 ? vol_pos(d0 + 4, pb.ord, 4) : 0;
+  const int coff = vol_pos(d0, pb.ord, 4);  // DPL consecutive bytes
+  const int soff0 = vol_pos(d0, pb.ord, 2);  // first 4 (or 2) sums
+  const int soff1 = DPL == 8 ? vol_pos(d0 + 4, pb.ord, 2) - soff0 : 0;
   const int64_t pstride = (int64_t)g.dy * W + g.dx;  // pixels per step
+  const int64_t estride = pstride * D;                // volume elements per step
   const int64_t pf = (int64_t)g.sy * W + g.sx;
   const int64_t pbk = pf + (int64_t)(len - 1) * pstride;
   const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
-  const uint8_t* cost = pb.cost;
-  const uint8_t* cmin = pb.cmin;
+  const uint8_t* cf = pb.cost + pf * D + coff;  // next load of each direction
+  const uint8_t* cb = pb.cost + pbk * D + coff;
+  int64_t ef = pf * D + soff0, eb = pbk * D + soff0;
 
   uint32_t Lf[NP], Lb[NP];
 #pragma unroll
@@ -253,60 +277,49 @@ __device__ __forceinline__ void agg_long_lines(const Problem& pb, const Method& 
   uint32_t mf = 0, mb = 0;
 
   Raw rf[U], rb[U];
-  uint32_t qf[U], qb[U];  // min_d C of the step's pixels
 #pragma unroll
   for (int u = 0; u < U; u++) {
-    const int64_t xf = pf + u * pstride, xb = pbk - u * pstride;
-    const bool ok = valid && u < len;
-    rf[u] = (active && ok) ? RC::load(cost + xf * D + coff) : Raw();
-    rb[u] = (active && ok) ? RC::load(cost + xb * D + coff) : Raw();
-    qf[u] = ok ? (uint32_t)__ldg(cmin + xf) : 0u;
-    qb[u] = ok ? (uint32_t)__ldg(cmin + xb) : 0u;
+    const bool ok = active && u < len;
+    rf[u] = ok ? RC::load(cf) : Raw();
+    rb[u] = ok ? RC::load(cb) : Raw();
+    if (u + 1 < len) {
+      cf += estride;
+      cb -= estride;
+    }
   }
   for (int t0 = 0; t0 < len; t0 += U) {
-    Raw nf[U], nb[U];
-    uint32_t nqf[U], nqb[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int t = t0 + U + u;
-      const int64_t xf = pf + t * pstride, xb = pbk - t * pstride;
-      const bool ok = valid && t < len;
-      nf[u] = (active && ok) ? RC::load(cost + xf * D + coff) : Raw();
-      nb[u] = (active && ok) ? RC::load(cost + xb * D + coff) : Raw();
-      nqf[u] = ok ? (uint32_t)__ldg(cmin + xf) : 0u;
-      nqb[u] = ok ? (uint32_t)__ldg(cmin + xb) : 0u;
-    }
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const int t = t0 + u;
-      if (t < len) {
-        uint32_t c[NP];
-        RC::unpack(rf[u], c);
-        long_step<DPL, LPL>(Lf, mf, c, (qf[u] * 0x10001u) + P2P2, active, lig, P1P1, P2P2);
-        RC::unpack(rb[u], c);
-        long_step<DPL, LPL>(Lb, mb, c, (qb[u] * 0x10001u) + P2P2, active, lig, P1P1, P2P2);
-        if (active && valid) {
-          const int64_t ef = (pf + t * pstride) * D, eb = (pbk - t * pstride) * D;
-          if (DPL == 2) {
-            add2<WIDE>(pb.agg, ef + soff0, Lf[0]);
-            add2<WIDE>(pb.agg, eb + soff0, Lb[0]);
-          } else {
-            add4<WIDE>(pb.agg, ef + soff0, Lf[0], Lf[1]);
-            add4<WIDE>(pb.agg, eb + soff0, Lb[0], Lb[1]);
-            if (DPL == 8) {
-              add4<WIDE>(pb.agg, ef + soff1, Lf[NP - 2], Lf[NP - 1]);
-              add4<WIDE>(pb.agg, eb + soff1, Lb[NP - 2], Lb[NP - 1]);
-            }
+      if (t >= len) break;
+      uint32_t c[NP];
+      RC::unpack(rf[u], c);
+      long_step<DPL, LPL, FULL>(Lf, mf, c, active, lig, P1P1, P2P2);
+      RC::unpack(rb[u], c);
+      long_step<DPL, LPL, FULL>(Lb, mb, c, active, lig, P1P1, P2P2);
+      // refill this slot with step t + U (the pointers sit there already)
+      const bool ok = active && t + U < len;
+      rf[u] = ok ? RC::load(cf) : Raw();
+      rb[u] = ok ? RC::load(cb) : Raw();
+      if (t + U + 1 < len) {
+        cf += estride;
+        cb -= estride;
+      }
+      if (active) {
+        if (DPL == 2) {
+          add2<WIDE>(pb.agg, ef, Lf[0]);
+          add2<WIDE>(pb.agg, eb, Lb[0]);
+        } else {
+          add4<WIDE>(pb.agg, ef, Lf[0], Lf[1 % NP]);
+          add4<WIDE>(pb.agg, eb, Lb[0], Lb[1 % NP]);
+          if (DPL == 8) {
+            add4<WIDE>(pb.agg, ef + soff1, Lf[2 % NP], Lf[3 % NP]);
+            add4<WIDE>(pb.agg, eb + soff1, Lb[2 % NP], Lb[3 % NP]);
           }
         }
       }
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      rf[u] = nf[u];
-      rb[u] = nb[u];
-      qf[u] = nqf[u];
-      qb[u] = nqb[u];
+      ef += estride;
+      eb -= estride;
     }
   }
 }
@@ -314,11 +327,15 @@ __device__ __forceinline__ void agg_long_lines(const Problem& pb, const Method& 
 // ------------------------------------------------------------------------------- other axes
 // Chains [chain0, min(chain0 + 32 / WD, chain_end)): chain c walks line c / 2 of the other axes,
 // forward when c is even, backward when odd. WD lanes per chain, DPL disparities per lane.
-template <int DPL, int WD, bool WIDE>
+// FULL: every lane owns disparities (D == WD * DPL). Each lane copies its own 16-byte cost
+// pieces into `ring` (this warp's kBulkRing * (DPL / 16) * 32 uint4) with cp.async and waits
+// only for its own copies, kBulkRing - 1 steps ahead.
+template <int DPL, int WD, bool WIDE, bool FULL>
 __device__ __forceinline__ void agg_bulk_chains(const Problem& pb, const Method& mt, int chain0,
-                                                int chain_end) {
+                                                int chain_end, uint4* ring) {
   constexpr int NP = DPL / 2;
-  constexpr int NV = DPL / 16;  // 16-byte cost vectors per lane
+  constexpr int NV = DPL / 16;  // 16-byte cost vectors per lane and step
+  constexpr int KS = kBulkRing;
   const int lane = threadIdx.x & 31;
   const int lig = lane % WD;
   const int W = pb.W, H = pb.H, D = pb.D;
@@ -330,80 +347,91 @@ __device__ __forceinline__ void agg_bulk_chains(const Problem& pb, const Method&
   const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)g.len);
   if (maxlen == 0) return;
   const bool back = (ci & 1) != 0;
-  const bool active = valid && lig * DPL < D;
+  const bool active = FULL ? valid : (valid && lig * DPL < D);
   int64_t pstride = (int64_t)g.dy * W + g.dx;
   int64_t px = (int64_t)g.sy * W + g.sx;
   if (back) {
     px += (int64_t)(g.len - 1) * pstride;
     pstride = -pstride;
   }
-  // lane member lig owns disparities [d0, d0 + DPL): cost chunk h at (h * lpl + lig) * 16,
-  // sum chunk k at (k * lpl + lig) * 4 (VolOrder blocked, lpl = D / DPL)
-  const int lpl = D / DPL;
+  const int64_t estride = pstride * D;
+  // lane member lig owns disparities [lig * DPL, (lig + 1) * DPL): its cost piece v sits at
+  // cbo + v * cvs bytes and its sum chunk k at sbo + k * svs elements of the pixel vector
+  const int cvs = FULL ? WD * 16 : (pb.ord.blocked ? (D / DPL) * 16 : 16);
+  const int svs = FULL ? WD * 4 : (pb.ord.blocked ? (D / DPL) * 4 : 4);
+  const int cbo = (FULL || pb.ord.blocked) ? lig * 16 : lig * DPL;
+  const int sbo = (FULL || pb.ord.blocked) ? lig * 4 : lig * DPL;
+  const uint8_t* cp = pb.cost + px * D + cbo;  // next step to copy
+  int64_t e = px * D + sbo;                     // element of this step's first sum
   const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(ring);
 
   uint32_t L[NP];
 #pragma unroll
   for (int k = 0; k < NP; k++) L[k] = active ? 0u : kSent * 0x10001u;
   uint32_t mm = 0;
 
-  uint4 ra[NV], rb[NV];  // costs of the next two steps
+  // prologue: steps 0 .. KS - 2 in flight, one commit group each
 #pragma unroll
-  for (int v = 0; v < NV; v++) {
-    ra[v] = (active && 0 < g.len)
-                ? __ldg(reinterpret_cast<const uint4*>(pb.cost + px * D + (v * lpl + lig) * 16))
-                : make_uint4(0, 0, 0, 0);
-    rb[v] = (active && 1 < g.len) ? __ldg(reinterpret_cast<const uint4*>(
-                                        pb.cost + (px + pstride) * D + (v * lpl + lig) * 16))
-                                  : make_uint4(0, 0, 0, 0);
-  }
-  for (int t = 0; t < maxlen; t++) {
-    uint32_t c[NP];
+  for (int s = 0; s < KS - 1; s++) {
+    if (active && s < g.len) {
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-      const uint4 r = (t & 1) ? rb[v] : ra[v];
-      c[8 * v + 0] = __byte_perm(r.x, 0u, 0x4140);
-      c[8 * v + 1] = __byte_perm(r.x, 0u, 0x4342);
-      c[8 * v + 2] = __byte_perm(r.y, 0u, 0x4140);
-      c[8 * v + 3] = __byte_perm(r.y, 0u, 0x4342);
-      c[8 * v + 4] = __byte_perm(r.z, 0u, 0x4140);
-      c[8 * v + 5] = __byte_perm(r.z, 0u, 0x4342);
-      c[8 * v + 6] = __byte_perm(r.w, 0u, 0x4140);
-      c[8 * v + 7] = __byte_perm(r.w, 0u, 0x4342);
+      for (int v = 0; v < NV; v++)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         sbase + (uint32_t)(((s * NV + v) * 32 + lane) * 16)),
+                     "l"(cp + v * cvs));
+      if (s + 1 < g.len) cp += estride;
     }
-    {  // load step t + 2 into the buffer just consumed
-      const bool ok = active && t + 2 < g.len;
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (int t0 = 0; t0 < maxlen; t0 += KS) {
+#pragma unroll
+    for (int u = 0; u < KS; u++) {
+      const int t = t0 + u;
+      if (t >= maxlen) break;
+      {  // issue step t + KS - 1 into slot (u + KS - 1) % KS, then wait for step t
+        const int slot = (u + KS - 1) % KS;
+        if (active && t + KS - 1 < g.len) {
+#pragma unroll
+          for (int v = 0; v < NV; v++)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             sbase + (uint32_t)(((slot * NV + v) * 32 + lane) * 16)),
+                         "l"(cp + v * cvs));
+          if (t + KS < g.len) cp += estride;
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 3;" ::: "memory");
+      }
+      uint32_t c[NP];
 #pragma unroll
       for (int v = 0; v < NV; v++) {
-        const uint4 n = ok ? __ldg(reinterpret_cast<const uint4*>(
-                                 pb.cost + (px + 2 * pstride) * D + (v * lpl + lig) * 16))
-                           : make_uint4(0, 0, 0, 0);
-        if (t & 1)
-          rb[v] = n;
-        else
-          ra[v] = n;
+        const uint4 r = ring[(u * NV + v) * 32 + lane];
+        unpack4(r.x, c[8 * v + 0], c[8 * v + 1]);
+        unpack4(r.y, c[8 * v + 2], c[8 * v + 3]);
+        unpack4(r.z, c[8 * v + 4], c[8 * v + 5]);
+        unpack4(r.w, c[8 * v + 6], c[8 * v + 7]);
       }
-    }
-    uint32_t X[NP + 1];
-    neighbours<NP, WD>(L, lig, X);
-    const uint32_t mP2 = mm + P2P2;
-    uint32_t lmin = 0xFFFFFFFFu;
+      uint32_t X[NP + 1];
+      neighbours<NP, WD>(L, lig, X);
+      const uint32_t mP2 = mm + P2P2;
+      uint32_t lmin = 0xFFFFFFFFu;
 #pragma unroll
-    for (int k = 0; k < NP; k++) {
-      const uint32_t tt = vmin2(X[k], X[k + 1]) + P1P1;
-      const uint32_t u = vmin2(vmin2(L[k], tt), mP2);  // >= m(q) in both halves
-      const uint32_t ln = u + c[k] - mm;                // each half in [0, 255 + P2]
-      L[k] = active ? ln : kSent * 0x10001u;
-      lmin = vmin2(lmin, L[k]);
-    }
-    mm = group_min<WD>(halves_min(lmin));
-    if (active && t < g.len) {
-      const int64_t e = px * D;
+      for (int k = 0; k < NP; k++) {
+        const uint32_t tt = vmin2(X[k], X[k + 1]) + P1P1;
+        const uint32_t uu = vmin2(vmin2(L[k], tt), mP2);  // >= m(q) in both halves
+        const uint32_t ln = uu + c[k] - mm;                // each half in [0, 255 + P2]
+        L[k] = (FULL || active) ? ln : kSent * 0x10001u;
+        lmin = vmin2(lmin, L[k]);
+      }
+      mm = group_min<WD>(halves_min(lmin));
+      if (active && t < g.len) {
 #pragma unroll
-      for (int k = 0; k < NP / 2; k++) add4<WIDE>(pb.agg, e + (k * lpl + lig) * 4, L[2 * k], L[2 * k + 1]);
+        for (int k = 0; k < NP / 2; k++) add4<WIDE>(pb.agg, e + k * svs, L[2 * k], L[2 * k + 1]);
+      }
+      e += estride;
     }
-    px += pstride;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 }  // namespace r2t

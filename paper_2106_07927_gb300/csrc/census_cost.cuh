@@ -38,8 +38,8 @@ __device__ __forceinline__ void census_tile(const Problem& pb, int item, CensusS
   const uint8_t* src = img ? pb.right : pb.left;
   uint64_t* dst = img ? pb.ctr : pb.ctl;
   for (int i = threadIdx.x; i < SW * SH; i += blockDim.x) {
-    int ty = i / SW, tx = i % SW;
-    int gx = x0 + tx - RX, gy = y0 + ty - RY;
+    const int ty = i / SW, tx = i - ty * SW;
+    const int gx = x0 + tx - RX, gy = y0 + ty - RY;
     uint8_t v = 0;
     if (gx >= 0 && gx < pb.W && gy >= 0 && gy < pb.H) v = src[(int64_t)gy * pb.in_pitch + gx];
     sm.tile[ty][tx] = v;
@@ -76,55 +76,49 @@ __device__ __forceinline__ void census_tile_dispatch(const Problem& pb, const Me
 struct CostSmem {
   uint64_t r[kCostTX + 256];  // CT_R(x0 - D + 1 .. x0 + 31)
   uint64_t l[kCostTX];
-  unsigned int cmin[kCostTX];  // min_d C of each pixel of the tile
 };
 
-// One row segment of 32 pixels, all disparities, written as 4-byte words (coalesced along d).
-// The same tile of the aggregated volume is cleared here (16-byte stores) and the tile's
-// right-disparity keys are set to their maximum, so the later stages can add / atomicMin into
-// them without separate memset passes; agg_bytes_per_de is 2, or 4 when wide.
+// One row segment of 32 pixels, all disparities, written as 4-byte words (4 consecutive
+// disparities stay consecutive in the volume's order, which moves chunks of 16). The same tile of
+// the aggregated volume is cleared here (16-byte stores) and the tile's right-disparity keys are
+// set to their maximum, so the later stages can add / atomicMin into them without separate memset
+// passes; agg_bytes_per_de is 2, or 4 when wide.
 __device__ __forceinline__ void cost_tile(const Problem& pb, int item, CostSmem& sm,
                                           int agg_bytes_per_de) {
   const int ntx = (pb.W + kCostTX - 1) / kCostTX;
   const int y = item / ntx;
-  const int x0 = (item % ntx) * kCostTX;
+  const int x0 = (item - y * ntx) * kCostTX;
   const int D = pb.D;
   const uint64_t* rowr = pb.ctr + (int64_t)y * pb.W;
   const uint64_t* rowl = pb.ctl + (int64_t)y * pb.W;
   for (int i = threadIdx.x; i < kCostTX + D - 1; i += blockDim.x) {
-    int xr = x0 - (D - 1) + i;
+    const int xr = x0 - (D - 1) + i;
     sm.r[i] = (xr >= 0 && xr < pb.W) ? rowr[xr] : 0ull;
   }
-  for (int i = threadIdx.x; i < kCostTX; i += blockDim.x) {
+  for (int i = threadIdx.x; i < kCostTX; i += blockDim.x)
     sm.l[i] = (x0 + i < pb.W) ? rowl[x0 + i] : 0ull;
-    sm.cmin[i] = 0xFFu;
-  }
   __syncthreads();
-  const int nq = D / 4;
+  const int nq = D / 4;  // 4-disparity words per pixel
+  // exact it / nq for it < 2^16 (nq <= 64): multiply by ceil(2^32 / nq), keep the high word
+  const uint32_t inv = (uint32_t)((0xFFFFFFFFull + nq) / nq);
+  const int64_t rowe = (int64_t)y * pb.W * D;
   for (int it = threadIdx.x; it < kCostTX * nq; it += blockDim.x) {
-    const int px = it / nq, q = it - px * nq;
+    const int px = (int)__umulhi((uint32_t)it, inv), q = it - px * nq;
     const int x = x0 + px;
     if (x >= pb.W) continue;
     const uint64_t cl = sm.l[px];
-    uint32_t word = 0, mn = 0xFFu;
+    uint32_t word = 0;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       const int d = 4 * q + j;
       uint32_t v = kCostOutside;
       if (x >= d) v = (uint32_t)__popcll(cl ^ sm.r[px + D - 1 - d]);
       word |= v << (8 * j);
-      mn = min(mn, v);
     }
-    // 4 consecutive disparities stay consecutive in the volume's order (chunks of 16)
-    *reinterpret_cast<uint32_t*>(pb.cost + ((int64_t)y * pb.W + x) * D + vol_pos(4 * q, pb.ord, 16)) =
-        word;
-    atomicMin(&sm.cmin[px], mn);
+    *reinterpret_cast<uint32_t*>(pb.cost + rowe + (int64_t)x * D + vol_pos(4 * q, pb.ord, 4)) = word;
   }
-  __syncthreads();
   {
     const int npx = min(kCostTX, pb.W - x0);
-    for (int i = threadIdx.x; i < npx; i += blockDim.x)
-      pb.cmin[(int64_t)y * pb.W + x0 + i] = (uint8_t)sm.cmin[i];
     const int64_t bytes = (int64_t)npx * D * agg_bytes_per_de;  // multiple of 32
     uint4* z = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(pb.agg) +
                                         ((int64_t)y * pb.W + x0) * D * agg_bytes_per_de);

@@ -17,19 +17,20 @@ constexpr uint32_t kSent = 0xBFFFu;
 // by the lpl members of a lane group, dpl consecutive ones each, and are cut into chunks of
 // `chunk` disparities; chunk c of member l sits at chunk slot c * lpl + l, so the members'
 // accesses to chunk c are contiguous in memory (chunk = 16 for the cost, 4 for the sums).
+// dpl and lpl are powers of two (their log2 in ldpl, llpl); chunk is 4 or 16 (log2 lc).
 struct VolOrder {
-  int blocked, dpl, lpl;
+  int blocked, ldpl, llpl;
 };
-__host__ __device__ inline int vol_pos(int d, VolOrder o, int chunk) {
+__host__ __device__ inline int vol_pos(int d, VolOrder o, int lc) {
   if (!o.blocked) return d;
-  const int l = d / o.dpl, w = d - l * o.dpl;
-  return ((w / chunk) * o.lpl + l) * chunk + (w % chunk);
+  const int l = d >> o.ldpl, w = d & ((1 << o.ldpl) - 1);
+  return ((((w >> lc) << o.llpl) + l) << lc) + (w & ((1 << lc) - 1));
 }
 // Inverse of vol_pos: the disparity stored at position p.
-__host__ __device__ inline int vol_index(int p, VolOrder o, int chunk) {
+__host__ __device__ inline int vol_index(int p, VolOrder o, int lc) {
   if (!o.blocked) return p;
-  const int c = p / chunk, k = c / o.lpl, l = c - k * o.lpl;
-  return l * o.dpl + k * chunk + (p - c * chunk);
+  const int c = p >> lc, k = c >> o.llpl, l = c & ((1 << o.llpl) - 1);
+  return (l << o.ldpl) + (k << lc) + (p & ((1 << lc) - 1));
 }
 
 __host__ __device__ inline int pow2ceil(int v) {
@@ -37,13 +38,20 @@ __host__ __device__ inline int pow2ceil(int v) {
   while (p < v) p *= 2;
   return p;
 }
-// Disparities per lane of the short-line aggregation kernel, which fixes the volumes' order.
+__host__ __device__ inline int ilog2(int v) {
+  int l = 0;
+  while ((1 << (l + 1)) <= v) l++;
+  return l;
+}
+// Disparities per lane of the short-line aggregation kernel, which fixes the volumes' order:
+// blocked when the D / dpl lane members are a power of two, natural otherwise.
 __host__ __device__ inline int bulk_dpl(int D) { return D % 32 == 0 ? 32 : 16; }
 __host__ __device__ inline VolOrder vol_order_for(int D) {
   VolOrder o;
-  o.blocked = 1;
-  o.dpl = bulk_dpl(D);
-  o.lpl = D / o.dpl;
+  const int dpl = bulk_dpl(D), lpl = D / dpl;
+  o.blocked = (lpl & (lpl - 1)) == 0 ? 1 : 0;
+  o.ldpl = ilog2(dpl);
+  o.llpl = ilog2(lpl);
   return o;
 }
 
@@ -60,7 +68,6 @@ struct Problem {
   uint64_t* ctl;      // census descriptors of the left / right image, [H][W]
   uint64_t* ctr;
   uint8_t* cost;      // [H][W][D]
-  uint8_t* cmin;      // [H][W] min_d C(x, y, d)
   void* agg;          // [H][W][D], uint16 (or uint32 when wide)
   uint16_t* dl;       // [H][W] winner-takes-all map
   uint16_t* dr;       // [H][W] approximate right map

@@ -101,35 +101,53 @@ __global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
   }
 }
 
+template <int DPL, int LPL, bool WIDE>
+__device__ __forceinline__ void long_full(const Problem& pb, const Method& mt, int line0,
+                                          int line_end) {
+  if (pb.D == DPL * LPL)
+    agg_long_lines<DPL, LPL, WIDE, true>(pb, mt, line0, line_end);
+  else
+    agg_long_lines<DPL, LPL, WIDE, false>(pb, mt, line0, line_end);
+}
+
 template <bool WIDE>
 __device__ __forceinline__ void long_dispatch(const Problem& pb, const Method& mt, int line0,
                                               int line_end, int dpl) {
   switch (dpl * 100 + long_lanes(pb.D, dpl)) {
-    case 208: agg_long_lines<2, 8, WIDE>(pb, mt, line0, line_end); break;
-    case 216: agg_long_lines<2, 16, WIDE>(pb, mt, line0, line_end); break;
-    case 232: agg_long_lines<2, 32, WIDE>(pb, mt, line0, line_end); break;
-    case 408: agg_long_lines<4, 8, WIDE>(pb, mt, line0, line_end); break;
-    case 416: agg_long_lines<4, 16, WIDE>(pb, mt, line0, line_end); break;
-    case 432: agg_long_lines<4, 32, WIDE>(pb, mt, line0, line_end); break;
-    case 808: agg_long_lines<8, 8, WIDE>(pb, mt, line0, line_end); break;
-    case 816: agg_long_lines<8, 16, WIDE>(pb, mt, line0, line_end); break;
-    case 832: agg_long_lines<8, 32, WIDE>(pb, mt, line0, line_end); break;
+    case 208: long_full<2, 8, WIDE>(pb, mt, line0, line_end); break;
+    case 216: long_full<2, 16, WIDE>(pb, mt, line0, line_end); break;
+    case 232: long_full<2, 32, WIDE>(pb, mt, line0, line_end); break;
+    case 408: long_full<4, 8, WIDE>(pb, mt, line0, line_end); break;
+    case 416: long_full<4, 16, WIDE>(pb, mt, line0, line_end); break;
+    case 432: long_full<4, 32, WIDE>(pb, mt, line0, line_end); break;
+    case 808: long_full<8, 8, WIDE>(pb, mt, line0, line_end); break;
+    case 816: long_full<8, 16, WIDE>(pb, mt, line0, line_end); break;
+    case 832: long_full<8, 32, WIDE>(pb, mt, line0, line_end); break;
     default: break;
   }
 }
 
+template <int DPL, int WD, bool WIDE>
+__device__ __forceinline__ void bulk_full(const Problem& pb, const Method& mt, int chain0,
+                                          int chain_end, uint4* ring) {
+  if (pb.D == DPL * WD)
+    agg_bulk_chains<DPL, WD, WIDE, true>(pb, mt, chain0, chain_end, ring);
+  else
+    agg_bulk_chains<DPL, WD, WIDE, false>(pb, mt, chain0, chain_end, ring);
+}
+
 template <bool WIDE>
 __device__ __forceinline__ void bulk_dispatch(const Problem& pb, const Method& mt, int chain0,
-                                              int chain_end) {
+                                              int chain_end, uint4* ring) {
   switch (bulk_dpl(pb.D) * 100 + bulk_width(pb.D)) {
-    case 1601: agg_bulk_chains<16, 1, WIDE>(pb, mt, chain0, chain_end); break;
-    case 1604: agg_bulk_chains<16, 4, WIDE>(pb, mt, chain0, chain_end); break;
-    case 1608: agg_bulk_chains<16, 8, WIDE>(pb, mt, chain0, chain_end); break;
-    case 1616: agg_bulk_chains<16, 16, WIDE>(pb, mt, chain0, chain_end); break;
-    case 3201: agg_bulk_chains<32, 1, WIDE>(pb, mt, chain0, chain_end); break;
-    case 3202: agg_bulk_chains<32, 2, WIDE>(pb, mt, chain0, chain_end); break;
-    case 3204: agg_bulk_chains<32, 4, WIDE>(pb, mt, chain0, chain_end); break;
-    case 3208: agg_bulk_chains<32, 8, WIDE>(pb, mt, chain0, chain_end); break;
+    case 1601: bulk_full<16, 1, WIDE>(pb, mt, chain0, chain_end, ring); break;
+    case 1604: bulk_full<16, 4, WIDE>(pb, mt, chain0, chain_end, ring); break;
+    case 1608: bulk_full<16, 8, WIDE>(pb, mt, chain0, chain_end, ring); break;
+    case 1616: bulk_full<16, 16, WIDE>(pb, mt, chain0, chain_end, ring); break;
+    case 3201: bulk_full<32, 1, WIDE>(pb, mt, chain0, chain_end, ring); break;
+    case 3202: bulk_full<32, 2, WIDE>(pb, mt, chain0, chain_end, ring); break;
+    case 3204: bulk_full<32, 4, WIDE>(pb, mt, chain0, chain_end, ring); break;
+    case 3208: bulk_full<32, 8, WIDE>(pb, mt, chain0, chain_end, ring); break;
     default: break;
   }
 }
@@ -154,6 +172,8 @@ template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_bulk_kernel(const BatchHeader* hd, const Problem* probs,
                                                          const AggSeg* segs, const int* seg_prefix,
                                                          int nseg, Method mt, unsigned* counters) {
+  extern __shared__ uint4 bring[];
+  uint4* ring = bring + (threadIdx.x >> 5) * (bulk_ring_bytes(32) / 16);
   const int total = hd->total[kStBulk];
   for (;;) {
     const int item = claim_warp(&counters[kStBulk]);
@@ -161,7 +181,7 @@ __global__ void __launch_bounds__(256) batch_bulk_kernel(const BatchHeader* hd, 
     const int si = find_slot(seg_prefix, nseg, item);
     const AggSeg sg = segs[si];
     const Problem pb = probs[sg.pair];
-    bulk_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, sg.end);
+    bulk_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, sg.end, ring);
   }
 }
 
@@ -335,7 +355,10 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   const int g_census = persistent_grid(batch_census_kernel, 0);
   const int g_cost = persistent_grid(batch_cost_kernel, 0);
   const int g_long = persistent_grid(batch_long_kernel<WIDE>, 0);
-  const int g_bulk = persistent_grid(batch_bulk_kernel<WIDE>, 0);
+  const int bulk_smem = 8 * bulk_ring_bytes(32);  // 8 warps per block
+  cudaFuncSetAttribute(batch_bulk_kernel<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       bulk_smem);
+  const int g_bulk = persistent_grid(batch_bulk_kernel<WIDE>, bulk_smem);
   const int g_wta = persistent_grid(batch_wta_kernel<WIDE>, wta_smem);
   const int g_med = persistent_grid(batch_median_kernel, 0);
   cudaError_t c = cudaGetLastError();
@@ -355,7 +378,8 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   cudaStreamWaitEvent(e->fork.aux, e->fork.fork, 0);
   batch_long_kernel<WIDE><<<g_long, 256, 0, e->fork.aux>>>(hd, probs, lsegs, lpre, cap, mt,
                                                            e->d_counters);
-  batch_bulk_kernel<WIDE><<<g_bulk, 256, 0, cs>>>(hd, probs, bsegs, bpre, cap, mt, e->d_counters);
+  batch_bulk_kernel<WIDE><<<g_bulk, 256, bulk_smem, cs>>>(hd, probs, bsegs, bpre, cap, mt,
+                                                          e->d_counters);
   cudaEventRecord(e->fork.join, e->fork.aux);
   cudaStreamWaitEvent(cs, e->fork.join, 0);
   batch_wta_kernel<WIDE><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 2 * stride,

@@ -16,16 +16,19 @@ __global__ void __launch_bounds__(256) cost_kernel(Problem pb, int agg_bytes_per
   cost_tile(pb, blockIdx.x, sm, agg_bytes_per_de);
 }
 
-template <int DPL, int LPL, bool WIDE>
+template <int DPL, int LPL, bool WIDE, bool FULL>
 __global__ void __launch_bounds__(512) agg_long_kernel(Problem pb, Method mt) {
   const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  agg_long_lines<DPL, LPL, WIDE>(pb, mt, warp * (32 / LPL), 0x7FFFFFFF);
+  agg_long_lines<DPL, LPL, WIDE, FULL>(pb, mt, warp * (32 / LPL), 0x7FFFFFFF);
 }
 
-template <int DPL, int WD, bool WIDE>
+template <int DPL, int WD, bool WIDE, bool FULL>
 __global__ void __launch_bounds__(512) agg_bulk_kernel(Problem pb, Method mt) {
-  const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  agg_bulk_chains<DPL, WD, WIDE>(pb, mt, warp * (32 / WD), 0x7FFFFFFF);
+  extern __shared__ uint4 bring[];
+  const int wib = threadIdx.x >> 5;
+  const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+  agg_bulk_chains<DPL, WD, WIDE, FULL>(pb, mt, warp * (32 / WD), 0x7FFFFFFF,
+                                       bring + wib * (bulk_ring_bytes(DPL) / 16));
 }
 
 template <bool WIDE>
@@ -48,7 +51,7 @@ __global__ void agg_copy_kernel(const void* src, uint16_t* dst, int64_t npx, int
     const int pos = (int)(i - p * D);
     const uint32_t v = WIDE ? min(reinterpret_cast<const uint32_t*>(src)[i], 65535u)
                             : reinterpret_cast<const uint16_t*>(src)[i];
-    dst[p * D + vol_index(pos - pos % 4, o, 4) + pos % 4] = (uint16_t)v;
+    dst[p * D + vol_index(pos, o, 2)] = (uint16_t)v;
   }
 }
 __global__ void cost_copy_kernel(const uint8_t* src, uint8_t* dst, int64_t npx, int D, VolOrder o) {
@@ -56,7 +59,7 @@ __global__ void cost_copy_kernel(const uint8_t* src, uint8_t* dst, int64_t npx, 
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = i / D;
     const int pos = (int)(i - p * D);
-    dst[p * D + vol_index(pos - pos % 16, o, 16) + pos % 16] = src[i];
+    dst[p * D + vol_index(pos, o, 4)] = src[i];
   }
 }
 
@@ -100,7 +103,11 @@ template <int DPL, int LPL, bool WIDE>
 static cudaError_t launch_long_t(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
   const int nl = axis_lines(long_axis(pb.W, pb.H), pb.W, pb.H);
   const int nwarp = (nl + 32 / LPL - 1) / (32 / LPL);
-  agg_long_kernel<DPL, LPL, WIDE><<<(nwarp + warps - 1) / warps, warps * 32, 0, s>>>(pb, mt);
+  const int grid = (nwarp + warps - 1) / warps;
+  if (pb.D == DPL * LPL)
+    agg_long_kernel<DPL, LPL, WIDE, true><<<grid, warps * 32, 0, s>>>(pb, mt);
+  else
+    agg_long_kernel<DPL, LPL, WIDE, false><<<grid, warps * 32, 0, s>>>(pb, mt);
   return cudaGetLastError();
 }
 
@@ -125,7 +132,17 @@ template <int DPL, int WD, bool WIDE>
 static cudaError_t launch_bulk_t(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
   const int nc = 2 * bulk_num_lines(pb.W, pb.H, mt.num_paths);
   const int nwarp = (nc + 32 / WD - 1) / (32 / WD);
-  agg_bulk_kernel<DPL, WD, WIDE><<<(nwarp + warps - 1) / warps, warps * 32, 0, s>>>(pb, mt);
+  const int grid = (nwarp + warps - 1) / warps;
+  const size_t smem = (size_t)warps * bulk_ring_bytes(DPL);
+  if (pb.D == DPL * WD) {
+    cudaFuncSetAttribute(agg_bulk_kernel<DPL, WD, WIDE, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    agg_bulk_kernel<DPL, WD, WIDE, true><<<grid, warps * 32, smem, s>>>(pb, mt);
+  } else {
+    cudaFuncSetAttribute(agg_bulk_kernel<DPL, WD, WIDE, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    agg_bulk_kernel<DPL, WD, WIDE, false><<<grid, warps * 32, smem, s>>>(pb, mt);
+  }
   return cudaGetLastError();
 }
 

@@ -8,14 +8,13 @@
 namespace r2t {
 
 struct Layout {
-  size_t ctl, ctr, cost, cmin, agg, dl, dr, kr, mask, total;
+  size_t ctl, ctr, cost, agg, dl, dr, kr, mask, total;
 };
 
 inline size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Census maps 16 B/px, cost 1 B/DE, its per-pixel minimum 1 B/px, aggregated volume 2 B/DE
-// (4 when wide), D^L and D^R 2 B/px each, right-disparity keys 4 B/px, LR mask 1 B/px:
-// 3 B per DE + 26 B per pixel.
+// Census maps 16 B/px, cost 1 B/DE, aggregated volume 2 B/DE (4 when wide), D^L and D^R
+// 2 B/px each, right-disparity keys 4 B/px, LR mask 1 B/px: 3 B per DE + 25 B per pixel.
 inline Layout layout_for(int W, int H, int D, bool wide) {
   const size_t npx = (size_t)W * H, nde = npx * D;
   Layout l;
@@ -23,7 +22,6 @@ inline Layout layout_for(int W, int H, int D, bool wide) {
   l.ctl = o; o = align256(o + npx * 8);
   l.ctr = o; o = align256(o + npx * 8);
   l.cost = o; o = align256(o + nde);
-  l.cmin = o; o = align256(o + npx);
   l.agg = o; o = align256(o + nde * (wide ? 4 : 2));
   l.dl = o; o = align256(o + npx * 2);
   l.dr = o; o = align256(o + npx * 2);
@@ -42,7 +40,6 @@ inline Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
   pb.ctl = reinterpret_cast<uint64_t*>(base + l.ctl);
   pb.ctr = reinterpret_cast<uint64_t*>(base + l.ctr);
   pb.cost = reinterpret_cast<uint8_t*>(base + l.cost);
-  pb.cmin = reinterpret_cast<uint8_t*>(base + l.cmin);
   pb.ord = vol_order_for(D);
   pb.agg = base + l.agg;
   pb.dl = reinterpret_cast<uint16_t*>(base + l.dl);

@@ -23,7 +23,7 @@
 namespace r2t {
 
 // Default pixels per block of the WTA / right-disparity stage (T * D * 2 B of shared memory).
-__host__ __device__ inline int wta_tile_px(int D) { return D > 128 ? 64 : 128; }
+__host__ __device__ inline int wta_tile_px(int D) { return D > 128 ? 128 : 256; }
 __host__ __device__ inline size_t wta_smem_bytes(int D, int T) { return (size_t)T * D * 2; }
 __host__ __device__ inline int wta_items(int W, int H, int T) { return H * ((W + T - 1) / T); }
 
@@ -37,8 +37,11 @@ __device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint16_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   // stage S of pixels [x0, x0 + n) in natural disparity order
   const int vpp = D / 8;  // 8-element vectors per pixel
+  // exact v / vpp for v < 2^16: multiply by ceil(2^32 / vpp), keep the high word
+  const uint32_t inv = (uint32_t)((0xFFFFFFFFull + vpp) / vpp);
   for (int v = threadIdx.x; v < n * vpp; v += blockDim.x) {
-    const int px = v / vpp, p8 = (v - px * vpp) * 8;  // first element position of the vector
+    const int px = (int)__umulhi((uint32_t)v, inv);
+    const int p8 = (v - px * vpp) * 8;  // first element position of the vector
     const int64_t e = (rowbase + x0 + px) * D + p8;
     uint32_t w[4];
     if (WIDE) {
@@ -52,7 +55,7 @@ __device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint16_
       w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
     }
     uint16_t* dst = sm + px * D;
-    const int d0 = vol_index(p8, pb.ord, 4), d1 = vol_index(p8 + 4, pb.ord, 4);
+    const int d0 = vol_index(p8, pb.ord, 2), d1 = vol_index(p8 + 4, pb.ord, 2);
     *reinterpret_cast<uint2*>(dst + d0) = make_uint2(w[0], w[1]);
     *reinterpret_cast<uint2*>(dst + d1) = make_uint2(w[2], w[3]);
   }
