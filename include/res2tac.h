@@ -80,8 +80,8 @@ typedef struct res2tac_pair {
 /* Kernel configuration of a context. Every valid setting gives bit-identical results; only the
  * speed differs. agg_dpl: disparities per lane of the aggregation kernel (0 = automatic, else
  * 2, 4 or 8 with D / agg_dpl <= 32). agg_warps: warps per aggregation block (1..16).
- * wta_chunk: pixels per block of the winner-takes-all / right-disparity kernel (32, 64, 128 or
- * 256 with wta_chunk * D * 2 <= 96 KiB; 0 = automatic). */
+ * wta_chunk: pixels (= threads) per block of the winner-takes-all / right-disparity kernel
+ * (64, 128 or 256; 0 = automatic). */
 typedef struct res2tac_tuning {
   int32_t agg_dpl;
   int32_t agg_warps;

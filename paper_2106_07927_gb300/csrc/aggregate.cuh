@@ -103,9 +103,9 @@ __host__ __device__ inline int long_lanes(int D, int dpl) {
 }
 __host__ __device__ inline int bulk_width(int D) { return pow2ceil(D / bulk_dpl(D)); }
 
-// Steps of register prefetch in the long-axis kernel, and of the per-lane cp.async ring in the
-// other-axes kernel (one commit group per step, waited with cp.async.wait_group 3).
-constexpr int kBulkRing = 4;
+// Slots (steps) of the per-lane cp.async ring of the other-axes kernel. Two steps form one commit
+// group and each pair of steps waits with cp.async.wait_group 3, so six steps are in flight.
+constexpr int kBulkRing = 8;
 __host__ __device__ inline int bulk_ring_bytes(int dpl) { return kBulkRing * (dpl / 16) * 32 * 16; }
 
 // Adds 4 packed u16 sums (2 registers) into S at element e (uint16 or, when wide, uint32).
@@ -237,6 +237,52 @@ __device__ __forceinline__ void long_step(uint32_t (&L)[DPL / 2], uint32_t& mm,
   mm = vmin2(aa - mm, cc + P2P2);
 }
 
+// The same step for the two chains of a line, written stage by stage (neighbour shuffles of both,
+// arithmetic of both, group minima of both, updates of both) so that one chain's shuffle and
+// redux latencies overlap the other chain's work.
+template <int DPL, int LPL, bool FULL>
+__device__ __forceinline__ void long_step2(uint32_t (&Lf)[DPL / 2], uint32_t& mf,
+                                           const uint32_t (&cf)[DPL / 2], uint32_t (&Lb)[DPL / 2],
+                                           uint32_t& mb, const uint32_t (&cb)[DPL / 2],
+                                           bool active, int lig, uint32_t P1P1, uint32_t P2P2) {
+  constexpr int NP = DPL / 2;
+  uint32_t Xf[NP + 1], Xb[NP + 1];
+  neighbours<NP, LPL>(Lf, lig, Xf);
+  neighbours<NP, LPL>(Lb, lig, Xb);
+  uint32_t hf[NP], hb[NP];
+  uint32_t hminf = 0xFFFFFFFFu, cminf = 0xFFFFFFFFu, hminb = 0xFFFFFFFFu, cminb = 0xFFFFFFFFu;
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    hf[k] = vmin2(Lf[k], vmin2(Xf[k], Xf[k + 1]) + P1P1) + cf[k];
+    hb[k] = vmin2(Lb[k], vmin2(Xb[k], Xb[k + 1]) + P1P1) + cb[k];
+    hminf = vmin2(hminf, hf[k]);
+    hminb = vmin2(hminb, hb[k]);
+    cminf = vmin2(cminf, cf[k]);
+    cminb = vmin2(cminb, cb[k]);
+  }
+  hminf = halves_min(hminf);
+  hminb = halves_min(hminb);
+  cminf = halves_min(cminf);
+  cminb = halves_min(cminb);
+  if (!FULL) {
+    hminf = active ? hminf : 0xFFFFFFFFu;
+    hminb = active ? hminb : 0xFFFFFFFFu;
+    cminf = active ? cminf : 0xFFFFFFFFu;
+    cminb = active ? cminb : 0xFFFFFFFFu;
+  }
+  const uint32_t aaf = group_min<LPL>(hminf), aab = group_min<LPL>(hminb);
+  const uint32_t ccf = group_min<LPL>(cminf), ccb = group_min<LPL>(cminb);
+#pragma unroll
+  for (int k = 0; k < NP; k++) {
+    const uint32_t lf = vmin2(hf[k] - mf, cf[k] + P2P2);  // h >= m(q) in both halves
+    const uint32_t lb = vmin2(hb[k] - mb, cb[k] + P2P2);
+    Lf[k] = (FULL || active) ? lf : kSent * 0x10001u;
+    Lb[k] = (FULL || active) ? lb : kSent * 0x10001u;
+  }
+  mf = vmin2(aaf - mf, ccf + P2P2);
+  mb = vmin2(aab - mb, ccb + P2P2);
+}
+
 // Lines [line0, min(line0 + 32 / LPL, line_end)) of the long axis, both directions each.
 // FULL: every lane of a group owns disparities (D == LPL * DPL). Costs are loaded U steps ahead
 // into a register ring that each step refills in place.
@@ -292,11 +338,10 @@ __device__ __forceinline__ void agg_long_lines(const Problem& pb, const Method& 
     for (int u = 0; u < U; u++) {
       const int t = t0 + u;
       if (t >= len) break;
-      uint32_t c[NP];
-      RC::unpack(rf[u], c);
-      long_step<DPL, LPL, FULL>(Lf, mf, c, active, lig, P1P1, P2P2);
-      RC::unpack(rb[u], c);
-      long_step<DPL, LPL, FULL>(Lb, mb, c, active, lig, P1P1, P2P2);
+      uint32_t c1[NP], c2[NP];
+      RC::unpack(rf[u], c1);
+      RC::unpack(rb[u], c2);
+      long_step2<DPL, LPL, FULL>(Lf, mf, c1, Lb, mb, c2, active, lig, P1P1, P2P2);
       // refill this slot with step t + U (the pointers sit there already)
       const bool ok = active && t + U < len;
       rf[u] = ok ? RC::load(cf) : Raw();
@@ -371,17 +416,22 @@ __device__ __forceinline__ void agg_bulk_chains(const Problem& pb, const Method&
   for (int k = 0; k < NP; k++) L[k] = active ? 0u : kSent * 0x10001u;
   uint32_t mm = 0;
 
-  // prologue: steps 0 .. KS - 2 in flight, one commit group each
-#pragma unroll
-  for (int s = 0; s < KS - 1; s++) {
+  // copies step s into its ring slot (s % KS) and moves the copy pointer on
+  auto copy_step = [&](int s) {
     if (active && s < g.len) {
 #pragma unroll
       for (int v = 0; v < NV; v++)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                         sbase + (uint32_t)(((s * NV + v) * 32 + lane) * 16)),
+                         sbase + (uint32_t)((((s % KS) * NV + v) * 32 + lane) * 16)),
                      "l"(cp + v * cvs));
       if (s + 1 < g.len) cp += estride;
     }
+  };
+  // prologue: steps 0 .. 5 in flight as three groups of two
+#pragma unroll
+  for (int s = 0; s < KS - 2; s += 2) {
+    copy_step(s);
+    copy_step(s + 1);
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
   for (int t0 = 0; t0 < maxlen; t0 += KS) {
@@ -389,16 +439,9 @@ __device__ __forceinline__ void agg_bulk_chains(const Problem& pb, const Method&
     for (int u = 0; u < KS; u++) {
       const int t = t0 + u;
       if (t >= maxlen) break;
-      {  // issue step t + KS - 1 into slot (u + KS - 1) % KS, then wait for step t
-        const int slot = (u + KS - 1) % KS;
-        if (active && t + KS - 1 < g.len) {
-#pragma unroll
-          for (int v = 0; v < NV; v++)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                             sbase + (uint32_t)(((slot * NV + v) * 32 + lane) * 16)),
-                         "l"(cp + v * cvs));
-          if (t + KS < g.len) cp += estride;
-        }
+      if ((u & 1) == 0) {  // issue steps t + 6, t + 7, then wait for steps t, t + 1
+        copy_step(t + KS - 2);
+        copy_step(t + KS - 1);
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 3;" ::: "memory");
       }

@@ -12,7 +12,7 @@ namespace r2t {
 
 constexpr int kCensusTW = 64;  // census tile: 64 x 4 pixels, one per thread
 constexpr int kCensusTH = 4;
-constexpr int kCostTX = 32;    // cost tile: 32 pixels of one row, all D disparities
+constexpr int kCostTX = 128;   // cost tile: 128 pixels of one row, all D disparities
 
 __host__ __device__ inline int census_tiles_x(int W) { return (W + kCensusTW - 1) / kCensusTW; }
 __host__ __device__ inline int census_tiles_y(int H) { return (H + kCensusTH - 1) / kCensusTH; }
@@ -74,11 +74,11 @@ __device__ __forceinline__ void census_tile_dispatch(const Problem& pb, const Me
 }
 
 struct CostSmem {
-  uint64_t r[kCostTX + 256];  // CT_R(x0 - D + 1 .. x0 + 31)
+  uint64_t r[kCostTX + 256];  // CT_R(x0 - D + 1 .. x0 + kCostTX - 1)
   uint64_t l[kCostTX];
 };
 
-// One row segment of 32 pixels, all disparities, written as 4-byte words (4 consecutive
+// One row segment of kCostTX pixels, all disparities, written as 4-byte words (4 consecutive
 // disparities stay consecutive in the volume's order, which moves chunks of 16). The same tile of
 // the aggregated volume is cleared here (16-byte stores) and the tile's right-disparity keys are
 // set to their maximum, so the later stages can add / atomicMin into them without separate memset

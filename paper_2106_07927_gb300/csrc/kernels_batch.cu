@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) batch_bulk_kernel(const BatchHeader* hd, 
 template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, const Problem* probs,
                                                         const int* prefix, unsigned* counters) {
-  extern __shared__ __align__(16) uint16_t wsm[];
+  extern __shared__ __align__(16) uint32_t wkeys[];
   __shared__ int s_item;
   const int total = hd->total[kStWta], n = hd->n;
   for (;;) {
@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, c
     if (item >= total) break;
     const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
-    wta_dr_tile<WIDE>(pb, item - prefix[p], wsm, wta_tile_px(pb.D));
+    wta_dr_tile<WIDE>(pb, item - prefix[p], wkeys, 256);
   }
 }
 

@@ -33,8 +33,8 @@ __global__ void __launch_bounds__(512) agg_bulk_kernel(Problem pb, Method mt) {
 
 template <bool WIDE>
 __global__ void __launch_bounds__(256) wta_dr_kernel(Problem pb, int T) {
-  extern __shared__ __align__(16) uint16_t wsm[];
-  wta_dr_tile<WIDE>(pb, blockIdx.x, wsm, T);
+  extern __shared__ __align__(16) uint32_t wkeys[];
+  wta_dr_tile<WIDE>(pb, blockIdx.x, wkeys, T);
 }
 
 __global__ void __launch_bounds__(256) lr_median_kernel(Problem pb, Method mt) {
@@ -76,9 +76,7 @@ bool tuning_valid(const Tuning& t, int D) {
   if (D % t.agg_dpl != 0) return false;
   if ((D + t.agg_dpl - 1) / t.agg_dpl > 32) return false;
   if (t.agg_warps < 1 || t.agg_warps > 16) return false;
-  if (t.wta_chunk != 32 && t.wta_chunk != 64 && t.wta_chunk != 128 && t.wta_chunk != 256)
-    return false;
-  if (wta_smem_bytes(D, t.wta_chunk) > 96 * 1024) return false;
+  if (t.wta_chunk != 64 && t.wta_chunk != 128 && t.wta_chunk != 256) return false;
   return true;
 }
 
@@ -197,15 +195,12 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
   if ((e = launch_aggregate(pb, mt, tn, s, fork)) != cudaSuccess) return e;
   n += 2;
   if (ev) cudaEventRecord(ev[3], s);
-  const int T = tn.wta_chunk;
+  const int T = tn.wta_chunk;  // one thread per pixel
   const size_t smem = wta_smem_bytes(pb.D, T);
-  if (mt.wide) {
-    cudaFuncSetAttribute(wta_dr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    wta_dr_kernel<true><<<wta_items(pb.W, pb.H, T), 256, smem, s>>>(pb, T);
-  } else {
-    cudaFuncSetAttribute(wta_dr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    wta_dr_kernel<false><<<wta_items(pb.W, pb.H, T), 256, smem, s>>>(pb, T);
-  }
+  if (mt.wide)
+    wta_dr_kernel<true><<<wta_items(pb.W, pb.H, T), T, smem, s>>>(pb, T);
+  else
+    wta_dr_kernel<false><<<wta_items(pb.W, pb.H, T), T, smem, s>>>(pb, T);
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[4], s);

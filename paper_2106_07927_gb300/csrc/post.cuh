@@ -1,15 +1,13 @@
 // Disparity selection and post-processing, Sec. 2.1.2 - 2.1.3, as block-level routines.
 //
-// wta_dr_tile: one block reads the aggregated vectors S(x, .) of T consecutive pixels of a row
-// (each element of S is read from memory once, with 16-byte loads) and computes
+// wta_dr_tile: for T consecutive pixels of a row, one thread per pixel reads that pixel's
+// aggregated vector S(x, .) once (16-byte loads) and computes
 //   D^L(x) = smallest d with the least S(x, d)                                  Eq. (wta)
-// for those pixels, and its share of
+// as a running minimum, and its share of
 //   D^R(x) = smallest d <= min(D-1, W-1-x) with the least S(x + d, d)          Eq. (right_disparity)
-// for every target x whose sources x + d fall into the tile. The paper gathers S for D^R with
-// strided, uncoalesced reads (Sec. 2.2.3); here every source is read once and its keys are
-// scattered to its targets: targets whose D sources all lie in the tile get a plain store, the
-// others (at most D - 1 per tile side) an atomicMin. Keys are S << 8 | d, so the minimum key
-// carries the least S and, among equal S, the smallest d.
+// for every target x' = x - d. The paper gathers S for D^R with strided, uncoalesced reads
+// (Sec. 2.2.3); here every source is read once and each of its keys is scattered to its target.
+// Keys are S << 8 | d, so the minimum key carries the least S and, among equal S, the smallest d.
 //
 // lr_median_tile: the left-right check of Eq. (LR_check) (App. B) for a tile and its 1-pixel
 // frame, then the 3x3 median of the valid pixels (Sec. 2.1.3): element [4] of the nine sorted
@@ -22,68 +20,74 @@
 
 namespace r2t {
 
-// Default pixels per block of the WTA / right-disparity stage (T * D * 2 B of shared memory).
-__host__ __device__ inline int wta_tile_px(int D) { return D > 128 ? 128 : 256; }
-__host__ __device__ inline size_t wta_smem_bytes(int D, int T) { return (size_t)T * D * 2; }
+// Pixels per block of the WTA / right-disparity stage: one thread per pixel.
+__host__ __device__ inline int wta_tile_px(int D) { return 256; }
+// Shared memory: one key per target pixel of the tile, T + D - 1 of them.
+__host__ __device__ inline size_t wta_smem_bytes(int D, int T) { return (size_t)(T + D - 1) * 4; }
 __host__ __device__ inline int wta_items(int W, int H, int T) { return H * ((W + T - 1) / T); }
 
+// One thread walks the D sums of one source pixel x' once: a running minimum of the keys gives
+// D^L(x'), and every key S(x', d) << 8 | d is offered to target x' - d with a shared-memory
+// atomicMin (the 32 lanes of a warp hit 32 consecutive targets, so no bank conflict). Targets whose
+// sources all lie in the tile are then stored, the others (at most D - 1 per tile side) merged with
+// a global atomicMin. T must equal blockDim.x.
 template <bool WIDE>
-__device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint16_t* sm, int T) {
+__device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint32_t* keys, int T) {
   const int W = pb.W, D = pb.D;
   const int ntx = (W + T - 1) / T;
-  const int y = item / ntx, x0 = (item % ntx) * T;
+  const int y = item / ntx, x0 = (item - y * ntx) * T;
   const int n = min(T, W - x0);
   const int64_t rowbase = (int64_t)y * W;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  // stage S of pixels [x0, x0 + n) in natural disparity order
-  const int vpp = D / 8;  // 8-element vectors per pixel
-  // exact v / vpp for v < 2^16: multiply by ceil(2^32 / vpp), keep the high word
-  const uint32_t inv = (uint32_t)((0xFFFFFFFFull + vpp) / vpp);
-  for (int v = threadIdx.x; v < n * vpp; v += blockDim.x) {
-    const int px = (int)__umulhi((uint32_t)v, inv);
-    const int p8 = (v - px * vpp) * 8;  // first element position of the vector
-    const int64_t e = (rowbase + x0 + px) * D + p8;
-    uint32_t w[4];
-    if (WIDE) {
-      const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const uint32_t*>(pb.agg) + e);
-      const uint4 a = src[0], b = src[1];
-      const uint32_t s[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  const int ntar = T + D - 1;  // targets x0 - D + 1 .. x0 + T - 1
+  for (int i = threadIdx.x; i < ntar; i += blockDim.x) keys[i] = 0xFFFFFFFFu;
+  __syncthreads();
+  const int px = threadIdx.x;
+  if (px < n) {
+    const int x = x0 + px;
+    uint32_t* kt = keys + (px + D - 1);  // kt[-d] is the key of target x - d
+    uint32_t kl = 0xFFFFFFFFu;
+    const bool edge = x < D - 1;  // some targets x - d fall left of the image
+    for (int c = 0; c < D / 8; c++) {
+      uint32_t w[4];  // 8 sums at positions 8c .. 8c + 7, saturated to 16 bits
+      if (WIDE) {
+        const uint4* src =
+            reinterpret_cast<const uint4*>(reinterpret_cast<const uint32_t*>(pb.agg) + (rowbase + x) * D + 8 * c);
+        const uint4 a = __ldg(src), b = __ldg(src + 1);
+        const uint32_t s[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
 #pragma unroll
-      for (int j = 0; j < 4; j++) w[j] = min(s[2 * j], 65535u) | (min(s[2 * j + 1], 65535u) << 16);
-    } else {
-      const uint4 a = *reinterpret_cast<const uint4*>(reinterpret_cast<const uint16_t*>(pb.agg) + e);
-      w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+        for (int j = 0; j < 4; j++) w[j] = min(s[2 * j], 65535u) | (min(s[2 * j + 1], 65535u) << 16);
+      } else {
+        const uint4 a = __ldg(reinterpret_cast<const uint4*>(
+            reinterpret_cast<const uint16_t*>(pb.agg) + (rowbase + x) * D + 8 * c));
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int d0 = vol_index(8 * c + 4 * h, pb.ord, 2);  // 4 consecutive disparities
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+          const uint32_t s = (j & 1) ? (w[2 * h + j / 2] >> 16) : (w[2 * h + j / 2] & 0xFFFFu);
+          const int d = d0 + j;
+          const uint32_t key = (s << 8) | (uint32_t)d;
+          kl = min(kl, key);
+          if (!edge || d <= x) atomicMin(kt - d, key);
+        }
+      }
     }
-    uint16_t* dst = sm + px * D;
-    const int d0 = vol_index(p8, pb.ord, 2), d1 = vol_index(p8 + 4, pb.ord, 2);
-    *reinterpret_cast<uint2*>(dst + d0) = make_uint2(w[0], w[1]);
-    *reinterpret_cast<uint2*>(dst + d1) = make_uint2(w[2], w[3]);
+    pb.dl[rowbase + x] = (uint16_t)(kl & 0xFFu);
   }
   __syncthreads();
-  for (int px = warp; px < n; px += nwarps) {
-    const uint16_t* s = sm + px * D;
-    uint32_t k = 0xFFFFFFFFu;
-    for (int d = lane; d < D; d += 32) k = min(k, ((uint32_t)s[d] << 8) | (uint32_t)d);
-    k = __reduce_min_sync(0xffffffffu, k);
-    if (lane == 0) pb.dl[rowbase + x0 + px] = (uint16_t)(k & 0xFF);
-  }
-  // targets x in [x0 - D + 1, x0 + n) intersected with the image
-  const int tlo = max(0, x0 - D + 1);
-  for (int x = tlo + warp; x < x0 + n; x += nwarps) {
-    uint32_t k = 0xFFFFFFFFu;
-    for (int d = lane; d < D; d += 32) {
-      const int src = x + d - x0;
-      if (src >= 0 && src < n) k = min(k, ((uint32_t)sm[src * D + d] << 8) | (uint32_t)d);
-    }
-    k = __reduce_min_sync(0xffffffffu, k);
-    if (lane == 0) {
-      // all sources of x inside this tile: x >= x0 and min(x + D - 1, W - 1) < x0 + n
-      const bool whole = x >= x0 && min(x + D - 1, W - 1) < x0 + n;
-      if (whole)
-        pb.kr[rowbase + x] = k;
-      else if (k != 0xFFFFFFFFu)
-        atomicMin(&pb.kr[rowbase + x], k);
-    }
+  for (int i = threadIdx.x; i < ntar; i += blockDim.x) {
+    const int x = x0 - D + 1 + i;
+    if (x < 0 || x >= x0 + n) continue;
+    const uint32_t k = keys[i];
+    if (k == 0xFFFFFFFFu) continue;
+    // all sources x .. min(x + D - 1, W - 1) of this target lie in the tile
+    const bool whole = x >= x0 && min(x + D - 1, W - 1) < x0 + n;
+    if (whole)
+      pb.kr[rowbase + x] = k;
+    else
+      atomicMin(&pb.kr[rowbase + x], k);
   }
   __syncthreads();
 }

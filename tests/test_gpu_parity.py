@@ -112,7 +112,7 @@ def test_every_tuning_is_bit_identical():
     n = 0
     for dpl in (4, 8):
         for warps in (1, 4, 8):
-            for chunk in (32, 128, 256):
+            for chunk in (64, 128, 256):
                 t = binding.res2tac_tuning(dpl, warps, chunk, 0)
                 out, got = _gpu(left, right, prm, tuning=t)
                 assert np.array_equal(out, ref), (dpl, warps, chunk)
