@@ -78,14 +78,22 @@ typedef struct res2tac_pair {
 } res2tac_pair;
 
 /* Kernel configuration of a context. Every valid setting gives bit-identical results; only the
- * speed differs. agg_dpl: disparities per lane of the aggregation kernel (0 = automatic, else
- * 2, 4 or 8 with D / agg_dpl <= 32). agg_warps: warps per aggregation block (1..16).
- * wta_chunk: pixels (= threads) per block of the winner-takes-all / right-disparity kernel
- * (64, 128 or 256; 0 = automatic). */
+ * speed differs; 0 in a field selects its automatic value.
+ * agg_dpl: disparities per lane of the row-path kernel (LR, RL): 2, 4 or 8 with
+ *   D / agg_dpl <= 32.
+ * agg_warps: warps per block of both aggregation kernels (1..16).
+ * wta_chunk: pixels per block of the winner-takes-all / right-disparity kernel (64, 128 or
+ *   256; one warp per pixel at a time).
+ * shear_dpl: disparities per lane of the column / diagonal path kernel: 16, or 32 when
+ *   D % 32 == 0.
+ * row_mode: 1 = both directions of a row in one lane group, 2 = one direction per group.
+ * reserved: set to 0. */
 typedef struct res2tac_tuning {
   int32_t agg_dpl;
   int32_t agg_warps;
   int32_t wta_chunk;
+  int32_t shear_dpl;
+  int32_t row_mode;
   int32_t reserved;
 } res2tac_tuning;
 

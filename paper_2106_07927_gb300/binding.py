@@ -48,7 +48,8 @@ class res2tac_pair(ctypes.Structure):
 
 
 class res2tac_tuning(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int32) for n in ("agg_dpl", "agg_warps", "wta_chunk", "reserved")]
+    _fields_ = [(n, ctypes.c_int32) for n in ("agg_dpl", "agg_warps", "wta_chunk", "shear_dpl",
+                                               "row_mode", "reserved")]
 
 
 class Res2tacError(RuntimeError):

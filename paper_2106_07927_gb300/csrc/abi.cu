@@ -231,6 +231,8 @@ int res2tac_get_tuning(res2tac_t h, res2tac_tuning* t) {
   t->agg_dpl = h->tuning.agg_dpl;
   t->agg_warps = h->tuning.agg_warps;
   t->wta_chunk = h->tuning.wta_chunk;
+  t->shear_dpl = h->tuning.shear_dpl;
+  t->row_mode = h->tuning.row_split ? 2 : 1;
   t->reserved = 0;
   return RES2TAC_OK;
 }
@@ -241,9 +243,12 @@ int res2tac_set_tuning(res2tac_t h, const res2tac_tuning* t) {
   if (t->agg_dpl) n.agg_dpl = t->agg_dpl;
   if (t->agg_warps) n.agg_warps = t->agg_warps;
   if (t->wta_chunk) n.wta_chunk = t->wta_chunk;
+  if (t->shear_dpl) n.shear_dpl = t->shear_dpl;
+  if (t->row_mode) n.row_split = t->row_mode == 2 ? 1 : (t->row_mode == 1 ? 0 : -1);
   if (!r2t::tuning_valid(n, h->p.max_disp))
-    return fail(RES2TAC_EINVAL, "tuning (dpl %d, warps %d, chunk %d) invalid for D = %d",
-                n.agg_dpl, n.agg_warps, n.wta_chunk, h->p.max_disp);
+    return fail(RES2TAC_EINVAL,
+                "tuning (dpl %d, warps %d, chunk %d, shear dpl %d, row mode %d) invalid for D = %d",
+                n.agg_dpl, n.agg_warps, n.wta_chunk, n.shear_dpl, t->row_mode, h->p.max_disp);
   h->tuning = n;
   return RES2TAC_OK;
 }
@@ -256,12 +261,15 @@ int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int
   cudaStream_t st = (cudaStream_t)s;
   std::vector<r2t::Tuning> cands;
   const int dpls[3] = {2, 4, 8}, warps[3] = {2, 4, 8}, chunks[3] = {64, 128, 256};
+  const int sdpls[2] = {16, 32};
   for (int a : dpls)
     for (int w : warps)
-      for (int c : chunks) {
-        r2t::Tuning t{a, w, c};
-        if (r2t::tuning_valid(t, h->p.max_disp)) cands.push_back(t);
-      }
+      for (int c : chunks)
+        for (int sd : sdpls)
+          for (int split = 0; split < 2; split++) {
+            r2t::Tuning t{a, w, c, sd, split};
+            if (r2t::tuning_valid(t, h->p.max_disp)) cands.push_back(t);
+          }
   if (cands.empty()) return fail(RES2TAC_EINVAL, "no valid tuning");
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

@@ -1,0 +1,7 @@
+// Row-path aggregation kernels (LR, RL) with uint32 sums, plain and batch variants.
+#include "agg_units.cuh"
+
+namespace r2t {
+template cudaError_t launch_rows<true>(const Problem&, const Method&, const Tuning&, cudaStream_t);
+template const void* batch_row_kernel_fn<true>();
+}  // namespace r2t

@@ -8,105 +8,40 @@
 // value fits 16 bits. S(p,d) = sum_r L_r(p,d), saturated at 65535.
 //
 // GB300 mapping (not the paper's). Every path line is a sequential chain; a group of lanes walks
-// one line with the D disparities spread over its lanes, held as packed u16x2 registers.
-// Neighbouring disparities cross lanes by one shuffle each way; the line's costs are added into
-// S with 64-bit atomic adds of four packed u16 lanes (no carry can cross a lane while
-// num_paths (255 + P2) <= 65535; above that the sums are uint32, "wide"). Integer addition is
-// associative, so the order in which directions arrive does not change S.
-// Two kernels split the lines:
-//  - the long axis (rows when W >= H, else columns) holds the longest chains, which bound the
-//    kernel's duration. One warp walks a line in both directions (two chains for ILP) with few
-//    disparities per lane, and forms m with a pipelined reduction: writing
+// one chain with the D disparities spread over its lanes, held as packed u16x2 registers.
+// Neighbouring disparities cross lanes by one shuffle each way. S is accumulated with 64-bit
+// atomic adds of four packed u16 sums: no carry can cross a half while num_paths (255 + P2) <=
+// 65535; above that the sums are uint32 ("wide"). Integer addition is associative, so the order
+// in which directions arrive does not change S. Two kernels split the paths:
+//  - rows (LR, RL), the longest chains when W >= H. A group of 8..32 lanes walks a row with 2..8
+//    disparities per lane, either both directions interleaved (two chains for ILP) or one
+//    direction per group, and forms m with a pipelined reduction: writing
 //    g(q,d) = min(L(q,d), L(q,d-1) + P1, L(q,d+1) + P1) and h(p,d) = C(p,d) + g(q,d),
 //      L(p,d) = min(h(p,d) - m(q), C(p,d) + P2),
 //      m(p)   = min(min_d h(p,d) - m(q), min_d C(p,d) + P2),
 //    so the group minima of h and of C (redux.sync) do not wait for m(q) and overlap the next
-//    step.
-//  - the other axes (short lines, many of them) run one chain per small lane group with 32
-//    disparities per lane, which amortises shuffles and reductions over much more arithmetic.
-// Costs are fetched several steps ahead (registers in the first kernel, a per-lane cp.async ring
-// in shared memory in the second). The cost and S vectors use a blocked disparity order
-// (VolOrder) matched to the second kernel, so each lane group's copies and atomic adds touch
-// contiguous memory in both kernels.
+//    step. Costs are fetched several steps ahead into a register ring.
+//  - sheared columns (TB, BT and, with 8 paths, the four diagonals). Each such path is walked row
+//    by row as W sheared chains of length H (see agg_shear), so the chains of one warp sit on
+//    adjacent pixels at every step. Lane groups hold 16 or 32 disparities per lane; the warp's
+//    cost vectors of a step (adjacent, so contiguous in memory) are copied into a shared-memory
+//    ring with cp.async several steps ahead, and its new L values are staged in shared memory and
+//    added to S by coalesced atomic adds that each cover whole pixel vectors.
 #pragma once
 #include "common.cuh"
 
 namespace r2t {
 
-struct LineGeom {
-  int sx, sy, dx, dy, len;
-};
-
-// Axes: 0 rows (LR/RL), 1 columns (TB/BT), 2 diagonals x - y = const (TLBR/BRTL),
-// 3 anti-diagonals x + y = const (TRBL/BLTR). Line i of an axis, walked forward.
-__host__ __device__ inline int axis_lines(int axis, int W, int H) {
-  return axis == 0 ? H : (axis == 1 ? W : W + H - 1);
-}
-__host__ __device__ inline LineGeom axis_line(int axis, int i, int W, int H) {
-  LineGeom g;
-  if (axis == 0) {
-    g.sx = 0; g.sy = i; g.dx = 1; g.dy = 0; g.len = W;
-  } else if (axis == 1) {
-    g.sx = i; g.sy = 0; g.dx = 0; g.dy = 1; g.len = H;
-  } else if (axis == 2) {
-    const int k = i - (H - 1);
-    g.sx = k > 0 ? k : 0;
-    g.sy = k < 0 ? -k : 0;
-    g.dx = 1; g.dy = 1;
-    g.len = (W - g.sx) < (H - g.sy) ? (W - g.sx) : (H - g.sy);
-  } else {
-    g.sy = i - (W - 1) > 0 ? i - (W - 1) : 0;
-    g.sx = i - g.sy;
-    g.dx = -1; g.dy = 1;
-    g.len = (g.sx + 1) < (H - g.sy) ? (g.sx + 1) : (H - g.sy);
-  }
-  return g;
-}
-__host__ __device__ inline int long_axis(int W, int H) { return W >= H ? 0 : 1; }
-// Axes of the second kernel: the other straight axis, plus both diagonals with 8 paths.
-__host__ __device__ inline int bulk_axes(int W, int H, int num_paths, int (&axes)[3]) {
-  axes[0] = 1 - long_axis(W, H);
-  if (num_paths == 8) {
-    axes[1] = 2;
-    axes[2] = 3;
-    return 3;
-  }
-  return 1;
-}
-__host__ __device__ inline int bulk_num_lines(int W, int H, int num_paths) {
-  int axes[3];
-  const int na = bulk_axes(W, H, num_paths, axes);
-  int n = 0;
-  for (int a = 0; a < na; a++) n += axis_lines(axes[a], W, H);
-  return n;
-}
-__host__ __device__ inline LineGeom bulk_line(int li, int W, int H, int num_paths) {
-  int axes[3];
-  const int na = bulk_axes(W, H, num_paths, axes);
-  for (int a = 0; a < na; a++) {
-    const int n = axis_lines(axes[a], W, H);
-    if (li < n) return axis_line(axes[a], li, W, H);
-    li -= n;
-  }
-  LineGeom g;
-  g.sx = g.sy = g.dx = g.dy = g.len = 0;
-  return g;
-}
-
-// Kernel configurations for D disparities. Long axis: dpl in {2, 4, 8}, lanes = next power of
-// two >= D / dpl (at least 8). Other axes: bulk_dpl(D) disparities per lane, group width = next
-// power of two >= D / dpl.
+// Row kernel configuration for D disparities: dpl in {2, 4, 8}, lanes = next power of two
+// >= D / dpl (at least 8).
 __host__ __device__ inline int long_dpl_default(int D) { return D <= 64 ? 2 : (D <= 128 ? 4 : 8); }
 __host__ __device__ inline int long_lanes(int D, int dpl) {
   const int l = pow2ceil((D + dpl - 1) / dpl);
   return l < 8 ? 8 : l;
 }
-__host__ __device__ inline int bulk_width(int D) { return pow2ceil(D / bulk_dpl(D)); }
-
-// Slots (steps) of the per-lane cp.async ring of the other-axes kernel. Two steps form one commit
-// group and each pair of steps waits with cp.async.wait_group 3, so six steps are in flight.
-constexpr int kBulkRing = 8;
-__host__ __device__ inline int bulk_ring_bytes(int dpl) { return kBulkRing * (dpl / 16) * 32 * 16; }
+// Work units of the row kernel of one pair: rows (both directions per lane group) or chains
+// (one direction per lane group, chain 2 y walks row y left to right, chain 2 y + 1 back).
+__host__ __device__ inline int row_units(int H, bool split) { return split ? 2 * H : H; }
 
 // Adds 4 packed u16 sums (2 registers) into S at element e (uint16 or, when wide, uint32).
 template <bool WIDE>
@@ -128,6 +63,17 @@ __device__ __forceinline__ void add2(void* agg, int64_t e, uint32_t a) {
   else
     atomicAdd(reinterpret_cast<unsigned long long*>(reinterpret_cast<uint32_t*>(agg) + e),
               (unsigned long long)(a & 0xFFFFu) | ((unsigned long long)(a >> 16) << 32));
+}
+// A lane's DPL consecutive sums, starting at element e.
+template <int DPL, bool WIDE>
+__device__ __forceinline__ void add_lane(void* agg, int64_t e, const uint32_t (&L)[DPL / 2]) {
+  constexpr int NP = DPL / 2;
+  if (DPL == 2) {
+    add2<WIDE>(agg, e, L[0]);
+  } else {
+    add4<WIDE>(agg, e, L[0], L[1 % NP]);
+    if (DPL == 8) add4<WIDE>(agg, e + 4, L[2 % NP], L[3 % NP]);
+  }
 }
 
 template <int DPL>
@@ -177,13 +123,29 @@ __device__ __forceinline__ uint32_t halves_min(uint32_t v) {
   return vmin2(v, __byte_perm(v, v, 0x1032));
 }
 
-// Minimum over a group of LPL lanes of a value whose halves are equal.
+// Minimum over a group of LPL lanes (aligned, LPL a power of two) of a value whose halves are
+// equal. A whole warp uses redux.sync. Smaller groups use xor shuffles in radix-4 rounds (three
+// independent shuffles per round), so a group of 8 or 16 lanes needs two shuffle latencies instead
+// of three or four. A redux.sync with a different member mask per group measured about 15 times
+// slower than a full-warp one and is not used.
 template <int LPL>
 __device__ __forceinline__ uint32_t group_min(uint32_t v) {
-  if (LPL == 32) return __reduce_min_sync(0xffffffffu, v);
+  if constexpr (LPL == 32) {
+    return __reduce_min_sync(0xffffffffu, v);
+  } else {
 #pragma unroll
-  for (int o = LPL / 2; o >= 1; o >>= 1) v = vmin2(v, __shfl_xor_sync(0xffffffffu, v, o, LPL));
-  return v;
+    for (int a = 1; a < LPL; a *= 4) {
+      if (4 * a <= LPL) {
+        const uint32_t v1 = __shfl_xor_sync(0xffffffffu, v, a, LPL);
+        const uint32_t v2 = __shfl_xor_sync(0xffffffffu, v, 2 * a, LPL);
+        const uint32_t v3 = __shfl_xor_sync(0xffffffffu, v, 3 * a, LPL);
+        v = vmin2(vmin2(v, v1), vmin2(v2, v3));
+      } else {
+        v = vmin2(v, __shfl_xor_sync(0xffffffffu, v, a, LPL));
+      }
+    }
+    return v;
+  }
 }
 
 // (L(d0 - 1), L(d0)) for every pair k of a lane, from the lane's registers and its neighbours.
@@ -202,7 +164,7 @@ __device__ __forceinline__ void neighbours(const uint32_t (&L)[NP], int lig, uin
   X[NP] = __byte_perm(L[NP - 1], dn, 0x5432);
 }
 
-// ------------------------------------------------------------------------------- long axis
+// ------------------------------------------------------------------------------- rows
 // One pipelined step. In: L = L(q, .), mm = m(q) in both halves, c = C(p, .). Out: L(p, .),
 // m(p) in both halves.
 template <int DPL, int LPL, bool FULL>
@@ -237,7 +199,7 @@ __device__ __forceinline__ void long_step(uint32_t (&L)[DPL / 2], uint32_t& mm,
   mm = vmin2(aa - mm, cc + P2P2);
 }
 
-// The same step for the two chains of a line, written stage by stage (neighbour shuffles of both,
+// The same step for the two chains of a row, written stage by stage (neighbour shuffles of both,
 // arithmetic of both, group minima of both, updates of both) so that one chain's shuffle and
 // redux latencies overlap the other chain's work.
 template <int DPL, int LPL, bool FULL>
@@ -283,12 +245,13 @@ __device__ __forceinline__ void long_step2(uint32_t (&Lf)[DPL / 2], uint32_t& mf
   mb = vmin2(aab - mb, ccb + P2P2);
 }
 
-// Lines [line0, min(line0 + 32 / LPL, line_end)) of the long axis, both directions each.
-// FULL: every lane of a group owns disparities (D == LPL * DPL). Costs are loaded U steps ahead
-// into a register ring that each step refills in place.
-template <int DPL, int LPL, bool WIDE, bool FULL>
-__device__ __forceinline__ void agg_long_lines(const Problem& pb, const Method& mt, int line0,
-                                               int line_end) {
+// Units [unit0, min(unit0 + 32 / LPL, unit_end)) of the row kernel, one per lane group (see
+// row_units). FULL: every lane of a group owns disparities (D == LPL * DPL). Lane member lig owns
+// disparities [lig DPL, (lig + 1) DPL). Costs are loaded U steps ahead into a register ring that
+// each step refills in place.
+template <int DPL, int LPL, bool WIDE, bool FULL, bool SPLIT>
+__device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, int unit0,
+                                         int unit_end) {
   typedef RawCost<DPL> RC;
   typedef typename RC::T Raw;
   constexpr int NP = DPL / 2;
@@ -296,137 +259,256 @@ __device__ __forceinline__ void agg_long_lines(const Problem& pb, const Method& 
   const int lane = threadIdx.x & 31;
   const int lig = lane % LPL;
   const int W = pb.W, H = pb.H, D = pb.D;
-  const int la = long_axis(W, H);
-  const int nl = min(axis_lines(la, W, H), line_end);
-  const int li = line0 + lane / LPL;
-  if (LPL == 32 && li >= nl) return;  // one line per warp: uniform
-  const bool valid = li < nl;
-  const LineGeom g = axis_line(la, valid ? li : 0, W, H);  // every line of the axis has len
-  const int len = g.len;
+  const int nu = min(row_units(H, SPLIT), unit_end);
+  const int ui = unit0 + lane / LPL;
+  if (LPL == 32 && ui >= nu) return;  // one unit per warp: uniform
+  const bool valid = ui < nu;
+  const int y = valid ? (SPLIT ? ui >> 1 : ui) : 0;
   const bool active = FULL ? valid : (valid && lig * DPL < D);
   const int d0 = active ? lig * DPL : 0;
-  const int coff = vol_pos(d0, pb.ord, 4);  // DPL consecutive bytes
-  const int soff0 = vol_pos(d0, pb.ord, 2);  // first 4 (or 2) sums
-  const int soff1 = DPL == 8 ? vol_pos(d0 + 4, pb.ord, 2) - soff0 : 0;
-  const int64_t pstride = (int64_t)g.dy * W + g.dx;  // pixels per step
-  const int64_t estride = pstride * D;                // volume elements per step
-  const int64_t pf = (int64_t)g.sy * W + g.sx;
-  const int64_t pbk = pf + (int64_t)(len - 1) * pstride;
+  const int64_t pl = (int64_t)y * W, pr = pl + W - 1;  // first and last pixel of the row
   const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
-  const uint8_t* cf = pb.cost + pf * D + coff;  // next load of each direction
-  const uint8_t* cb = pb.cost + pbk * D + coff;
-  int64_t ef = pf * D + soff0, eb = pbk * D + soff0;
-
-  uint32_t Lf[NP], Lb[NP];
+  if constexpr (SPLIT) {
+    const bool back = (ui & 1) != 0;
+    const int64_t estride = back ? -(int64_t)D : (int64_t)D;
+    const uint8_t* cp = pb.cost + (back ? pr : pl) * D + d0;  // next load
+    int64_t e = (back ? pr : pl) * D + d0;
+    uint32_t L[NP];
 #pragma unroll
-  for (int k = 0; k < NP; k++) Lf[k] = Lb[k] = active ? 0u : kSent * 0x10001u;
-  uint32_t mf = 0, mb = 0;
-
-  Raw rf[U], rb[U];
-#pragma unroll
-  for (int u = 0; u < U; u++) {
-    const bool ok = active && u < len;
-    rf[u] = ok ? RC::load(cf) : Raw();
-    rb[u] = ok ? RC::load(cb) : Raw();
-    if (u + 1 < len) {
-      cf += estride;
-      cb -= estride;
-    }
-  }
-  for (int t0 = 0; t0 < len; t0 += U) {
+    for (int k = 0; k < NP; k++) L[k] = active ? 0u : kSent * 0x10001u;
+    uint32_t mm = 0;
+    Raw r[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      const int t = t0 + u;
-      if (t >= len) break;
-      uint32_t c1[NP], c2[NP];
-      RC::unpack(rf[u], c1);
-      RC::unpack(rb[u], c2);
-      long_step2<DPL, LPL, FULL>(Lf, mf, c1, Lb, mb, c2, active, lig, P1P1, P2P2);
-      // refill this slot with step t + U (the pointers sit there already)
-      const bool ok = active && t + U < len;
+      r[u] = (active && u < W) ? RC::load(cp) : Raw();
+      if (u + 1 < W) cp += estride;
+    }
+    for (int t0 = 0; t0 < W; t0 += U) {
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int t = t0 + u;
+        if (t >= W) break;
+        uint32_t c[NP];
+        RC::unpack(r[u], c);
+        long_step<DPL, LPL, FULL>(L, mm, c, active, lig, P1P1, P2P2);
+        r[u] = (active && t + U < W) ? RC::load(cp) : Raw();  // step t + U
+        if (t + U + 1 < W) cp += estride;
+        if (active) add_lane<DPL, WIDE>(pb.agg, e, L);
+        e += estride;
+      }
+    }
+  } else {
+    const int64_t estride = D;
+    const uint8_t* cf = pb.cost + pl * D + d0;  // next load of each direction
+    const uint8_t* cb = pb.cost + pr * D + d0;
+    int64_t ef = pl * D + d0, eb = pr * D + d0;
+    uint32_t Lf[NP], Lb[NP];
+#pragma unroll
+    for (int k = 0; k < NP; k++) Lf[k] = Lb[k] = active ? 0u : kSent * 0x10001u;
+    uint32_t mf = 0, mb = 0;
+    Raw rf[U], rb[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const bool ok = active && u < W;
       rf[u] = ok ? RC::load(cf) : Raw();
       rb[u] = ok ? RC::load(cb) : Raw();
-      if (t + U + 1 < len) {
+      if (u + 1 < W) {
         cf += estride;
         cb -= estride;
       }
-      if (active) {
-        if (DPL == 2) {
-          add2<WIDE>(pb.agg, ef, Lf[0]);
-          add2<WIDE>(pb.agg, eb, Lb[0]);
-        } else {
-          add4<WIDE>(pb.agg, ef, Lf[0], Lf[1 % NP]);
-          add4<WIDE>(pb.agg, eb, Lb[0], Lb[1 % NP]);
-          if (DPL == 8) {
-            add4<WIDE>(pb.agg, ef + soff1, Lf[2 % NP], Lf[3 % NP]);
-            add4<WIDE>(pb.agg, eb + soff1, Lb[2 % NP], Lb[3 % NP]);
-          }
+    }
+    for (int t0 = 0; t0 < W; t0 += U) {
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int t = t0 + u;
+        if (t >= W) break;
+        uint32_t c1[NP], c2[NP];
+        RC::unpack(rf[u], c1);
+        RC::unpack(rb[u], c2);
+        long_step2<DPL, LPL, FULL>(Lf, mf, c1, Lb, mb, c2, active, lig, P1P1, P2P2);
+        // refill this slot with step t + U (the pointers sit there already)
+        const bool ok = active && t + U < W;
+        rf[u] = ok ? RC::load(cf) : Raw();
+        rb[u] = ok ? RC::load(cb) : Raw();
+        if (t + U + 1 < W) {
+          cf += estride;
+          cb -= estride;
         }
+        if (active) {
+          add_lane<DPL, WIDE>(pb.agg, ef, Lf);
+          add_lane<DPL, WIDE>(pb.agg, eb, Lb);
+        }
+        ef += estride;
+        eb -= estride;
       }
-      ef += estride;
-      eb -= estride;
     }
   }
 }
 
-// ------------------------------------------------------------------------------- other axes
-// Chains [chain0, min(chain0 + 32 / WD, chain_end)): chain c walks line c / 2 of the other axes,
-// forward when c is even, backward when odd. WD lanes per chain, DPL disparities per lane.
-// FULL: every lane owns disparities (D == WD * DPL). Each lane copies its own 16-byte cost
-// pieces into `ring` (this warp's kBulkRing * (DPL / 16) * 32 uint4) with cp.async and waits
-// only for its own copies, kBulkRing - 1 steps ahead.
-template <int DPL, int WD, bool WIDE, bool FULL>
-__device__ __forceinline__ void agg_bulk_chains(const Problem& pb, const Method& mt, int chain0,
-                                                int chain_end, uint4* ring) {
+// ------------------------------------------------------------------------------- sheared columns
+// Kinds of sheared chain: 0 TB, 1 BT, 2 TLBR, 3 BRTL, 4 TRBL, 5 BLTR. Chain j of a kind with shear
+// s (0 for kinds 0-1, +1 for 2-3, -1 for 4-5) visits pixel x = (j + s y) mod W of every row y,
+// top-down for the even kinds and bottom-up for the odd ones, so one step moves it by
+// (dx, dy) = (s, 1) or (-s, -1): the direction r of its path. Where x wraps around (x = 0 after a
+// step with dx = +1, x = W - 1 after dx = -1) the pixel's predecessor lies outside the image: a
+// new line of the path enters there and the chain restarts with L = C. Every pixel lies on exactly
+// one chain of each kind, j = (x - s y) mod W, so the W chains of a kind cover its path once.
+constexpr int kShearRing = 8;  // steps in the cost ring; 2 steps per cp.async group, 6 in flight
+__host__ __device__ inline int shear_kinds(int num_paths) { return num_paths == 8 ? 6 : 2; }
+__host__ __device__ inline int shear_dpl_default(int D) { return 16; }
+__host__ __device__ inline int shear_width(int D, int dpl) { return pow2ceil(D / dpl); }
+// Warp items of one pair: kinds x groups of 32 / width adjacent chains.
+__host__ __device__ inline int shear_items(int W, int D, int dpl, int num_paths) {
+  const int cpw = 32 / shear_width(D, dpl);
+  return shear_kinds(num_paths) * ((W + cpw - 1) / cpw);
+}
+// Shared memory of one warp: the cost ring (kShearRing steps of 32 / width pixel vectors of D
+// bytes, at most 32 dpl bytes per step) and the staging buffer of one step's sums.
+__host__ __device__ inline int shear_ring_bytes(int dpl) { return kShearRing * 32 * dpl; }
+__host__ __device__ inline int shear_smem_bytes(int dpl, bool wide) {
+  return shear_ring_bytes(dpl) + 32 * dpl * (wide ? 4 : 2);
+}
+// Per warp for the default width of every D (shear_dpl_default is 16 for all D).
+__host__ __device__ inline int shear_default_smem_bytes(bool wide) { return shear_smem_bytes(16, wide); }
+
+// Position, in 16-byte pieces, of piece i of pixel slot c in a buffer of pixel vectors of pp
+// pieces each. When pp is a power of two the pieces of slot c are permuted by c, so lanes that
+// access the same piece index of adjacent pixels hit different shared-memory banks.
+__device__ __forceinline__ int swz(int c, int i, int pp) {
+  return c * pp + ((pp & (pp - 1)) == 0 ? (i ^ (c & (pp - 1))) : i);
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t a) {
+  uint4 r;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "r"(a));
+  return r;
+}
+__device__ __forceinline__ void sts128(uint32_t a, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w)
+               : "memory");
+}
+__device__ __forceinline__ unsigned long long lds64(uint32_t a) {
+  unsigned long long r;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(r) : "r"(a));
+  return r;
+}
+
+// Warp item `item` of the sheared-column kernel: 32 / WD adjacent chains of one kind, WD lanes
+// per chain, DPL disparities per lane (lane member lig owns [lig DPL, (lig + 1) DPL)). FULL: every
+// lane owns disparities (D == WD * DPL). SH0: the kind has shear 0 (columns), so its runs never
+// wrap and its chains never restart. ring / stage: this warp's shear_ring_bytes(DPL) and
+// 32 DPL (2 or 4) bytes of shared memory, 16-byte aligned.
+//
+// Per step (one row): the warp's costs were copied 6 steps earlier by all lanes, each lane taking
+// 16-byte pieces of the contiguous pixel run so that every copy instruction is coalesced; after
+// cp.async.wait_group and __syncwarp each lane reads its own pieces. The new L values go to the
+// staging buffer in the volume's layout, and after __syncwarp every lane adds 8-byte units of the
+// run into S, consecutive lanes on consecutive units. Lanes of chains past the image's last column
+// (and, FULL, every lane) compute unconditionally; only their copies and adds are skipped.
+template <int DPL, int WD, bool WIDE, bool FULL, bool SH0>
+__device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt, int kind, int j0,
+                                            uint8_t* ring, uint8_t* stage) {
   constexpr int NP = DPL / 2;
-  constexpr int NV = DPL / 16;  // 16-byte cost vectors per lane and step
-  constexpr int KS = kBulkRing;
+  constexpr int CPW = 32 / WD;         // chains per warp
+  constexpr int KS = kShearRing;
+  constexpr int BPE = WIDE ? 4 : 2;    // bytes per sum
+  constexpr int NVC = DPL / 16;        // cost pieces a lane copies / reads per step
+  constexpr int NVS = DPL * BPE / 16;  // sum pieces a lane stages per step
+  constexpr int NR = DPL * BPE / 8;    // 8-byte atomic adds a lane issues per step (at most)
   const int lane = threadIdx.x & 31;
-  const int lig = lane % WD;
-  const int W = pb.W, H = pb.H, D = pb.D;
-  const int nc = min(2 * bulk_num_lines(W, H, mt.num_paths), chain_end);
-  const int ci = chain0 + lane / WD;
-  const bool valid = ci < nc;
-  LineGeom g = bulk_line(valid ? ci >> 1 : 0, W, H, mt.num_paths);
-  if (!valid) g.len = 0;
-  const int maxlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)g.len);
-  if (maxlen == 0) return;
-  const bool back = (ci & 1) != 0;
-  const bool active = FULL ? valid : (valid && lig * DPL < D);
-  int64_t pstride = (int64_t)g.dy * W + g.dx;
-  int64_t px = (int64_t)g.sy * W + g.sx;
-  if (back) {
-    px += (int64_t)(g.len - 1) * pstride;
-    pstride = -pstride;
-  }
-  const int64_t estride = pstride * D;
-  // lane member lig owns disparities [lig * DPL, (lig + 1) * DPL): its cost piece v sits at
-  // cbo + v * cvs bytes and its sum chunk k at sbo + k * svs elements of the pixel vector
-  const int cvs = FULL ? WD * 16 : (pb.ord.blocked ? (D / DPL) * 16 : 16);
-  const int svs = FULL ? WD * 4 : (pb.ord.blocked ? (D / DPL) * 4 : 4);
-  const int cbo = (FULL || pb.ord.blocked) ? lig * 16 : lig * DPL;
-  const int sbo = (FULL || pb.ord.blocked) ? lig * 4 : lig * DPL;
-  const uint8_t* cp = pb.cost + px * D + cbo;  // next step to copy
-  int64_t e = px * D + sbo;                     // element of this step's first sum
+  const int lig = lane % WD, c = lane / WD;
+  const int W = pb.W, H = pb.H;
+  const int D = FULL ? WD * DPL : pb.D;
+  const int PP = D / 16;        // cost pieces per pixel
+  const int PS = D * BPE / 16;  // sum pieces per pixel
+  const int UPP = D * BPE / 8;  // 8-byte sum units per pixel
+  const int n = min(CPW, W - j0);  // chains of this warp
+  const bool nfull = n == CPW;
+  const int sh = SH0 ? 0 : (kind < 4 ? 1 : -1);
+  const bool back = (kind & 1) != 0;
+  const int dy = back ? -1 : 1, dx = back ? -sh : sh;
+  const int edge = dx > 0 ? 0 : W - 1;  // (shear != 0) a chain arriving at x == edge restarts
+  const int ystart = back ? H - 1 : 0;
+  int xs = (j0 + sh * ystart) % W;  // pixel of chain 0 in the current row
+  if (xs < 0) xs += W;
+  const bool active = c < n && (FULL || lig * DPL < D);
+  const bool owns = FULL || lig * DPL < D;  // the lane holds disparities of its chain
+  const int slot_bytes = CPW * D;
+  const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+  const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
   const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
-  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(ring);
+  const int64_t rowstep = (int64_t)dy * W;  // pixels from one row to the next
+
+  // Per-lane pieces, fixed for the whole walk: cost piece v of the step's run (chain cp_c[v],
+  // shared offset cp_s[v] inside a ring slot) and 8-byte sum unit r (chain su_c[r], staging offset
+  // su_s[r]). A run that does not wrap around the image edge is contiguous in memory, so piece v
+  // then sits 16 (lane + 32 v) bytes and unit r 8 (lane + 32 r) bytes after the run's start.
+  int cp_c[NVC], cp_s[NVC], su_c[NR], su_s[NR];
+#pragma unroll
+  for (int v = 0; v < NVC; v++) {
+    const int p = lane + 32 * v;
+    const int pc = p / PP, pi = p - pc * PP;
+    cp_c[v] = pc < n ? pc : -1;
+    cp_s[v] = swz(pc, pi, PP) * 16;
+  }
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    const int q = lane + 32 * r;
+    const int qc = q / UPP, qk = q - qc * UPP;
+    su_c[r] = qc < n ? qc : -1;
+    su_s[r] = swz(qc, qk >> 1, PS) * 16 + (qk & 1) * 8;
+  }
+
+  // copy cursor: chain-0 pixel (row-major index) of the next step to copy, and its column
+  int64_t pc_next = (int64_t)ystart * W + xs;
+  int xc = xs;
+  auto copy_step = [&](int t) {
+    if (t < H) {
+      const uint32_t slot = ring_s + (uint32_t)((t % KS) * slot_bytes);
+      const uint8_t* run = pb.cost + pc_next * D;
+      if (nfull && (SH0 || xc + CPW <= W)) {  // every piece, contiguous run
+#pragma unroll
+        for (int v = 0; v < NVC; v++)
+          if (FULL || cp_c[v] >= 0)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(slot + cp_s[v]),
+                         "l"(run + 16 * (lane + 32 * v)));
+      } else {
+#pragma unroll
+        for (int v = 0; v < NVC; v++) {
+          if (cp_c[v] >= 0) {
+            const int p = lane + 32 * v;
+            const int pc = cp_c[v], pi = p - pc * PP;
+            const int back_w = (!SH0 && xc + pc >= W) ? W : 0;  // wrapped to the row's start
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(slot + cp_s[v]),
+                         "l"(run + ((int64_t)pc - back_w) * D + pi * 16));
+          }
+        }
+      }
+      pc_next += rowstep;
+      if (!SH0) {
+        xc += dx;
+        pc_next += dx;
+        if (xc >= W) {
+          xc -= W;
+          pc_next -= W;
+        } else if (xc < 0) {
+          xc += W;
+          pc_next += W;
+        }
+      }
+    }
+  };
 
   uint32_t L[NP];
 #pragma unroll
-  for (int k = 0; k < NP; k++) L[k] = active ? 0u : kSent * 0x10001u;
+  for (int k = 0; k < NP; k++) L[k] = owns ? 0u : kSent * 0x10001u;
   uint32_t mm = 0;
+  int x = xs + c;  // this lane's chain pixel (meaningful for chains c < n)
+  if (x >= W) x -= W;
+  int64_t prun = (int64_t)ystart * W + xs;  // chain-0 pixel of the current step
 
-  // copies step s into its ring slot (s % KS) and moves the copy pointer on
-  auto copy_step = [&](int s) {
-    if (active && s < g.len) {
-#pragma unroll
-      for (int v = 0; v < NV; v++)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                         sbase + (uint32_t)((((s % KS) * NV + v) * 32 + lane) * 16)),
-                     "l"(cp + v * cvs));
-      if (s + 1 < g.len) cp += estride;
-    }
-  };
   // prologue: steps 0 .. 5 in flight as three groups of two
 #pragma unroll
   for (int s = 0; s < KS - 2; s += 2) {
@@ -434,47 +516,122 @@ __device__ __forceinline__ void agg_bulk_chains(const Problem& pb, const Method&
     copy_step(s + 1);
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  for (int t0 = 0; t0 < maxlen; t0 += KS) {
+  for (int t0 = 0; t0 < H; t0 += 2) {
 #pragma unroll
-    for (int u = 0; u < KS; u++) {
+    for (int u = 0; u < 2; u++) {
       const int t = t0 + u;
-      if (t >= maxlen) break;
-      if ((u & 1) == 0) {  // issue steps t + 6, t + 7, then wait for steps t, t + 1
+      if (t >= H) break;
+      __syncwarp();  // every lane is done with the ring slot refilled below and with the staging
+      if (u == 0) {  // issue steps t + 6, t + 7, then wait for steps t, t + 1
         copy_step(t + KS - 2);
         copy_step(t + KS - 1);
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 3;" ::: "memory");
+        __syncwarp();
       }
-      uint32_t c[NP];
+      const uint32_t slot = ring_s + (uint32_t)((t % KS) * slot_bytes);
+      if (!SH0) {
+        if (__any_sync(0xffffffffu, x == edge)) {  // a new line of the path enters: L = C
+          if (x == edge) {
 #pragma unroll
-      for (int v = 0; v < NV; v++) {
-        const uint4 r = ring[(u * NV + v) * 32 + lane];
-        unpack4(r.x, c[8 * v + 0], c[8 * v + 1]);
-        unpack4(r.y, c[8 * v + 2], c[8 * v + 3]);
-        unpack4(r.z, c[8 * v + 4], c[8 * v + 5]);
-        unpack4(r.w, c[8 * v + 6], c[8 * v + 7]);
+            for (int k = 0; k < NP; k++) L[k] = owns ? 0u : kSent * 0x10001u;
+            mm = 0;
+          }
+        }
+      }
+      uint32_t cst[NP];
+      if (owns) {
+#pragma unroll
+        for (int v = 0; v < NVC; v++) {
+          const uint4 r = lds128(slot + (uint32_t)(swz(c, lig * NVC + v, PP) * 16));
+          unpack4(r.x, cst[8 * v + 0], cst[8 * v + 1]);
+          unpack4(r.y, cst[8 * v + 2], cst[8 * v + 3]);
+          unpack4(r.z, cst[8 * v + 4], cst[8 * v + 5]);
+          unpack4(r.w, cst[8 * v + 6], cst[8 * v + 7]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NP; k++) cst[k] = 0u;
       }
       uint32_t X[NP + 1];
       neighbours<NP, WD>(L, lig, X);
       const uint32_t mP2 = mm + P2P2;
-      uint32_t lmin = 0xFFFFFFFFu;
+      uint32_t lm[NP];
 #pragma unroll
       for (int k = 0; k < NP; k++) {
         const uint32_t tt = vmin2(X[k], X[k + 1]) + P1P1;
         const uint32_t uu = vmin2(vmin2(L[k], tt), mP2);  // >= m(q) in both halves
-        const uint32_t ln = uu + c[k] - mm;                // each half in [0, 255 + P2]
-        L[k] = (FULL || active) ? ln : kSent * 0x10001u;
-        lmin = vmin2(lmin, L[k]);
+        const uint32_t ln = uu + cst[k] - mm;              // each half in [0, 255 + P2]
+        L[k] = owns ? ln : kSent * 0x10001u;
+        lm[k] = L[k];
       }
-      mm = group_min<WD>(halves_min(lmin));
-      if (active && t < g.len) {
 #pragma unroll
-        for (int k = 0; k < NP / 2; k++) add4<WIDE>(pb.agg, e + k * svs, L[2 * k], L[2 * k + 1]);
+      for (int w = 1; w < NP; w *= 2)  // tree minimum of the lane's pairs
+#pragma unroll
+        for (int k = 0; k + w < NP; k += 2 * w) lm[k] = vmin2(lm[k], lm[k + w]);
+      mm = group_min<WD>(halves_min(lm[0]));
+      if (FULL || active) {
+#pragma unroll
+        for (int v = 0; v < NVS; v++) {
+          const uint32_t a = stage_s + (uint32_t)(swz(c, lig * NVS + v, PS) * 16);
+          if (!WIDE)
+            sts128(a, L[4 * v], L[4 * v + 1], L[4 * v + 2], L[4 * v + 3]);
+          else
+            sts128(a, L[2 * v] & 0xFFFFu, L[2 * v] >> 16, L[2 * v + 1] & 0xFFFFu,
+                   L[2 * v + 1] >> 16);
+        }
       }
-      e += estride;
+      __syncwarp();
+      uint8_t* run = reinterpret_cast<uint8_t*>(pb.agg) + prun * D * BPE;
+      if (nfull && (SH0 || xs + CPW <= W)) {  // every unit, contiguous run
+#pragma unroll
+        for (int r = 0; r < NR; r++)
+          if (FULL || su_c[r] >= 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(run + 8 * (lane + 32 * r)),
+                      lds64(stage_s + (uint32_t)su_s[r]));
+      } else {
+#pragma unroll
+        for (int r = 0; r < NR; r++) {
+          if (su_c[r] >= 0) {
+            const int q = lane + 32 * r;
+            const int back_w = (!SH0 && xs + su_c[r] >= W) ? W : 0;  // wrapped to the row's start
+            atomicAdd(reinterpret_cast<unsigned long long*>(
+                          run + (int64_t)(q - back_w * UPP) * 8),
+                      lds64(stage_s + (uint32_t)su_s[r]));
+          }
+        }
+      }
+      prun += rowstep;
+      if (!SH0) {
+        xs += dx;
+        prun += dx;
+        if (xs >= W) {
+          xs -= W;
+          prun -= W;
+        } else if (xs < 0) {
+          xs += W;
+          prun += W;
+        }
+        x += dx;
+        x = x >= W ? x - W : (x < 0 ? x + W : x);
+      }
     }
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Warp item `item` of a pair's sheared-column work (see shear_items).
+template <int DPL, int WD, bool WIDE, bool FULL>
+__device__ __forceinline__ void agg_shear(const Problem& pb, const Method& mt, int item,
+                                          uint8_t* ring, uint8_t* stage) {
+  constexpr int CPW = 32 / WD;
+  const int G = (pb.W + CPW - 1) / CPW;
+  const int kind = item / G;
+  const int j0 = (item - kind * G) * CPW;
+  if (kind < 2)
+    agg_shear_t<DPL, WD, WIDE, FULL, true>(pb, mt, kind, j0, ring, stage);
+  else
+    agg_shear_t<DPL, WD, WIDE, FULL, false>(pb, mt, kind, j0, ring, stage);
 }
 
 }  // namespace r2t

@@ -2,15 +2,15 @@
 // batch. A block (or, in the aggregation, a warp) claims its next work item from a device queue
 // with one atomic increment and maps it to (pair, item of that pair) through prefix tables; no
 // block ever waits for another, so the queues need no device-side spin. Stage order is kept by
-// the launch order on one stream; the two aggregation kernels (long-axis lines and the other
-// lines) run concurrently on a forked stream inside the graph. The descriptor upload, the queue
+// the launch order on one stream; the two aggregation kernels (row paths and sheared-column
+// paths) run concurrently on a forked stream inside the graph. The descriptor upload, the queue
 // reset and the stage kernels are recorded once into a CUDA graph and replayed while the
 // capacities last.
 //
-// Aggregation work is described by segments, two per pair: its long-axis lines (one warp item
-// per group of lines) and its other lines (one item per group of chains). Each queue is ordered
-// by the longest line of its segments across the whole batch (longest first), so the sequential
-// chains that bound the batch's duration start earliest.
+// Aggregation work is described by segments, two per pair: its rows (one warp item per group of
+// rows) and its sheared columns (one warp item per group of adjacent chains of one kind). Each
+// queue is ordered by the chain length of its segments across the whole batch (longest first),
+// so the sequential chains that bound the batch's duration start earliest.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
@@ -20,56 +20,13 @@
 
 #include "aggregate.cuh"
 #include "batch.h"
+#include "batch_dev.cuh"
 #include "census_cost.cuh"
 #include "launch.h"
 #include "post.cuh"
 
 namespace r2t {
 
-enum {
-  kStCensus = 0, kStCost = 1, kStLong = 2, kStBulk = 3, kStWta = 4, kStMedian = 5,
-  kNumCounters = 6
-};
-
-// Header of the device descriptor block. It is followed by Problem[cap], int prefix[4][cap + 1]
-// (census, cost, wta, median items), then for the long and the bulk queue each AggSeg[cap] and
-// int seg_prefix[cap + 1].
-struct BatchHeader {
-  int n;
-  int total[kNumCounters];
-  int pad;
-  signed char dpl_by_d16[17];  // long-axis disparities per lane, indexed by D / 16
-};
-
-struct AggSeg {
-  int pair, begin, end, group;  // lines / chains [begin, end) of one pair, `group` per warp item
-};
-
-__device__ __forceinline__ int find_slot(const int* prefix, int n, int item) {
-  int lo = 0, hi = n - 1;  // largest p with prefix[p] <= item
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= item)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ int claim_block(unsigned* counter, int* s_item) {
-  if (threadIdx.x == 0) *s_item = (int)atomicAdd(counter, 1u);
-  __syncthreads();
-  const int item = *s_item;
-  __syncthreads();
-  return item;
-}
-
-__device__ __forceinline__ int claim_warp(unsigned* counter) {
-  int item = 0;
-  if ((threadIdx.x & 31) == 0) item = (int)atomicAdd(counter, 1u);
-  return __shfl_sync(0xffffffffu, item, 0);
-}
 
 __global__ void __launch_bounds__(256) batch_census_kernel(const BatchHeader* hd,
                                                            const Problem* probs, const int* prefix,
@@ -97,93 +54,10 @@ __global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
     if (item >= total) break;
     const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
-    cost_tile(pb, item - prefix[p], sm, mt.wide ? 4 : 2);
+    cost_tile_dispatch(pb, mt, item - prefix[p], sm);
   }
 }
 
-template <int DPL, int LPL, bool WIDE>
-__device__ __forceinline__ void long_full(const Problem& pb, const Method& mt, int line0,
-                                          int line_end) {
-  if (pb.D == DPL * LPL)
-    agg_long_lines<DPL, LPL, WIDE, true>(pb, mt, line0, line_end);
-  else
-    agg_long_lines<DPL, LPL, WIDE, false>(pb, mt, line0, line_end);
-}
-
-template <bool WIDE>
-__device__ __forceinline__ void long_dispatch(const Problem& pb, const Method& mt, int line0,
-                                              int line_end, int dpl) {
-  switch (dpl * 100 + long_lanes(pb.D, dpl)) {
-    case 208: long_full<2, 8, WIDE>(pb, mt, line0, line_end); break;
-    case 216: long_full<2, 16, WIDE>(pb, mt, line0, line_end); break;
-    case 232: long_full<2, 32, WIDE>(pb, mt, line0, line_end); break;
-    case 408: long_full<4, 8, WIDE>(pb, mt, line0, line_end); break;
-    case 416: long_full<4, 16, WIDE>(pb, mt, line0, line_end); break;
-    case 432: long_full<4, 32, WIDE>(pb, mt, line0, line_end); break;
-    case 808: long_full<8, 8, WIDE>(pb, mt, line0, line_end); break;
-    case 816: long_full<8, 16, WIDE>(pb, mt, line0, line_end); break;
-    case 832: long_full<8, 32, WIDE>(pb, mt, line0, line_end); break;
-    default: break;
-  }
-}
-
-template <int DPL, int WD, bool WIDE>
-__device__ __forceinline__ void bulk_full(const Problem& pb, const Method& mt, int chain0,
-                                          int chain_end, uint4* ring) {
-  if (pb.D == DPL * WD)
-    agg_bulk_chains<DPL, WD, WIDE, true>(pb, mt, chain0, chain_end, ring);
-  else
-    agg_bulk_chains<DPL, WD, WIDE, false>(pb, mt, chain0, chain_end, ring);
-}
-
-template <bool WIDE>
-__device__ __forceinline__ void bulk_dispatch(const Problem& pb, const Method& mt, int chain0,
-                                              int chain_end, uint4* ring) {
-  switch (bulk_dpl(pb.D) * 100 + bulk_width(pb.D)) {
-    case 1601: bulk_full<16, 1, WIDE>(pb, mt, chain0, chain_end, ring); break;
-    case 1604: bulk_full<16, 4, WIDE>(pb, mt, chain0, chain_end, ring); break;
-    case 1608: bulk_full<16, 8, WIDE>(pb, mt, chain0, chain_end, ring); break;
-    case 1616: bulk_full<16, 16, WIDE>(pb, mt, chain0, chain_end, ring); break;
-    case 3201: bulk_full<32, 1, WIDE>(pb, mt, chain0, chain_end, ring); break;
-    case 3202: bulk_full<32, 2, WIDE>(pb, mt, chain0, chain_end, ring); break;
-    case 3204: bulk_full<32, 4, WIDE>(pb, mt, chain0, chain_end, ring); break;
-    case 3208: bulk_full<32, 8, WIDE>(pb, mt, chain0, chain_end, ring); break;
-    default: break;
-  }
-}
-
-template <bool WIDE>
-__global__ void __launch_bounds__(256) batch_long_kernel(const BatchHeader* hd, const Problem* probs,
-                                                         const AggSeg* segs, const int* seg_prefix,
-                                                         int nseg, Method mt, unsigned* counters) {
-  const int total = hd->total[kStLong];
-  for (;;) {
-    const int item = claim_warp(&counters[kStLong]);
-    if (item >= total) break;
-    const int si = find_slot(seg_prefix, nseg, item);
-    const AggSeg sg = segs[si];
-    const Problem pb = probs[sg.pair];
-    long_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, sg.end,
-                        hd->dpl_by_d16[pb.D / 16]);
-  }
-}
-
-template <bool WIDE>
-__global__ void __launch_bounds__(256) batch_bulk_kernel(const BatchHeader* hd, const Problem* probs,
-                                                         const AggSeg* segs, const int* seg_prefix,
-                                                         int nseg, Method mt, unsigned* counters) {
-  extern __shared__ uint4 bring[];
-  uint4* ring = bring + (threadIdx.x >> 5) * (bulk_ring_bytes(32) / 16);
-  const int total = hd->total[kStBulk];
-  for (;;) {
-    const int item = claim_warp(&counters[kStBulk]);
-    if (item >= total) break;
-    const int si = find_slot(seg_prefix, nseg, item);
-    const AggSeg sg = segs[si];
-    const Problem pb = probs[sg.pair];
-    bulk_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, sg.end, ring);
-  }
-}
 
 template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, const Problem* probs,
@@ -237,7 +111,7 @@ struct BatchEngine {
 
 static size_t probs_offset() { return (sizeof(BatchHeader) + 255) / 256 * 256; }
 static size_t prefix_offset(int cap) { return probs_offset() + (size_t)cap * sizeof(Problem); }
-static size_t segs_offset(int cap, int q) {  // q = 0 long, 1 bulk
+static size_t segs_offset(int cap, int q) {  // q = 0 rows, 1 sheared columns
   const size_t base = (prefix_offset(cap) + 4 * sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
   const size_t per = ((size_t)cap * sizeof(AggSeg) + sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
   return base + q * per;
@@ -354,11 +228,12 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
                        wta_smem);
   const int g_census = persistent_grid(batch_census_kernel, 0);
   const int g_cost = persistent_grid(batch_cost_kernel, 0);
-  const int g_long = persistent_grid(batch_long_kernel<WIDE>, 0);
-  const int bulk_smem = 8 * bulk_ring_bytes(32);  // 8 warps per block
-  cudaFuncSetAttribute(batch_bulk_kernel<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       bulk_smem);
-  const int g_bulk = persistent_grid(batch_bulk_kernel<WIDE>, bulk_smem);
+  const void* k_rows = batch_row_kernel_fn<WIDE>();
+  const void* k_shear = batch_shear_kernel_fn<WIDE>();
+  const int g_rows = persistent_grid(k_rows, 0);
+  const int shear_smem = 8 * shear_default_smem_bytes(WIDE);  // 8 warps per block
+  cudaFuncSetAttribute(k_shear, cudaFuncAttributeMaxDynamicSharedMemorySize, shear_smem);
+  const int g_shear = persistent_grid(k_shear, shear_smem);
   const int g_wta = persistent_grid(batch_wta_kernel<WIDE>, wta_smem);
   const int g_med = persistent_grid(batch_median_kernel, 0);
   cudaError_t c = cudaGetLastError();
@@ -376,10 +251,17 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   batch_cost_kernel<<<g_cost, 256, 0, cs>>>(hd, probs, prefix + 1 * stride, mt, e->d_counters);
   cudaEventRecord(e->fork.fork, cs);
   cudaStreamWaitEvent(e->fork.aux, e->fork.fork, 0);
-  batch_long_kernel<WIDE><<<g_long, 256, 0, e->fork.aux>>>(hd, probs, lsegs, lpre, cap, mt,
-                                                           e->d_counters);
-  batch_bulk_kernel<WIDE><<<g_bulk, 256, bulk_smem, cs>>>(hd, probs, bsegs, bpre, cap, mt,
-                                                          e->d_counters);
+  {
+    int nseg = cap;
+    Method m = mt;
+    unsigned* counters = e->d_counters;
+    void* rargs[] = {(void*)&hd, (void*)&probs, (void*)&lsegs, (void*)&lpre, (void*)&nseg,
+                     (void*)&m, (void*)&counters};
+    void* sargs[] = {(void*)&hd, (void*)&probs, (void*)&bsegs, (void*)&bpre, (void*)&nseg,
+                     (void*)&m, (void*)&counters};
+    cudaLaunchKernel(k_rows, dim3(g_rows), dim3(256), rargs, 0, e->fork.aux);
+    cudaLaunchKernel(k_shear, dim3(g_shear), dim3(256), sargs, shear_smem, cs);
+  }
   cudaEventRecord(e->fork.join, e->fork.aux);
   cudaStreamWaitEvent(cs, e->fork.join, 0);
   batch_wta_kernel<WIDE><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 2 * stride,
@@ -409,7 +291,7 @@ struct Keyed {
   int len;
 };
 
-// Writes one queue's segments, sorted by their longest line, and its prefix table.
+// Writes one queue's segments, sorted by their chain length, and its prefix table.
 static int write_queue(std::vector<Keyed>& kv, AggSeg* segs, int* pre, int cap) {
   std::stable_sort(kv.begin(), kv.end(), [](const Keyed& a, const Keyed& b) { return a.len > b.len; });
   int items = 0;
@@ -457,23 +339,20 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
     tot[3] += median_items(pb.W, pb.H);
     wta_smem = std::max(wta_smem, (int)wta_smem_bytes(pb.D, wta_tile_px(pb.D)));
     const int dpl = e->dpl_by_d16[pb.D / 16];
-    const int la = long_axis(pb.W, pb.H);
-    lk.push_back(Keyed{AggSeg{p, 0, axis_lines(la, pb.W, pb.H), 32 / long_lanes(pb.D, dpl)},
-                       std::max(pb.W, pb.H)});
-    bk.push_back(Keyed{AggSeg{p, 0, 2 * bulk_num_lines(pb.W, pb.H, mt.num_paths),
-                              32 / bulk_width(pb.D)},
-                       std::min(pb.W, pb.H)});
+    lk.push_back(Keyed{AggSeg{p, 0, row_units(pb.H, false), 32 / long_lanes(pb.D, dpl)}, pb.W});
+    bk.push_back(Keyed{AggSeg{p, 0, shear_items(pb.W, pb.D, shear_dpl_default(pb.D), mt.num_paths), 1},
+                       pb.H});
   }
   for (int k = 0; k < 4; k++) prefix[k * stride + n] = tot[k];
-  const int nlong = write_queue(lk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 0)),
+  const int nrows = write_queue(lk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 0)),
                                 reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 0)), cap);
-  const int nbulk = write_queue(bk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 1)),
+  const int nshear = write_queue(bk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 1)),
                                 reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 1)), cap);
   hd->n = n;
   hd->total[kStCensus] = tot[0];
   hd->total[kStCost] = tot[1];
-  hd->total[kStLong] = nlong;
-  hd->total[kStBulk] = nbulk;
+  hd->total[kStRows] = nrows;
+  hd->total[kStShear] = nshear;
   hd->total[kStWta] = tot[2];
   hd->total[kStMedian] = tot[3];
   memcpy(hd->dpl_by_d16, e->dpl_by_d16, sizeof(hd->dpl_by_d16));

@@ -11,24 +11,9 @@ __global__ void __launch_bounds__(256) census_kernel(Problem pb, Method mt) {
   census_tile_dispatch(pb, mt, blockIdx.x, sm);
 }
 
-__global__ void __launch_bounds__(256) cost_kernel(Problem pb, int agg_bytes_per_de) {
+__global__ void __launch_bounds__(256) cost_kernel(Problem pb, Method mt) {
   __shared__ CostSmem sm;
-  cost_tile(pb, blockIdx.x, sm, agg_bytes_per_de);
-}
-
-template <int DPL, int LPL, bool WIDE, bool FULL>
-__global__ void __launch_bounds__(512) agg_long_kernel(Problem pb, Method mt) {
-  const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  agg_long_lines<DPL, LPL, WIDE, FULL>(pb, mt, warp * (32 / LPL), 0x7FFFFFFF);
-}
-
-template <int DPL, int WD, bool WIDE, bool FULL>
-__global__ void __launch_bounds__(512) agg_bulk_kernel(Problem pb, Method mt) {
-  extern __shared__ uint4 bring[];
-  const int wib = threadIdx.x >> 5;
-  const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
-  agg_bulk_chains<DPL, WD, WIDE, FULL>(pb, mt, warp * (32 / WD), 0x7FFFFFFF,
-                                       bring + wib * (bulk_ring_bytes(DPL) / 16));
+  cost_tile_dispatch(pb, mt, blockIdx.x, sm);
 }
 
 template <bool WIDE>
@@ -42,24 +27,14 @@ __global__ void __launch_bounds__(256) lr_median_kernel(Problem pb, Method mt) {
   lr_median_tile(pb, mt, blockIdx.x, sm);
 }
 
-// Debug copies in natural disparity order: sums saturated to uint16, costs as they are.
+// Debug copy of the aggregated volume, sums saturated to uint16.
 template <bool WIDE>
-__global__ void agg_copy_kernel(const void* src, uint16_t* dst, int64_t npx, int D, VolOrder o) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx * D;
+__global__ void agg_copy_kernel(const void* src, uint16_t* dst, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = i / D;
-    const int pos = (int)(i - p * D);
     const uint32_t v = WIDE ? min(reinterpret_cast<const uint32_t*>(src)[i], 65535u)
                             : reinterpret_cast<const uint16_t*>(src)[i];
-    dst[p * D + vol_index(pos, o, 2)] = (uint16_t)v;
-  }
-}
-__global__ void cost_copy_kernel(const uint8_t* src, uint8_t* dst, int64_t npx, int D, VolOrder o) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npx * D;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = i / D;
-    const int pos = (int)(i - p * D);
-    dst[p * D + vol_index(pos, o, 4)] = src[i];
+    dst[i] = (uint16_t)v;
   }
 }
 
@@ -68,6 +43,8 @@ Tuning default_tuning(int D) {
   t.agg_dpl = long_dpl_default(D);
   t.agg_warps = 4;
   t.wta_chunk = wta_tile_px(D);
+  t.shear_dpl = shear_dpl_default(D);
+  t.row_split = 0;
   return t;
 }
 
@@ -77,6 +54,9 @@ bool tuning_valid(const Tuning& t, int D) {
   if ((D + t.agg_dpl - 1) / t.agg_dpl > 32) return false;
   if (t.agg_warps < 1 || t.agg_warps > 16) return false;
   if (t.wta_chunk != 64 && t.wta_chunk != 128 && t.wta_chunk != 256) return false;
+  if (t.shear_dpl != 16 && t.shear_dpl != 32) return false;
+  if (D % t.shear_dpl != 0) return false;
+  if (t.row_split != 0 && t.row_split != 1) return false;
   return true;
 }
 
@@ -97,68 +77,6 @@ void fork_destroy(Fork* f) {
   f->fork = f->join = nullptr;
 }
 
-template <int DPL, int LPL, bool WIDE>
-static cudaError_t launch_long_t(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
-  const int nl = axis_lines(long_axis(pb.W, pb.H), pb.W, pb.H);
-  const int nwarp = (nl + 32 / LPL - 1) / (32 / LPL);
-  const int grid = (nwarp + warps - 1) / warps;
-  if (pb.D == DPL * LPL)
-    agg_long_kernel<DPL, LPL, WIDE, true><<<grid, warps * 32, 0, s>>>(pb, mt);
-  else
-    agg_long_kernel<DPL, LPL, WIDE, false><<<grid, warps * 32, 0, s>>>(pb, mt);
-  return cudaGetLastError();
-}
-
-template <bool WIDE>
-static cudaError_t launch_long(const Problem& pb, const Method& mt, const Tuning& tn,
-                               cudaStream_t s) {
-  switch (tn.agg_dpl * 100 + long_lanes(pb.D, tn.agg_dpl)) {
-    case 208: return launch_long_t<2, 8, WIDE>(pb, mt, tn.agg_warps, s);
-    case 216: return launch_long_t<2, 16, WIDE>(pb, mt, tn.agg_warps, s);
-    case 232: return launch_long_t<2, 32, WIDE>(pb, mt, tn.agg_warps, s);
-    case 408: return launch_long_t<4, 8, WIDE>(pb, mt, tn.agg_warps, s);
-    case 416: return launch_long_t<4, 16, WIDE>(pb, mt, tn.agg_warps, s);
-    case 432: return launch_long_t<4, 32, WIDE>(pb, mt, tn.agg_warps, s);
-    case 808: return launch_long_t<8, 8, WIDE>(pb, mt, tn.agg_warps, s);
-    case 816: return launch_long_t<8, 16, WIDE>(pb, mt, tn.agg_warps, s);
-    case 832: return launch_long_t<8, 32, WIDE>(pb, mt, tn.agg_warps, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <int DPL, int WD, bool WIDE>
-static cudaError_t launch_bulk_t(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
-  const int nc = 2 * bulk_num_lines(pb.W, pb.H, mt.num_paths);
-  const int nwarp = (nc + 32 / WD - 1) / (32 / WD);
-  const int grid = (nwarp + warps - 1) / warps;
-  const size_t smem = (size_t)warps * bulk_ring_bytes(DPL);
-  if (pb.D == DPL * WD) {
-    cudaFuncSetAttribute(agg_bulk_kernel<DPL, WD, WIDE, true>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    agg_bulk_kernel<DPL, WD, WIDE, true><<<grid, warps * 32, smem, s>>>(pb, mt);
-  } else {
-    cudaFuncSetAttribute(agg_bulk_kernel<DPL, WD, WIDE, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    agg_bulk_kernel<DPL, WD, WIDE, false><<<grid, warps * 32, smem, s>>>(pb, mt);
-  }
-  return cudaGetLastError();
-}
-
-template <bool WIDE>
-static cudaError_t launch_bulk(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
-  switch (bulk_dpl(pb.D) * 100 + bulk_width(pb.D)) {
-    case 1601: return launch_bulk_t<16, 1, WIDE>(pb, mt, warps, s);
-    case 1604: return launch_bulk_t<16, 4, WIDE>(pb, mt, warps, s);
-    case 1608: return launch_bulk_t<16, 8, WIDE>(pb, mt, warps, s);
-    case 1616: return launch_bulk_t<16, 16, WIDE>(pb, mt, warps, s);
-    case 3201: return launch_bulk_t<32, 1, WIDE>(pb, mt, warps, s);
-    case 3202: return launch_bulk_t<32, 2, WIDE>(pb, mt, warps, s);
-    case 3204: return launch_bulk_t<32, 4, WIDE>(pb, mt, warps, s);
-    case 3208: return launch_bulk_t<32, 8, WIDE>(pb, mt, warps, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 static cudaError_t launch_aggregate(const Problem& pb, const Method& mt, const Tuning& tn,
                                     cudaStream_t s, const Fork* fork) {
   cudaStream_t ls = s;
@@ -167,10 +85,9 @@ static cudaError_t launch_aggregate(const Problem& pb, const Method& mt, const T
     cudaStreamWaitEvent(fork->aux, fork->fork, 0);
     ls = fork->aux;
   }
-  cudaError_t e = mt.wide ? launch_long<true>(pb, mt, tn, ls) : launch_long<false>(pb, mt, tn, ls);
+  cudaError_t e = mt.wide ? launch_rows<true>(pb, mt, tn, ls) : launch_rows<false>(pb, mt, tn, ls);
   if (e != cudaSuccess) return e;
-  e = mt.wide ? launch_bulk<true>(pb, mt, tn.agg_warps, s)
-              : launch_bulk<false>(pb, mt, tn.agg_warps, s);
+  e = mt.wide ? launch_shear<true>(pb, mt, tn, s) : launch_shear<false>(pb, mt, tn, s);
   if (e != cudaSuccess) return e;
   if (fork) {
     cudaEventRecord(fork->join, fork->aux);
@@ -188,19 +105,19 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
-  cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt.wide ? 4 : 2);
+  cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
   if ((e = launch_aggregate(pb, mt, tn, s, fork)) != cudaSuccess) return e;
   n += 2;
   if (ev) cudaEventRecord(ev[3], s);
-  const int T = tn.wta_chunk;  // one thread per pixel
+  const int T = tn.wta_chunk;  // pixels per block of 256 threads
   const size_t smem = wta_smem_bytes(pb.D, T);
   if (mt.wide)
-    wta_dr_kernel<true><<<wta_items(pb.W, pb.H, T), T, smem, s>>>(pb, T);
+    wta_dr_kernel<true><<<wta_items(pb.W, pb.H, T), 256, smem, s>>>(pb, T);
   else
-    wta_dr_kernel<false><<<wta_items(pb.W, pb.H, T), T, smem, s>>>(pb, T);
+    wta_dr_kernel<false><<<wta_items(pb.W, pb.H, T), 256, smem, s>>>(pb, T);
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[4], s);
@@ -213,18 +130,16 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
 }
 
 cudaError_t copy_agg_u16(const Problem& pb, bool wide, uint16_t* dst, cudaStream_t s) {
-  const int64_t npx = (int64_t)pb.W * pb.H;
+  const int64_t n = (int64_t)pb.W * pb.H * pb.D;
   if (wide)
-    agg_copy_kernel<true><<<1216, 256, 0, s>>>(pb.agg, dst, npx, pb.D, pb.ord);
+    agg_copy_kernel<true><<<1216, 256, 0, s>>>(pb.agg, dst, n);
   else
-    agg_copy_kernel<false><<<1216, 256, 0, s>>>(pb.agg, dst, npx, pb.D, pb.ord);
+    agg_copy_kernel<false><<<1216, 256, 0, s>>>(pb.agg, dst, n);
   return cudaGetLastError();
 }
 
 cudaError_t copy_cost(const Problem& pb, uint8_t* dst, cudaStream_t s) {
-  const int64_t npx = (int64_t)pb.W * pb.H;
-  cost_copy_kernel<<<1216, 256, 0, s>>>(pb.cost, dst, npx, pb.D, pb.ord);
-  return cudaGetLastError();
+  return cudaMemcpyAsync(dst, pb.cost, (size_t)pb.W * pb.H * pb.D, cudaMemcpyDeviceToDevice, s);
 }
 
 // Independent chains of packed u16x2 min and add: 16 chains per thread, 4 instructions per chain

@@ -8,13 +8,15 @@
 namespace r2t {
 
 struct Tuning {
-  int agg_dpl;    // disparities per lane of the long-axis aggregation (2, 4 or 8)
+  int agg_dpl;    // disparities per lane of the row aggregation kernel (2, 4 or 8)
   int agg_warps;  // warps per aggregation block
   int wta_chunk;  // pixels per block of the WTA / right-disparity stage
+  int shear_dpl;  // disparities per lane of the sheared-column kernel (16 or 32)
+  int row_split;  // 1: one row direction per lane group, 0: both directions in one group
 };
 
 // A second stream and two events that let the two aggregation kernels run concurrently: the
-// long-axis kernel goes to `aux` (forked from and joined back to the caller's stream).
+// row kernel goes to `aux` (forked from and joined back to the caller's stream).
 struct Fork {
   cudaStream_t aux;
   cudaEvent_t fork, join;
@@ -26,6 +28,21 @@ void fork_destroy(Fork* f);
 Tuning default_tuning(int D);
 // True when the configuration can run a pair with D disparities.
 bool tuning_valid(const Tuning& t, int D);
+
+// Aggregation kernels on one stream (one launch each; defined in the agg_*.cu units): the row
+// paths and the sheared-column paths.
+template <bool WIDE>
+cudaError_t launch_rows(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s);
+template <bool WIDE>
+cudaError_t launch_shear(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s);
+// Persistent batch variants of the two kernels, as handles for cudaLaunchKernel. Parameters:
+// (const BatchHeader*, const Problem*, const AggSeg* segs, const int* seg_prefix, int nseg,
+// Method, unsigned* counters); 256 threads; the sheared one takes 8 shear_default_smem_bytes(WIDE)
+// bytes of dynamic shared memory.
+template <bool WIDE>
+const void* batch_row_kernel_fn();
+template <bool WIDE>
+const void* batch_shear_kernel_fn();
 
 // Plain single-pair pipeline: 5 kernel launches on stream s (census; cost + clearing of the
 // aggregated volume; aggregation; WTA + right-disparity keys; LR check + median). Returns the

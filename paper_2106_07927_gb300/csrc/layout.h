@@ -40,7 +40,6 @@ inline Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
   pb.ctl = reinterpret_cast<uint64_t*>(base + l.ctl);
   pb.ctr = reinterpret_cast<uint64_t*>(base + l.ctr);
   pb.cost = reinterpret_cast<uint8_t*>(base + l.cost);
-  pb.ord = vol_order_for(D);
   pb.agg = base + l.agg;
   pb.dl = reinterpret_cast<uint16_t*>(base + l.dl);
   pb.dr = reinterpret_cast<uint16_t*>(base + l.dr);

@@ -1,9 +1,9 @@
 // Disparity selection and post-processing, Sec. 2.1.2 - 2.1.3, as block-level routines.
 //
-// wta_dr_tile: for T consecutive pixels of a row, one thread per pixel reads that pixel's
-// aggregated vector S(x, .) once (16-byte loads) and computes
+// wta_dr_tile: for T consecutive pixels of a row, each pixel's aggregated vector S(x, .) is read
+// once, by one warp with its lanes on consecutive disparities (coalesced loads), and gives
 //   D^L(x) = smallest d with the least S(x, d)                                  Eq. (wta)
-// as a running minimum, and its share of
+// as a warp minimum, and its share of
 //   D^R(x) = smallest d <= min(D-1, W-1-x) with the least S(x + d, d)          Eq. (right_disparity)
 // for every target x' = x - d. The paper gathers S for D^R with strided, uncoalesced reads
 // (Sec. 2.2.3); here every source is read once and each of its keys is scattered to its target.
@@ -20,19 +20,58 @@
 
 namespace r2t {
 
-// Pixels per block of the WTA / right-disparity stage: one thread per pixel.
+// Pixels per block of the WTA / right-disparity stage (the block has 256 threads).
 __host__ __device__ inline int wta_tile_px(int D) { return 256; }
 // Shared memory: one key per target pixel of the tile, T + D - 1 of them.
 __host__ __device__ inline size_t wta_smem_bytes(int D, int T) { return (size_t)(T + D - 1) * 4; }
 __host__ __device__ inline int wta_items(int W, int H, int T) { return H * ((W + T - 1) / T); }
 
-// One thread walks the D sums of one source pixel x' once: a running minimum of the keys gives
-// D^L(x'), and every key S(x', d) << 8 | d is offered to target x' - d with a shared-memory
-// atomicMin (the 32 lanes of a warp hit 32 consecutive targets, so no bank conflict). Targets whose
-// sources all lie in the tile are then stored, the others (at most D - 1 per tile side) merged with
-// a global atomicMin. T must equal blockDim.x.
-template <bool WIDE>
-__device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint32_t* keys, int T) {
+// Loads S(x, d) for the disparities d = lane + 32 i (i < NDL) of one pixel vector, saturated to
+// 16 bits (0xFFFF past D; EXACT: D == 32 NDL).
+template <bool WIDE, int NDL, bool EXACT>
+__device__ __forceinline__ void wta_load(const void* agg, int64_t vec, int D, int lane,
+                                         uint32_t (&s)[NDL]) {
+#pragma unroll
+  for (int i = 0; i < NDL; i++) {
+    const int d = lane + 32 * i;
+    s[i] = 0xFFFFu;
+    if (EXACT || d < D) {
+      if (WIDE)
+        s[i] = min(__ldg(reinterpret_cast<const uint32_t*>(agg) + vec + d), 65535u);
+      else
+        s[i] = __ldg(reinterpret_cast<const unsigned short*>(agg) + vec + d);
+    }
+  }
+}
+
+// The keys of one pixel x (tile position px): each lane offers its keys to targets x - d with a
+// shared-memory atomicMin (consecutive lanes hit consecutive targets, so no bank conflict) and the
+// warp minimum gives D^L(x).
+template <int NDL, bool EXACT>
+__device__ __forceinline__ void wta_keys(const Problem& pb, int64_t rowbase, int x, int px,
+                                         uint32_t* keys, int lane, const uint32_t (&s)[NDL]) {
+  const int D = pb.D;
+  uint32_t* kt = keys + (px + D - 1);  // kt[-d] is the key of target x - d
+  const bool edge = x < D - 1;                // some targets x - d fall left of the image
+  uint32_t kl = 0xFFFFFFFFu;
+#pragma unroll
+  for (int i = 0; i < NDL; i++) {
+    const int d = lane + 32 * i;
+    if (EXACT || d < D) {
+      const uint32_t key = (s[i] << 8) | (uint32_t)d;
+      kl = min(kl, key);
+      if (!edge || d <= x) atomicMin(kt - d, key);
+    }
+  }
+  kl = __reduce_min_sync(0xffffffffu, kl);
+  if (lane == 0) pb.dl[rowbase + x] = (uint16_t)(kl & 0xFFu);
+}
+
+// One tile of T pixels of a row, 256 threads: warp w takes pixels w, w + 8, ..., two at a time so
+// that both pixels' loads are in flight together. Targets whose sources all lie in the tile are
+// then stored, the others (at most D - 1 per tile side) merged with a global atomicMin.
+template <bool WIDE, int NDL, bool EXACT>
+__device__ __forceinline__ void wta_dr_tile_t(const Problem& pb, int item, uint32_t* keys, int T) {
   const int W = pb.W, D = pb.D;
   const int ntx = (W + T - 1) / T;
   const int y = item / ntx, x0 = (item - y * ntx) * T;
@@ -41,40 +80,14 @@ __device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint32_
   const int ntar = T + D - 1;  // targets x0 - D + 1 .. x0 + T - 1
   for (int i = threadIdx.x; i < ntar; i += blockDim.x) keys[i] = 0xFFFFFFFFu;
   __syncthreads();
-  const int px = threadIdx.x;
-  if (px < n) {
-    const int x = x0 + px;
-    uint32_t* kt = keys + (px + D - 1);  // kt[-d] is the key of target x - d
-    uint32_t kl = 0xFFFFFFFFu;
-    const bool edge = x < D - 1;  // some targets x - d fall left of the image
-    for (int c = 0; c < D / 8; c++) {
-      uint32_t w[4];  // 8 sums at positions 8c .. 8c + 7, saturated to 16 bits
-      if (WIDE) {
-        const uint4* src =
-            reinterpret_cast<const uint4*>(reinterpret_cast<const uint32_t*>(pb.agg) + (rowbase + x) * D + 8 * c);
-        const uint4 a = __ldg(src), b = __ldg(src + 1);
-        const uint32_t s[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int j = 0; j < 4; j++) w[j] = min(s[2 * j], 65535u) | (min(s[2 * j + 1], 65535u) << 16);
-      } else {
-        const uint4 a = __ldg(reinterpret_cast<const uint4*>(
-            reinterpret_cast<const uint16_t*>(pb.agg) + (rowbase + x) * D + 8 * c));
-        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-      }
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        const int d0 = vol_index(8 * c + 4 * h, pb.ord, 2);  // 4 consecutive disparities
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-          const uint32_t s = (j & 1) ? (w[2 * h + j / 2] >> 16) : (w[2 * h + j / 2] & 0xFFFFu);
-          const int d = d0 + j;
-          const uint32_t key = (s << 8) | (uint32_t)d;
-          kl = min(kl, key);
-          if (!edge || d <= x) atomicMin(kt - d, key);
-        }
-      }
-    }
-    pb.dl[rowbase + x] = (uint16_t)(kl & 0xFFu);
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int px = threadIdx.x >> 5; px < n; px += 2 * nw) {
+    const int pq = px + nw;
+    uint32_t sa[NDL], sb[NDL];
+    wta_load<WIDE, NDL, EXACT>(pb.agg, (rowbase + x0 + px) * D, D, lane, sa);
+    if (pq < n) wta_load<WIDE, NDL, EXACT>(pb.agg, (rowbase + x0 + pq) * D, D, lane, sb);
+    wta_keys<NDL, EXACT>(pb, rowbase, x0 + px, px, keys, lane, sa);
+    if (pq < n) wta_keys<NDL, EXACT>(pb, rowbase, x0 + pq, pq, keys, lane, sb);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < ntar; i += blockDim.x) {
@@ -90,6 +103,29 @@ __device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint32_
       atomicMin(&pb.kr[rowbase + x], k);
   }
   __syncthreads();
+}
+
+template <bool WIDE, int NDL>
+__device__ __forceinline__ void wta_dr_tile_n(const Problem& pb, int item, uint32_t* keys, int T) {
+  if (pb.D == 32 * NDL)
+    wta_dr_tile_t<WIDE, NDL, true>(pb, item, keys, T);
+  else
+    wta_dr_tile_t<WIDE, NDL, false>(pb, item, keys, T);
+}
+
+// T pixels of a row (T = 64, 128 or 256), 256 threads, T + D - 1 keys of shared memory.
+template <bool WIDE>
+__device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint32_t* keys, int T) {
+  switch ((pb.D + 31) / 32) {
+    case 1: wta_dr_tile_n<WIDE, 1>(pb, item, keys, T); break;
+    case 2: wta_dr_tile_n<WIDE, 2>(pb, item, keys, T); break;
+    case 3: wta_dr_tile_n<WIDE, 3>(pb, item, keys, T); break;
+    case 4: wta_dr_tile_n<WIDE, 4>(pb, item, keys, T); break;
+    case 5: wta_dr_tile_n<WIDE, 5>(pb, item, keys, T); break;
+    case 6: wta_dr_tile_n<WIDE, 6>(pb, item, keys, T); break;
+    case 7: wta_dr_tile_n<WIDE, 7>(pb, item, keys, T); break;
+    default: wta_dr_tile_n<WIDE, 8>(pb, item, keys, T); break;
+  }
 }
 
 constexpr int kMedTW = 64;  // median tile: 64 x 4 pixels, one per thread

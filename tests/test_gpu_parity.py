@@ -1,6 +1,8 @@
 """GPU path vs the CPU oracle, bit-exact on every intermediate (cost, aggregated volume, D^L,
 D^R, LR mask) and on the final map. All arithmetic of the method is integer, so the bar is
 equality, not a tolerance."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -110,15 +112,34 @@ def test_every_tuning_is_bit_identical():
     prm = scenes.params(300, 120, 128, 9, 7, 10, 120, 8, 3)
     ref, rdbg = _oracle(left, right, prm)
     n = 0
-    for dpl in (4, 8):
-        for warps in (1, 4, 8):
-            for chunk in (64, 128, 256):
-                t = binding.res2tac_tuning(dpl, warps, chunk, 0)
-                out, got = _gpu(left, right, prm, tuning=t)
-                assert np.array_equal(out, ref), (dpl, warps, chunk)
-                assert np.array_equal(got["agg"], rdbg["agg"])
-                n += 1
-    assert n == 18
+    for dpl, warps, chunk, sdpl, mode in itertools.product((4, 8), (1, 4, 8), (64, 256), (16, 32),
+                                                           (1, 2)):
+        t = binding.res2tac_tuning(dpl, warps, chunk, sdpl, mode, 0)
+        out, got = _gpu(left, right, prm, tuning=t)
+        assert np.array_equal(out, ref), (dpl, warps, chunk, sdpl, mode)
+        assert np.array_equal(got["agg"], rdbg["agg"])
+        n += 1
+    assert n == 48
+
+
+@pytest.mark.parametrize("D", [48, 80, 96, 144, 160, 256])
+def test_partial_lane_groups_every_mode(D):
+    # D that leaves lanes of a group without disparities, in both row modes and both sheared
+    # widths the D allows
+    rng = np.random.default_rng(D)
+    W, H = 97, 45
+    left = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    right = np.roll(left, -5, axis=1)
+    prm = scenes.params(W, H, D, 9, 7, 7, 90, 8, 3)
+    ref, rdbg = _oracle(left, right, prm)
+    for sdpl in (16, 32):
+        if D % sdpl:
+            continue
+        for mode in (1, 2):
+            t = binding.res2tac_tuning(0, 0, 0, sdpl, mode, 0)
+            out, got = _gpu(left, right, prm, tuning=t)
+            assert np.array_equal(got["agg"], rdbg["agg"]), (sdpl, mode)
+            assert np.array_equal(out, ref), (sdpl, mode)
 
 
 def test_repeatable_and_host_path():
