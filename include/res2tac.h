@@ -84,17 +84,17 @@ typedef struct res2tac_pair {
  * agg_warps: warps per block of both aggregation kernels (1..16).
  * wta_chunk: pixels per block of the winner-takes-all / right-disparity kernel (64, 128 or
  *   256; one warp per pixel at a time).
- * shear_dpl: disparities per lane of the column / diagonal path kernel: 16, or 32 when
- *   D % 32 == 0.
+ * shear_dpl: disparities per lane of the column / diagonal path kernel: 8, 16 or 32, with
+ *   D % shear_dpl == 0.
  * row_mode: 1 = both directions of a row in one lane group, 2 = one direction per group.
- * reserved: set to 0. */
+ * shear_cpl: chains per lane of the column / diagonal path kernel (1 or 2). */
 typedef struct res2tac_tuning {
   int32_t agg_dpl;
   int32_t agg_warps;
   int32_t wta_chunk;
   int32_t shear_dpl;
   int32_t row_mode;
-  int32_t reserved;
+  int32_t shear_cpl;
 } res2tac_tuning;
 
 /* Validates *p, allocates the context's device scratch for a W x H x D pair on the current

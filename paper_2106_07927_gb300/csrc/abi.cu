@@ -233,7 +233,7 @@ int res2tac_get_tuning(res2tac_t h, res2tac_tuning* t) {
   t->wta_chunk = h->tuning.wta_chunk;
   t->shear_dpl = h->tuning.shear_dpl;
   t->row_mode = h->tuning.row_split ? 2 : 1;
-  t->reserved = 0;
+  t->shear_cpl = h->tuning.shear_cpl;
   return RES2TAC_OK;
 }
 
@@ -245,10 +245,13 @@ int res2tac_set_tuning(res2tac_t h, const res2tac_tuning* t) {
   if (t->wta_chunk) n.wta_chunk = t->wta_chunk;
   if (t->shear_dpl) n.shear_dpl = t->shear_dpl;
   if (t->row_mode) n.row_split = t->row_mode == 2 ? 1 : (t->row_mode == 1 ? 0 : -1);
+  if (t->shear_cpl) n.shear_cpl = t->shear_cpl;
   if (!r2t::tuning_valid(n, h->p.max_disp))
     return fail(RES2TAC_EINVAL,
-                "tuning (dpl %d, warps %d, chunk %d, shear dpl %d, row mode %d) invalid for D = %d",
-                n.agg_dpl, n.agg_warps, n.wta_chunk, n.shear_dpl, t->row_mode, h->p.max_disp);
+                "tuning (dpl %d, warps %d, chunk %d, shear dpl %d, row mode %d, shear cpl %d) "
+                "invalid for D = %d",
+                n.agg_dpl, n.agg_warps, n.wta_chunk, n.shear_dpl, t->row_mode, n.shear_cpl,
+                h->p.max_disp);
   h->tuning = n;
   return RES2TAC_OK;
 }
@@ -261,15 +264,16 @@ int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int
   cudaStream_t st = (cudaStream_t)s;
   std::vector<r2t::Tuning> cands;
   const int dpls[3] = {2, 4, 8}, warps[3] = {2, 4, 8}, chunks[3] = {64, 128, 256};
-  const int sdpls[2] = {16, 32};
+  const int sdpls[3] = {8, 16, 32};
   for (int a : dpls)
     for (int w : warps)
       for (int c : chunks)
         for (int sd : sdpls)
-          for (int split = 0; split < 2; split++) {
-            r2t::Tuning t{a, w, c, sd, split};
-            if (r2t::tuning_valid(t, h->p.max_disp)) cands.push_back(t);
-          }
+          for (int split = 0; split < 2; split++)
+            for (int cpl = 1; cpl <= 2; cpl++) {
+              r2t::Tuning t{a, w, c, sd, split, cpl};
+              if (r2t::tuning_valid(t, h->p.max_disp)) cands.push_back(t);
+            }
   if (cands.empty()) return fail(RES2TAC_EINVAL, "no valid tuning");
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)

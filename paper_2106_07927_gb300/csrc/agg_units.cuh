@@ -15,14 +15,14 @@ __global__ void __launch_bounds__(512) agg_row_kernel(Problem pb, Method mt) {
   agg_rows<DPL, LPL, WIDE, FULL, SPLIT>(pb, mt, warp * (32 / LPL), 0x7FFFFFFF);
 }
 
-template <int DPL, int WD, bool WIDE, bool FULL>
+template <int DPL, int WD, int CPL, bool WIDE, bool FULL>
 __global__ void __launch_bounds__(256) agg_shear_kernel(Problem pb, Method mt, int items) {
   extern __shared__ __align__(16) uint8_t shm[];
   const int wib = threadIdx.x >> 5;
   const int item = blockIdx.x * (blockDim.x >> 5) + wib;
   if (item >= items) return;  // whole warp
-  uint8_t* base = shm + wib * shear_smem_bytes(DPL, WIDE);
-  agg_shear<DPL, WD, WIDE, FULL>(pb, mt, item, base, base + shear_ring_bytes(DPL));
+  uint8_t* base = shm + wib * shear_smem_bytes(DPL, WIDE, CPL);
+  agg_shear<DPL, WD, CPL, WIDE, FULL>(pb, mt, item, base, base + shear_ring_bytes(DPL, CPL));
 }
 
 template <int DPL, int LPL, bool WIDE, bool SPLIT>
@@ -61,39 +61,51 @@ cudaError_t launch_rows(const Problem& pb, const Method& mt, const Tuning& tn,
                       : launch_rows_s<WIDE, false>(pb, mt, tn, s);
 }
 
-template <int DPL, int WD, bool WIDE>
+template <int DPL, int WD, int CPL, bool WIDE>
 static cudaError_t launch_shear_t(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
-  const int items = shear_items(pb.W, pb.D, DPL, mt.num_paths);
+  const int items = shear_items(pb.W, pb.D, DPL, mt.num_paths, CPL);
   if (warps > 8) warps = 8;  // blocks of at most 256 threads (the kernel's launch bound)
+  while (warps > 1 && warps * shear_smem_bytes(DPL, WIDE, CPL) > (200 << 10)) warps--;
   const int grid = (items + warps - 1) / warps;
-  const size_t smem = (size_t)warps * shear_smem_bytes(DPL, WIDE);
+  const size_t smem = (size_t)warps * shear_smem_bytes(DPL, WIDE, CPL);
   if (pb.D == DPL * WD) {
-    cudaFuncSetAttribute(agg_shear_kernel<DPL, WD, WIDE, true>,
+    cudaFuncSetAttribute(agg_shear_kernel<DPL, WD, CPL, WIDE, true>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    agg_shear_kernel<DPL, WD, WIDE, true><<<grid, warps * 32, smem, s>>>(pb, mt, items);
+    agg_shear_kernel<DPL, WD, CPL, WIDE, true><<<grid, warps * 32, smem, s>>>(pb, mt, items);
   } else {
-    cudaFuncSetAttribute(agg_shear_kernel<DPL, WD, WIDE, false>,
+    cudaFuncSetAttribute(agg_shear_kernel<DPL, WD, CPL, WIDE, false>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    agg_shear_kernel<DPL, WD, WIDE, false><<<grid, warps * 32, smem, s>>>(pb, mt, items);
+    agg_shear_kernel<DPL, WD, CPL, WIDE, false><<<grid, warps * 32, smem, s>>>(pb, mt, items);
   }
   return cudaGetLastError();
 }
 
-template <bool WIDE>
-cudaError_t launch_shear(const Problem& pb, const Method& mt, const Tuning& tn,
-                                cudaStream_t s) {
+template <int CPL, bool WIDE>
+static cudaError_t launch_shear_c(const Problem& pb, const Method& mt, const Tuning& tn,
+                                  cudaStream_t s) {
   switch (tn.shear_dpl * 100 + shear_width(pb.D, tn.shear_dpl)) {
-    case 1601: return launch_shear_t<16, 1, WIDE>(pb, mt, tn.agg_warps, s);
-    case 1602: return launch_shear_t<16, 2, WIDE>(pb, mt, tn.agg_warps, s);
-    case 1604: return launch_shear_t<16, 4, WIDE>(pb, mt, tn.agg_warps, s);
-    case 1608: return launch_shear_t<16, 8, WIDE>(pb, mt, tn.agg_warps, s);
-    case 1616: return launch_shear_t<16, 16, WIDE>(pb, mt, tn.agg_warps, s);
-    case 3201: return launch_shear_t<32, 1, WIDE>(pb, mt, tn.agg_warps, s);
-    case 3202: return launch_shear_t<32, 2, WIDE>(pb, mt, tn.agg_warps, s);
-    case 3204: return launch_shear_t<32, 4, WIDE>(pb, mt, tn.agg_warps, s);
-    case 3208: return launch_shear_t<32, 8, WIDE>(pb, mt, tn.agg_warps, s);
+    case 802: return launch_shear_t<8, 2, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 804: return launch_shear_t<8, 4, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 808: return launch_shear_t<8, 8, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 816: return launch_shear_t<8, 16, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 832: return launch_shear_t<8, 32, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 1601: return launch_shear_t<16, 1, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 1602: return launch_shear_t<16, 2, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 1604: return launch_shear_t<16, 4, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 1608: return launch_shear_t<16, 8, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 1616: return launch_shear_t<16, 16, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 3201: return launch_shear_t<32, 1, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 3202: return launch_shear_t<32, 2, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 3204: return launch_shear_t<32, 4, CPL, WIDE>(pb, mt, tn.agg_warps, s);
+    case 3208: return launch_shear_t<32, 8, CPL, WIDE>(pb, mt, tn.agg_warps, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <bool WIDE>
+cudaError_t launch_shear(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s) {
+  return tn.shear_cpl == 2 ? launch_shear_c<2, WIDE>(pb, mt, tn, s)
+                           : launch_shear_c<1, WIDE>(pb, mt, tn, s);
 }
 
 // ------------------------------------------------------------------------------- batch kernels
@@ -127,9 +139,9 @@ template <int DPL, int WD, bool WIDE>
 __device__ __forceinline__ void shear_full(const Problem& pb, const Method& mt, int item,
                                            uint8_t* base) {
   if (pb.D == DPL * WD)
-    agg_shear<DPL, WD, WIDE, true>(pb, mt, item, base, base + shear_ring_bytes(DPL));
+    agg_shear<DPL, WD, 1, WIDE, true>(pb, mt, item, base, base + shear_ring_bytes(DPL, 1));
   else
-    agg_shear<DPL, WD, WIDE, false>(pb, mt, item, base, base + shear_ring_bytes(DPL));
+    agg_shear<DPL, WD, 1, WIDE, false>(pb, mt, item, base, base + shear_ring_bytes(DPL, 1));
 }
 
 // Batch pairs use the default 16 disparities per lane. base: this warp's

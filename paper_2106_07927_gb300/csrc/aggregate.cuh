@@ -356,20 +356,23 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
 constexpr int kShearRing = 8;  // steps in the cost ring; 2 steps per cp.async group, 6 in flight
 __host__ __device__ inline int shear_kinds(int num_paths) { return num_paths == 8 ? 6 : 2; }
 __host__ __device__ inline int shear_dpl_default(int D) { return 16; }
+__host__ __device__ inline int shear_cpl_default(int D) { return 1; }
 __host__ __device__ inline int shear_width(int D, int dpl) { return pow2ceil(D / dpl); }
-// Warp items of one pair: kinds x groups of 32 / width adjacent chains.
-__host__ __device__ inline int shear_items(int W, int D, int dpl, int num_paths) {
-  const int cpw = 32 / shear_width(D, dpl);
-  return shear_kinds(num_paths) * ((W + cpw - 1) / cpw);
+// Warp items of one pair: kinds x groups of cpl * 32 / width adjacent chains (cpl chains per lane).
+__host__ __device__ inline int shear_items(int W, int D, int dpl, int num_paths, int cpl) {
+  const int ch = cpl * (32 / shear_width(D, dpl));
+  return shear_kinds(num_paths) * ((W + ch - 1) / ch);
 }
-// Shared memory of one warp: the cost ring (kShearRing steps of 32 / width pixel vectors of D
-// bytes, at most 32 dpl bytes per step) and the staging buffer of one step's sums.
-__host__ __device__ inline int shear_ring_bytes(int dpl) { return kShearRing * 32 * dpl; }
-__host__ __device__ inline int shear_smem_bytes(int dpl, bool wide) {
-  return shear_ring_bytes(dpl) + 32 * dpl * (wide ? 4 : 2);
+// Shared memory of one warp: the cost ring (kShearRing steps of cpl * 32 / width pixel vectors of
+// D bytes, at most 32 cpl dpl bytes per step) and the staging buffer of one step's sums.
+__host__ __device__ inline int shear_ring_bytes(int dpl, int cpl) { return kShearRing * 32 * dpl * cpl; }
+__host__ __device__ inline int shear_smem_bytes(int dpl, bool wide, int cpl) {
+  return shear_ring_bytes(dpl, cpl) + 32 * dpl * cpl * (wide ? 4 : 2);
 }
-// Per warp for the default width of every D (shear_dpl_default is 16 for all D).
-__host__ __device__ inline int shear_default_smem_bytes(bool wide) { return shear_smem_bytes(16, wide); }
+// Per warp for the default configuration of every D.
+__host__ __device__ inline int shear_default_smem_bytes(bool wide) {
+  return shear_smem_bytes(16, wide, 1);
+}
 
 // Position, in 16-byte pieces, of piece i of pixel slot c in a buffer of pixel vectors of pp
 // pieces each. When pp is a power of two the pieces of slot c are permuted by c, so lanes that
@@ -395,28 +398,35 @@ __device__ __forceinline__ unsigned long long lds64(uint32_t a) {
   return r;
 }
 
-// Warp item `item` of the sheared-column kernel: 32 / WD adjacent chains of one kind, WD lanes
-// per chain, DPL disparities per lane (lane member lig owns [lig DPL, (lig + 1) DPL)). FULL: every
-// lane owns disparities (D == WD * DPL). SH0: the kind has shear 0 (columns), so its runs never
-// wrap and its chains never restart. ring / stage: this warp's shear_ring_bytes(DPL) and
-// 32 DPL (2 or 4) bytes of shared memory, 16-byte aligned.
+// Warp item of the sheared-column kernel: CH = CPL * 32 / WD adjacent chains of one kind, WD lanes
+// per chain and CPL chains per lane (lane (c, lig) walks chains c, c + 32 / WD, ...), DPL
+// disparities per lane and chain (member lig owns [lig DPL, (lig + 1) DPL)). FULL: every lane owns
+// disparities (D == WD * DPL). SH0: the kind has shear 0 (columns), so its runs never wrap and its
+// chains never restart. ring / stage: this warp's shear_ring_bytes(DPL, CPL) and
+// 32 CPL DPL (2 or 4) bytes of shared memory, 16-byte aligned.
 //
 // Per step (one row): the warp's costs were copied 6 steps earlier by all lanes, each lane taking
 // 16-byte pieces of the contiguous pixel run so that every copy instruction is coalesced; after
 // cp.async.wait_group and __syncwarp each lane reads its own pieces. The new L values go to the
 // staging buffer in the volume's layout, and after __syncwarp every lane adds 8-byte units of the
 // run into S, consecutive lanes on consecutive units. Lanes of chains past the image's last column
-// (and, FULL, every lane) compute unconditionally; only their copies and adds are skipped.
-template <int DPL, int WD, bool WIDE, bool FULL, bool SH0>
+// (and, FULL, every lane) compute unconditionally; only their copies and adds are skipped. With
+// CPL = 2 the step's bookkeeping (syncs, ring slots, run pointers) serves twice the chains and the
+// two chains' arithmetic interleaves.
+template <int DPL, int WD, int CPL, bool WIDE, bool FULL, bool SH0>
 __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt, int kind, int j0,
                                             uint8_t* ring, uint8_t* stage) {
   constexpr int NP = DPL / 2;
-  constexpr int CPW = 32 / WD;         // chains per warp
+  constexpr int CPW = 32 / WD;                // chains per warp and lane slot
+  constexpr int CH = CPW * CPL;               // chains of the warp item
   constexpr int KS = kShearRing;
-  constexpr int BPE = WIDE ? 4 : 2;    // bytes per sum
-  constexpr int NVC = DPL / 16;        // cost pieces a lane copies / reads per step
-  constexpr int NVS = DPL * BPE / 16;  // sum pieces a lane stages per step
-  constexpr int NR = DPL * BPE / 8;    // 8-byte atomic adds a lane issues per step (at most)
+  constexpr int BPE = WIDE ? 4 : 2;           // bytes per sum
+  constexpr int CW = DPL < 16 ? DPL : 16;     // disparities per cost read (8 or 16 bytes)
+  constexpr int NVC = DPL / CW;               // cost reads a lane makes per chain and step
+  constexpr int NCP = CPL * DPL >= 16 ? CPL * DPL / 16 : 1;  // 16-byte pieces a lane copies per step
+  constexpr int NVS = DPL * BPE / 16;         // sum pieces a lane stages per chain and step
+  constexpr int NR = CPL * DPL * BPE / 8;     // 8-byte atomic adds a lane issues per step (at most)
+  constexpr int NA = NP < 4 ? NP : 4;         // independent accumulators of a lane's minimum
   const int lane = threadIdx.x & 31;
   const int lig = lane % WD, c = lane / WD;
   const int W = pb.W, H = pb.H;
@@ -424,8 +434,8 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   const int PP = D / 16;        // cost pieces per pixel
   const int PS = D * BPE / 16;  // sum pieces per pixel
   const int UPP = D * BPE / 8;  // 8-byte sum units per pixel
-  const int n = min(CPW, W - j0);  // chains of this warp
-  const bool nfull = n == CPW;
+  const int n = min(CH, W - j0);  // chains of this warp item
+  const bool nfull = n == CH;
   const int sh = SH0 ? 0 : (kind < 4 ? 1 : -1);
   const bool back = (kind & 1) != 0;
   const int dy = back ? -1 : 1, dx = back ? -sh : sh;
@@ -433,21 +443,25 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   const int ystart = back ? H - 1 : 0;
   int xs = (j0 + sh * ystart) % W;  // pixel of chain 0 in the current row
   if (xs < 0) xs += W;
-  const bool active = c < n && (FULL || lig * DPL < D);
-  const bool owns = FULL || lig * DPL < D;  // the lane holds disparities of its chain
-  const int slot_bytes = CPW * D;
+  const bool owns = FULL || lig * DPL < D;  // the lane holds disparities of its chains
+  const int slot_bytes = CH * D;
   const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
+  const uint32_t ring_end = ring_s + KS * slot_bytes;
   const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
   const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
-  const int64_t rowstep = (int64_t)dy * W;  // pixels from one row to the next
+  // bytes from one step's run to the next (before any wrap correction)
+  const int64_t cstride = ((int64_t)dy * W + dx) * D, astride = cstride * BPE;
+  const int64_t cwrap = (int64_t)W * D, awrap = cwrap * BPE;  // one row, subtracted at a wrap
 
   // Per-lane pieces, fixed for the whole walk: cost piece v of the step's run (chain cp_c[v],
   // shared offset cp_s[v] inside a ring slot) and 8-byte sum unit r (chain su_c[r], staging offset
-  // su_s[r]). A run that does not wrap around the image edge is contiguous in memory, so piece v
-  // then sits 16 (lane + 32 v) bytes and unit r 8 (lane + 32 r) bytes after the run's start.
-  int cp_c[NVC], cp_s[NVC], su_c[NR], su_s[NR];
+  // su_s[r]); the lane's own cost pieces (rd_s) and sum pieces (st_s) of each of its chains. A run
+  // that does not wrap around the image edge is contiguous in memory, so piece v then sits
+  // 16 (lane + 32 v) bytes and unit r 8 (lane + 32 r) bytes after the run's start.
+  int cp_c[NCP], cp_s[NCP], su_c[NR], su_s[NR], rd_s[CPL][NVC], st_s[CPL][NVS];
+  bool act[CPL];  // the lane's chain g exists and the lane owns disparities of it
 #pragma unroll
-  for (int v = 0; v < NVC; v++) {
+  for (int v = 0; v < NCP; v++) {
     const int p = lane + 32 * v;
     const int pc = p / PP, pi = p - pc * PP;
     cp_c[v] = pc < n ? pc : -1;
@@ -460,54 +474,71 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
     su_c[r] = qc < n ? qc : -1;
     su_s[r] = swz(qc, qk >> 1, PS) * 16 + (qk & 1) * 8;
   }
+#pragma unroll
+  for (int g = 0; g < CPL; g++) {
+    const int cg = c + CPW * g;
+    act[g] = owns && cg < n;
+#pragma unroll
+    for (int v = 0; v < NVC; v++) {
+      const int b = lig * DPL + v * CW;  // byte of the pixel's cost vector
+      rd_s[g][v] = swz(cg, b >> 4, PP) * 16 + (b & 15);
+    }
+#pragma unroll
+    for (int v = 0; v < NVS; v++) st_s[g][v] = swz(cg, lig * NVS + v, PS) * 16;
+  }
 
-  // copy cursor: chain-0 pixel (row-major index) of the next step to copy, and its column
-  int64_t pc_next = (int64_t)ystart * W + xs;
+  // copy cursor: global start of the next step's run, its column, and its ring slot
+  const uint8_t* crun = pb.cost + ((int64_t)ystart * W + xs) * D;
   int xc = xs;
+  uint32_t cslot = ring_s;
   auto copy_step = [&](int t) {
     if (t < H) {
-      const uint32_t slot = ring_s + (uint32_t)((t % KS) * slot_bytes);
-      const uint8_t* run = pb.cost + pc_next * D;
-      if (nfull && (SH0 || xc + CPW <= W)) {  // every piece, contiguous run
+      if (nfull && (SH0 || xc + CH <= W)) {  // every piece, contiguous run
+        const uint8_t* src = crun + 16 * lane;
 #pragma unroll
-        for (int v = 0; v < NVC; v++)
-          if (FULL || cp_c[v] >= 0)
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(slot + cp_s[v]),
-                         "l"(run + 16 * (lane + 32 * v)));
+        for (int v = 0; v < NCP; v++)
+          if ((FULL && CPL * DPL >= 16) || cp_c[v] >= 0)  // (a step has 32 NCP pieces then)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(cslot + cp_s[v]),
+                         "l"(src + 512 * v));
       } else {
 #pragma unroll
-        for (int v = 0; v < NVC; v++) {
+        for (int v = 0; v < NCP; v++) {
           if (cp_c[v] >= 0) {
             const int p = lane + 32 * v;
             const int pc = cp_c[v], pi = p - pc * PP;
             const int back_w = (!SH0 && xc + pc >= W) ? W : 0;  // wrapped to the row's start
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(slot + cp_s[v]),
-                         "l"(run + ((int64_t)pc - back_w) * D + pi * 16));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(cslot + cp_s[v]),
+                         "l"(crun + ((int64_t)pc - back_w) * D + pi * 16));
           }
         }
       }
-      pc_next += rowstep;
+      crun += cstride;
+      cslot += slot_bytes;
+      if (cslot == ring_end) cslot = ring_s;
       if (!SH0) {
         xc += dx;
-        pc_next += dx;
         if (xc >= W) {
           xc -= W;
-          pc_next -= W;
+          crun -= cwrap;
         } else if (xc < 0) {
           xc += W;
-          pc_next += W;
+          crun += cwrap;
         }
       }
     }
   };
 
-  uint32_t L[NP];
+  uint32_t L[CPL][NP], mm[CPL];
+  int x[CPL];  // the lane's chain pixels (meaningful for chains that exist)
 #pragma unroll
-  for (int k = 0; k < NP; k++) L[k] = owns ? 0u : kSent * 0x10001u;
-  uint32_t mm = 0;
-  int x = xs + c;  // this lane's chain pixel (meaningful for chains c < n)
-  if (x >= W) x -= W;
-  int64_t prun = (int64_t)ystart * W + xs;  // chain-0 pixel of the current step
+  for (int g = 0; g < CPL; g++) {
+#pragma unroll
+    for (int k = 0; k < NP; k++) L[g][k] = owns ? 0u : kSent * 0x10001u;
+    mm[g] = 0;
+    x[g] = (xs + c + CPW * g) % W;
+  }
+  uint8_t* arun = reinterpret_cast<uint8_t*>(pb.agg) + ((int64_t)ystart * W + xs) * D * BPE;
+  uint32_t rslot = ring_s;  // ring slot of the current step
 
   // prologue: steps 0 .. 5 in flight as three groups of two
 #pragma unroll
@@ -529,66 +560,112 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
         asm volatile("cp.async.wait_group 3;" ::: "memory");
         __syncwarp();
       }
-      const uint32_t slot = ring_s + (uint32_t)((t % KS) * slot_bytes);
-      if (!SH0) {
-        if (__any_sync(0xffffffffu, x == edge)) {  // a new line of the path enters: L = C
-          if (x == edge) {
+      const uint32_t cur = rslot;  // ring slot of this step
+      rslot += slot_bytes;
+      if (rslot == ring_end) rslot = ring_s;
+      uint4 raw[CPL][NVC];  // the step's cost pieces, all loaded before any is used
 #pragma unroll
-            for (int k = 0; k < NP; k++) L[k] = owns ? 0u : kSent * 0x10001u;
-            mm = 0;
+      for (int g = 0; g < CPL; g++)
+#pragma unroll
+        for (int v = 0; v < NVC; v++)
+          if (CW == 16) {
+            raw[g][v] = owns ? lds128(cur + rd_s[g][v]) : make_uint4(0, 0, 0, 0);
+          } else {
+            const unsigned long long r8 = owns ? lds64(cur + rd_s[g][v]) : 0ull;
+            raw[g][v] = make_uint4((uint32_t)r8, (uint32_t)(r8 >> 32), 0u, 0u);
+          }
+      if (!SH0) {
+        bool hit = false;
+#pragma unroll
+        for (int g = 0; g < CPL; g++) hit |= x[g] == edge;
+        if (__any_sync(0xffffffffu, hit)) {  // a new line of the path enters: L = C
+#pragma unroll
+          for (int g = 0; g < CPL; g++) {
+            if (x[g] == edge) {
+#pragma unroll
+              for (int k = 0; k < NP; k++) L[g][k] = owns ? 0u : kSent * 0x10001u;
+              mm[g] = 0;
+            }
           }
         }
       }
-      uint32_t cst[NP];
-      if (owns) {
+      // Neighbour pairs are formed on the fly from the old L: xp = (L(d0 - 1), L(d0)) of pair k,
+      // xn the same for pair k + 1; L[k] is overwritten only after both were formed.
+      uint32_t xp[CPL], dn[CPL], mP2[CPL], lm[CPL][NA];
 #pragma unroll
-        for (int v = 0; v < NVC; v++) {
-          const uint4 r = lds128(slot + (uint32_t)(swz(c, lig * NVC + v, PP) * 16));
-          unpack4(r.x, cst[8 * v + 0], cst[8 * v + 1]);
-          unpack4(r.y, cst[8 * v + 2], cst[8 * v + 3]);
-          unpack4(r.z, cst[8 * v + 4], cst[8 * v + 5]);
-          unpack4(r.w, cst[8 * v + 6], cst[8 * v + 7]);
+      for (int g = 0; g < CPL; g++) {
+        uint32_t up = kSent << 16;
+        dn[g] = kSent;
+        if (WD > 1) {
+          const uint32_t a = __shfl_up_sync(0xffffffffu, L[g][NP - 1], 1, WD);
+          const uint32_t b = __shfl_down_sync(0xffffffffu, L[g][0], 1, WD);
+          up = lig == 0 ? up : a;
+          dn[g] = lig == WD - 1 ? dn[g] : b;
         }
-      } else {
+        xp[g] = __byte_perm(up, L[g][0], 0x5432);
+        mP2[g] = mm[g] + P2P2;
 #pragma unroll
-        for (int k = 0; k < NP; k++) cst[k] = 0u;
-      }
-      uint32_t X[NP + 1];
-      neighbours<NP, WD>(L, lig, X);
-      const uint32_t mP2 = mm + P2P2;
-      uint32_t lm[NP];
-#pragma unroll
-      for (int k = 0; k < NP; k++) {
-        const uint32_t tt = vmin2(X[k], X[k + 1]) + P1P1;
-        const uint32_t uu = vmin2(vmin2(L[k], tt), mP2);  // >= m(q) in both halves
-        const uint32_t ln = uu + cst[k] - mm;              // each half in [0, 255 + P2]
-        L[k] = owns ? ln : kSent * 0x10001u;
-        lm[k] = L[k];
+        for (int a = 0; a < NA; a++) lm[g][a] = 0xFFFFFFFFu;
       }
 #pragma unroll
-      for (int w = 1; w < NP; w *= 2)  // tree minimum of the lane's pairs
+      for (int v = 0; v < NVC; v++) {  // CW disparities (CW / 2 pairs) per cost read
+        uint32_t cst[CPL][8];
 #pragma unroll
-        for (int k = 0; k + w < NP; k += 2 * w) lm[k] = vmin2(lm[k], lm[k + w]);
-      mm = group_min<WD>(halves_min(lm[0]));
-      if (FULL || active) {
+        for (int g = 0; g < CPL; g++) {
+          unpack4(raw[g][v].x, cst[g][0], cst[g][1]);
+          unpack4(raw[g][v].y, cst[g][2], cst[g][3]);
+          unpack4(raw[g][v].z, cst[g][4], cst[g][5]);
+          unpack4(raw[g][v].w, cst[g][6], cst[g][7]);
+        }
 #pragma unroll
-        for (int v = 0; v < NVS; v++) {
-          const uint32_t a = stage_s + (uint32_t)(swz(c, lig * NVS + v, PS) * 16);
-          if (!WIDE)
-            sts128(a, L[4 * v], L[4 * v + 1], L[4 * v + 2], L[4 * v + 3]);
-          else
-            sts128(a, L[2 * v] & 0xFFFFu, L[2 * v] >> 16, L[2 * v + 1] & 0xFFFFu,
-                   L[2 * v + 1] >> 16);
+        for (int j = 0; j < CW / 2; j++) {
+          const int k = (CW / 2) * v + j;
+#pragma unroll
+          for (int g = 0; g < CPL; g++) {
+            const uint32_t xn =
+                __byte_perm(L[g][k], k + 1 < NP ? L[g][(k + 1) % NP] : dn[g], 0x5432);
+            const uint32_t tt = vmin2(xp[g], xn) + P1P1;
+            const uint32_t uu = vmin2(vmin2(L[g][k], tt), mP2[g]);  // >= m(q) in both halves
+            const uint32_t ln = uu + cst[g][j] - mm[g];             // each half in [0, 255 + P2]
+            L[g][k] = owns ? ln : kSent * 0x10001u;
+            lm[g][k % NA] = vmin2(lm[g][k % NA], L[g][k]);
+            xp[g] = xn;
+          }
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < CPL; g++) {
+#pragma unroll
+        for (int w = 1; w < NA; w *= 2)
+#pragma unroll
+          for (int a = 0; a + w < NA; a += 2 * w) lm[g][a] = vmin2(lm[g][a], lm[g][a + w]);
+        mm[g] = group_min<WD>(halves_min(lm[g][0]));
+      }
+#pragma unroll
+      for (int g = 0; g < CPL; g++) {
+        if (FULL || act[g]) {
+#pragma unroll
+          for (int v = 0; v < NVS; v++) {
+            const uint32_t a = stage_s + (uint32_t)st_s[g][v];
+            if (!WIDE)
+              sts128(a, L[g][4 * v], L[g][4 * v + 1], L[g][4 * v + 2], L[g][4 * v + 3]);
+            else
+              sts128(a, L[g][2 * v] & 0xFFFFu, L[g][2 * v] >> 16, L[g][2 * v + 1] & 0xFFFFu,
+                     L[g][2 * v + 1] >> 16);
+          }
         }
       }
       __syncwarp();
-      uint8_t* run = reinterpret_cast<uint8_t*>(pb.agg) + prun * D * BPE;
-      if (nfull && (SH0 || xs + CPW <= W)) {  // every unit, contiguous run
+      // all staged units first (the shared loads are ordered asm), then the atomic adds
+      unsigned long long sv[NR];
+#pragma unroll
+      for (int r = 0; r < NR; r++) sv[r] = lds64(stage_s + (uint32_t)su_s[r]);
+      if (nfull && (SH0 || xs + CH <= W)) {  // every unit, contiguous run
+        uint8_t* dst = arun + 8 * lane;
 #pragma unroll
         for (int r = 0; r < NR; r++)
           if (FULL || su_c[r] >= 0)
-            atomicAdd(reinterpret_cast<unsigned long long*>(run + 8 * (lane + 32 * r)),
-                      lds64(stage_s + (uint32_t)su_s[r]));
+            atomicAdd(reinterpret_cast<unsigned long long*>(dst + 256 * r), sv[r]);
       } else {
 #pragma unroll
         for (int r = 0; r < NR; r++) {
@@ -596,24 +673,26 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
             const int q = lane + 32 * r;
             const int back_w = (!SH0 && xs + su_c[r] >= W) ? W : 0;  // wrapped to the row's start
             atomicAdd(reinterpret_cast<unsigned long long*>(
-                          run + (int64_t)(q - back_w * UPP) * 8),
-                      lds64(stage_s + (uint32_t)su_s[r]));
+                          arun + (int64_t)(q - back_w * UPP) * 8),
+                      sv[r]);
           }
         }
       }
-      prun += rowstep;
+      arun += astride;
       if (!SH0) {
         xs += dx;
-        prun += dx;
         if (xs >= W) {
           xs -= W;
-          prun -= W;
+          arun -= awrap;
         } else if (xs < 0) {
           xs += W;
-          prun += W;
+          arun += awrap;
         }
-        x += dx;
-        x = x >= W ? x - W : (x < 0 ? x + W : x);
+#pragma unroll
+        for (int g = 0; g < CPL; g++) {
+          x[g] += dx;
+          x[g] = x[g] >= W ? x[g] - W : (x[g] < 0 ? x[g] + W : x[g]);
+        }
       }
     }
   }
@@ -621,17 +700,17 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
 }
 
 // Warp item `item` of a pair's sheared-column work (see shear_items).
-template <int DPL, int WD, bool WIDE, bool FULL>
+template <int DPL, int WD, int CPL, bool WIDE, bool FULL>
 __device__ __forceinline__ void agg_shear(const Problem& pb, const Method& mt, int item,
                                           uint8_t* ring, uint8_t* stage) {
-  constexpr int CPW = 32 / WD;
-  const int G = (pb.W + CPW - 1) / CPW;
+  constexpr int CH = CPL * (32 / WD);
+  const int G = (pb.W + CH - 1) / CH;
   const int kind = item / G;
-  const int j0 = (item - kind * G) * CPW;
+  const int j0 = (item - kind * G) * CH;
   if (kind < 2)
-    agg_shear_t<DPL, WD, WIDE, FULL, true>(pb, mt, kind, j0, ring, stage);
+    agg_shear_t<DPL, WD, CPL, WIDE, FULL, true>(pb, mt, kind, j0, ring, stage);
   else
-    agg_shear_t<DPL, WD, WIDE, FULL, false>(pb, mt, kind, j0, ring, stage);
+    agg_shear_t<DPL, WD, CPL, WIDE, FULL, false>(pb, mt, kind, j0, ring, stage);
 }
 
 }  // namespace r2t

@@ -340,8 +340,7 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
     wta_smem = std::max(wta_smem, (int)wta_smem_bytes(pb.D, wta_tile_px(pb.D)));
     const int dpl = e->dpl_by_d16[pb.D / 16];
     lk.push_back(Keyed{AggSeg{p, 0, row_units(pb.H, false), 32 / long_lanes(pb.D, dpl)}, pb.W});
-    bk.push_back(Keyed{AggSeg{p, 0, shear_items(pb.W, pb.D, shear_dpl_default(pb.D), mt.num_paths), 1},
-                       pb.H});
+    bk.push_back(Keyed{AggSeg{p, 0, shear_items(pb.W, pb.D, 16, mt.num_paths, 1), 1}, pb.H});
   }
   for (int k = 0; k < 4; k++) prefix[k * stride + n] = tot[k];
   const int nrows = write_queue(lk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 0)),

@@ -41,9 +41,10 @@ __global__ void agg_copy_kernel(const void* src, uint16_t* dst, int64_t n) {
 Tuning default_tuning(int D) {
   Tuning t;
   t.agg_dpl = long_dpl_default(D);
-  t.agg_warps = 4;
+  t.agg_warps = 1;  // one warp per block balances the sheared chains best across SMs
   t.wta_chunk = wta_tile_px(D);
   t.shear_dpl = shear_dpl_default(D);
+  t.shear_cpl = shear_cpl_default(D);
   t.row_split = 0;
   return t;
 }
@@ -54,7 +55,8 @@ bool tuning_valid(const Tuning& t, int D) {
   if ((D + t.agg_dpl - 1) / t.agg_dpl > 32) return false;
   if (t.agg_warps < 1 || t.agg_warps > 16) return false;
   if (t.wta_chunk != 64 && t.wta_chunk != 128 && t.wta_chunk != 256) return false;
-  if (t.shear_dpl != 16 && t.shear_dpl != 32) return false;
+  if (t.shear_dpl != 8 && t.shear_dpl != 16 && t.shear_dpl != 32) return false;
+  if (t.shear_cpl != 1 && t.shear_cpl != 2) return false;
   if (D % t.shear_dpl != 0) return false;
   if (t.row_split != 0 && t.row_split != 1) return false;
   return true;

@@ -12,6 +12,7 @@ struct Tuning {
   int agg_warps;  // warps per aggregation block
   int wta_chunk;  // pixels per block of the WTA / right-disparity stage
   int shear_dpl;  // disparities per lane of the sheared-column kernel (16 or 32)
+  int shear_cpl;  // chains per lane of the sheared-column kernel (1 or 2)
   int row_split;  // 1: one row direction per lane group, 0: both directions in one group
 };
 

@@ -112,14 +112,14 @@ def test_every_tuning_is_bit_identical():
     prm = scenes.params(300, 120, 128, 9, 7, 10, 120, 8, 3)
     ref, rdbg = _oracle(left, right, prm)
     n = 0
-    for dpl, warps, chunk, sdpl, mode in itertools.product((4, 8), (1, 4, 8), (64, 256), (16, 32),
-                                                           (1, 2)):
-        t = binding.res2tac_tuning(dpl, warps, chunk, sdpl, mode, 0)
+    for dpl, warps, chunk, sdpl, mode, cpl in itertools.product((4, 8), (1, 4, 8), (64, 256),
+                                                                (8, 16, 32), (1, 2), (1, 2)):
+        t = binding.res2tac_tuning(dpl, warps, chunk, sdpl, mode, cpl)
         out, got = _gpu(left, right, prm, tuning=t)
-        assert np.array_equal(out, ref), (dpl, warps, chunk, sdpl, mode)
+        assert np.array_equal(out, ref), (dpl, warps, chunk, sdpl, mode, cpl)
         assert np.array_equal(got["agg"], rdbg["agg"])
         n += 1
-    assert n == 48
+    assert n == 144
 
 
 @pytest.mark.parametrize("D", [48, 80, 96, 144, 160, 256])
@@ -132,14 +132,13 @@ def test_partial_lane_groups_every_mode(D):
     right = np.roll(left, -5, axis=1)
     prm = scenes.params(W, H, D, 9, 7, 7, 90, 8, 3)
     ref, rdbg = _oracle(left, right, prm)
-    for sdpl in (16, 32):
+    for sdpl, mode, cpl in itertools.product((8, 16, 32), (1, 2), (1, 2)):
         if D % sdpl:
             continue
-        for mode in (1, 2):
-            t = binding.res2tac_tuning(0, 0, 0, sdpl, mode, 0)
-            out, got = _gpu(left, right, prm, tuning=t)
-            assert np.array_equal(got["agg"], rdbg["agg"]), (sdpl, mode)
-            assert np.array_equal(out, ref), (sdpl, mode)
+        t = binding.res2tac_tuning(0, 0, 0, sdpl, mode, cpl)
+        out, got = _gpu(left, right, prm, tuning=t)
+        assert np.array_equal(got["agg"], rdbg["agg"]), (sdpl, mode, cpl)
+        assert np.array_equal(out, ref), (sdpl, mode, cpl)
 
 
 def test_repeatable_and_host_path():
