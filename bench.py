@@ -44,8 +44,20 @@ def _args():
     ap.add_argument("--batch-pairs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
+
+
+def _traffic():
+    """DRAM bytes (read + write) per launch of the aggregation stage, from the ncu capture recorded
+    in profiles/aggregate_traffic.json, or None when that capture is missing."""
+    p = os.path.join(ROOT, "profiles", "aggregate_traffic.json")
+    if not os.path.exists(p):
+        return None
+    return json.load(open(p)).get("dram_bytes_per_launch")
 
 
 def _dist():
@@ -329,6 +341,26 @@ def main():
             for c, *_ in singles:
                 c.close()
             bctx.close()
+        serving = None
+        if not args.no_serve and rank == 0:
+            # continuous batching over 4 streams: Poisson arrivals of uneven pairs (5 % 3840x2160,
+            # D = 256), admitted by device memory; latency = completion - arrival
+            from paper_2106_07927_gb300 import serve
+            srv = serve.Server(n_streams=4, max_batch=16)
+            reqs, pool = serve.make_requests(torch, args.serve_requests, args.serve_rate, 0, 0.05)
+            warm, _ = serve.make_requests(torch, 32, args.serve_rate, 1, 0.05, pool)
+            srv.run(warm)
+            l0 = srv.launches
+            serving = srv.run(reqs)
+            rng = np.random.default_rng(1)
+            idx = sorted(rng.choice(len(reqs), max(1, len(reqs) // 100), replace=False))
+            serving.update({
+                "rate_per_s": args.serve_rate, "streams": 4, "max_batch": 16,
+                "gpu_launches": srv.launches - l0,
+                "sample_checked_vs_single_pair": len(idx),
+                "sample_mismatches": len(serve.check_alone(srv, reqs, idx)),
+                "sizes": "as the batch, plus 5 % 3840x2160 with D = 256"})
+            srv.close()
     mean_ms = max_over_ranks(sum(step_ms) / len(step_ms))
     value = ws * de / (mean_ms / 1e3) / 1e6
     agg_ms = stage["aggregate"] / args.steps
@@ -357,13 +389,14 @@ def main():
                      "frac": round(achieved / int_peak, 3),
                      "peak_source": "measured packed-u16 min+add probe on this GPU",
                      "hbm_achieved_gbs": round(bytes_agg / (agg_ms / 1e3) / 1e9, 1),
-                     "hbm_peak_gbs": hbm, "traffic": None,
+                     "hbm_peak_gbs": hbm, "traffic": _traffic(),
                      "ops_per_launch": ops_agg, "algorithmic_bytes_per_launch": bytes_agg,
                      "dominant_stage": dominant},
         "e2e": {"value": round(ws * de * args.steps / e2e_s / 1e6, 1), "unit": "MDE/s",
                 "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
                 "ms_per_step": round(1e3 * e2e_s / args.steps, 4), "matches_device_path": e2e_ok},
         "batched": batched,
+        "serving": serving,
         "gpu_launches": launches,
         "clocks": clocks,
         "wall_s_timed_plain": round(t_wall, 3),

@@ -98,7 +98,7 @@ typedef struct res2tac_tuning {
 } res2tac_tuning;
 
 /* Validates *p, allocates the context's device scratch for a W x H x D pair on the current
- * device, and returns the handle in *out. The scratch (census maps, cost volume, aggregated
+ * device, and returns the handle in *out. The scratch (cost volume, aggregated
  * volume, intermediate maps, host staging) is owned by the context until res2tac_destroy.
  * Returns RES2TAC_EINVAL for invalid parameters, RES2TAC_ENOMEM if the scratch does not fit. */
 int res2tac_create(const res2tac_params* p, res2tac_t* out);
@@ -167,8 +167,8 @@ int res2tac_last_launch_count(res2tac_t h);
 
 /* Per-stage timing. With profiling enabled, res2tac_compute records a CUDA event on the caller's
  * stream before and after each stage. res2tac_stage_times waits for the last call and writes up
- * to n durations in milliseconds: [0] census, [1] cost (+ clearing of the aggregated volume),
- * [2] path aggregation, [3] WTA + right-disparity keys, [4] LR check + median. */
+ * to n durations in milliseconds: [0] census + cost (+ clearing of the aggregated volume),
+ * [1] path aggregation, [2] WTA + right-disparity keys, [3] LR check + median. */
 int res2tac_set_profiling(res2tac_t h, int enable);
 int res2tac_stage_times(res2tac_t h, float* ms, int n);
 
@@ -185,11 +185,11 @@ int res2tac_probe_int_peak(int iters, res2tac_stream_t s, double* lane_ops_per_s
  * cudaMalloc / cudaFree may cause. It needs no context and calls no cudaMalloc, cudaFree or
  * other allocating routine.
  * It runs the same pipeline as res2tac_compute on stream s, for the problem *p, with left /
- * right / disp and the pitches as in res2tac_compute. Its scratch (census maps, cost volume,
- * aggregated volume, intermediate maps) is one fixed device array of
+ * right / disp and the pitches as in res2tac_compute. Its scratch (cost volume, aggregated
+ * volume, intermediate maps) is one fixed device array of
  * RES2TAC_STATIC_SCRATCH_BYTES compiled into the library; every GPU that loads the library holds
  * that array until the process exits.
- * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 25 B per pixel,
+ * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 9 B per pixel,
  * 5 B per W*H*D when num_paths * (255 + p2) > 65535) is rejected with RES2TAC_ENOMEM and a
  * message giving both sizes; 640 x 480 with D = 64 fits.
  * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)

@@ -31,7 +31,7 @@ EXPORTS = (
     "res2tac_compute_static",
 )
 RES2TAC_STATIC_SCRATCH_BYTES = 80 << 20
-STAGES = ("census", "cost", "aggregate", "wta_dr", "lr_median")
+STAGES = ("census_cost", "aggregate", "wta_dr", "lr_median")
 
 
 class res2tac_params(ctypes.Structure):
@@ -200,8 +200,8 @@ def res2tac_set_profiling(h: int, enable: bool) -> None:
 
 
 def res2tac_stage_times(h: int) -> dict:
-    ms = (ctypes.c_float * 5)()
-    _check(load().res2tac_stage_times(h, ms, 5))
+    ms = (ctypes.c_float * len(STAGES))()
+    _check(load().res2tac_stage_times(h, ms, len(STAGES)))
     return dict(zip(STAGES, [float(v) for v in ms]))
 
 

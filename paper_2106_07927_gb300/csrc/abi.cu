@@ -86,7 +86,7 @@ struct res2tac_ctx {
   int last_launches;
   r2t::BatchEngine* batch;
   int profiling;
-  cudaEvent_t ev[6];  // stage boundaries of the last profiled compute
+  cudaEvent_t ev[5];  // stage boundaries of the last profiled compute
   r2t::Fork fork;     // second stream for the concurrent aggregation kernels
 };
 
@@ -149,7 +149,7 @@ void res2tac_destroy(res2tac_t h) {
   if (cur != h->device) cudaSetDevice(h->device);
   r2t::batch_destroy(h->batch);
   r2t::fork_destroy(&h->fork);
-  for (int i = 0; i < 6; i++)
+  for (int i = 0; i < 5; i++)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   cudaFree(h->scratch);
   cudaFree(h->stage_in);
@@ -318,7 +318,7 @@ int res2tac_last_launch_count(res2tac_t h) { return h ? h->last_launches : 0; }
 int res2tac_set_profiling(res2tac_t h, int enable) {
   if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
   if (enable && !h->ev[0]) {
-    for (int i = 0; i < 6; i++) {
+    for (int i = 0; i < 5; i++) {
       cudaError_t e = cudaEventCreate(&h->ev[i]);
       if (e != cudaSuccess) return fail_cuda(e, "cudaEventCreate");
     }
@@ -330,9 +330,9 @@ int res2tac_set_profiling(res2tac_t h, int enable) {
 int res2tac_stage_times(res2tac_t h, float* ms, int n) {
   if (!h || !ms || n < 0) return fail(RES2TAC_EINVAL, "NULL argument");
   if (!h->profiling || !h->ev[0]) return fail(RES2TAC_EINVAL, "profiling is not enabled");
-  cudaError_t e = cudaEventSynchronize(h->ev[5]);
+  cudaError_t e = cudaEventSynchronize(h->ev[4]);
   if (e != cudaSuccess) return fail_cuda(e, "cudaEventSynchronize");
-  for (int i = 0; i < n && i < 5; i++) {
+  for (int i = 0; i < n && i < 4; i++) {
     float t = 0;
     e = cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]);
     if (e != cudaSuccess) return fail_cuda(e, "cudaEventElapsedTime");

@@ -364,10 +364,14 @@ __host__ __device__ inline int shear_items(int W, int D, int dpl, int num_paths,
   return shear_kinds(num_paths) * ((W + ch - 1) / ch);
 }
 // Shared memory of one warp: the cost ring (kShearRing steps of cpl * 32 / width pixel vectors of
-// D bytes, at most 32 cpl dpl bytes per step) and the staging buffer of one step's sums.
+// D bytes, at most 32 cpl dpl bytes per step) and the staging buffers of the steps' sums.
 __host__ __device__ inline int shear_ring_bytes(int dpl, int cpl) { return kShearRing * 32 * dpl * cpl; }
+__host__ __device__ inline int shear_stage_bytes(int dpl, bool wide, int cpl) {
+  return 32 * dpl * cpl * (wide ? 4 : 2);
+}
+// Ring plus two staging buffers (steps alternate between them).
 __host__ __device__ inline int shear_smem_bytes(int dpl, bool wide, int cpl) {
-  return shear_ring_bytes(dpl, cpl) + 32 * dpl * cpl * (wide ? 4 : 2);
+  return shear_ring_bytes(dpl, cpl) + 2 * shear_stage_bytes(dpl, wide, cpl);
 }
 // Per warp for the default configuration of every D.
 __host__ __device__ inline int shear_default_smem_bytes(bool wide) {
@@ -403,13 +407,13 @@ __device__ __forceinline__ unsigned long long lds64(uint32_t a) {
 // disparities per lane and chain (member lig owns [lig DPL, (lig + 1) DPL)). FULL: every lane owns
 // disparities (D == WD * DPL). SH0: the kind has shear 0 (columns), so its runs never wrap and its
 // chains never restart. ring / stage: this warp's shear_ring_bytes(DPL, CPL) and
-// 32 CPL DPL (2 or 4) bytes of shared memory, 16-byte aligned.
+// 2 shear_stage_bytes(DPL, WIDE, CPL) bytes of shared memory, 16-byte aligned.
 //
 // Per step (one row): the warp's costs were copied 6 steps earlier by all lanes, each lane taking
 // 16-byte pieces of the contiguous pixel run so that every copy instruction is coalesced; after
-// cp.async.wait_group and __syncwarp each lane reads its own pieces. The new L values go to the
-// staging buffer in the volume's layout, and after __syncwarp every lane adds 8-byte units of the
-// run into S, consecutive lanes on consecutive units. Lanes of chains past the image's last column
+// cp.async.wait_group and __syncwarp each lane reads its own pieces. The new L values go to a
+// staging buffer in the volume's layout, which one bulk reduction adds into S. Lanes of chains
+// past the image's last column
 // (and, FULL, every lane) compute unconditionally; only their copies and adds are skipped. With
 // CPL = 2 the step's bookkeeping (syncs, ring slots, run pointers) serves twice the chains and the
 // two chains' arithmetic interleaves.
@@ -425,7 +429,6 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   constexpr int NVC = DPL / CW;               // cost reads a lane makes per chain and step
   constexpr int NCP = CPL * DPL >= 16 ? CPL * DPL / 16 : 1;  // 16-byte pieces a lane copies per step
   constexpr int NVS = DPL * BPE / 16;         // sum pieces a lane stages per chain and step
-  constexpr int NR = CPL * DPL * BPE / 8;     // 8-byte atomic adds a lane issues per step (at most)
   constexpr int NA = NP < 4 ? NP : 4;         // independent accumulators of a lane's minimum
   const int lane = threadIdx.x & 31;
   const int lig = lane % WD, c = lane / WD;
@@ -433,7 +436,6 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   const int D = FULL ? WD * DPL : pb.D;
   const int PP = D / 16;        // cost pieces per pixel
   const int PS = D * BPE / 16;  // sum pieces per pixel
-  const int UPP = D * BPE / 8;  // 8-byte sum units per pixel
   const int n = min(CH, W - j0);  // chains of this warp item
   const bool nfull = n == CH;
   const int sh = SH0 ? 0 : (kind < 4 ? 1 : -1);
@@ -448,17 +450,18 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
   const uint32_t ring_end = ring_s + KS * slot_bytes;
   const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
+  const int stage_bytes = CH * D * BPE;  // one step's run of sums (two such buffers)
   const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
   // bytes from one step's run to the next (before any wrap correction)
   const int64_t cstride = ((int64_t)dy * W + dx) * D, astride = cstride * BPE;
   const int64_t cwrap = (int64_t)W * D, awrap = cwrap * BPE;  // one row, subtracted at a wrap
 
   // Per-lane pieces, fixed for the whole walk: cost piece v of the step's run (chain cp_c[v],
-  // shared offset cp_s[v] inside a ring slot) and 8-byte sum unit r (chain su_c[r], staging offset
-  // su_s[r]); the lane's own cost pieces (rd_s) and sum pieces (st_s) of each of its chains. A run
-  // that does not wrap around the image edge is contiguous in memory, so piece v then sits
-  // 16 (lane + 32 v) bytes and unit r 8 (lane + 32 r) bytes after the run's start.
-  int cp_c[NCP], cp_s[NCP], su_c[NR], su_s[NR], rd_s[CPL][NVC], st_s[CPL][NVS];
+  // shared offset cp_s[v] inside a ring slot); the lane's own cost pieces (rd_s) and sum pieces
+  // (st_s, in the run's memory order) of each of its chains. A run that does not wrap around the
+  // image edge is contiguous in memory, so piece v then sits 16 (lane + 32 v) bytes after the
+  // run's start.
+  int cp_c[NCP], cp_s[NCP], rd_s[CPL][NVC], st_s[CPL][NVS];
   bool act[CPL];  // the lane's chain g exists and the lane owns disparities of it
 #pragma unroll
   for (int v = 0; v < NCP; v++) {
@@ -466,13 +469,6 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
     const int pc = p / PP, pi = p - pc * PP;
     cp_c[v] = pc < n ? pc : -1;
     cp_s[v] = swz(pc, pi, PP) * 16;
-  }
-#pragma unroll
-  for (int r = 0; r < NR; r++) {
-    const int q = lane + 32 * r;
-    const int qc = q / UPP, qk = q - qc * UPP;
-    su_c[r] = qc < n ? qc : -1;
-    su_s[r] = swz(qc, qk >> 1, PS) * 16 + (qk & 1) * 8;
   }
 #pragma unroll
   for (int g = 0; g < CPL; g++) {
@@ -484,7 +480,7 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
       rd_s[g][v] = swz(cg, b >> 4, PP) * 16 + (b & 15);
     }
 #pragma unroll
-    for (int v = 0; v < NVS; v++) st_s[g][v] = swz(cg, lig * NVS + v, PS) * 16;
+    for (int v = 0; v < NVS; v++) st_s[g][v] = (cg * PS + lig * NVS + v) * 16;
   }
 
   // copy cursor: global start of the next step's run, its column, and its ring slot
@@ -539,6 +535,7 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   }
   uint8_t* arun = reinterpret_cast<uint8_t*>(pb.agg) + ((int64_t)ystart * W + xs) * D * BPE;
   uint32_t rslot = ring_s;  // ring slot of the current step
+  uint32_t sbuf = stage_s;  // staging buffer of the current step
 
   // prologue: steps 0 .. 5 in flight as three groups of two
 #pragma unroll
@@ -552,6 +549,8 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
     for (int u = 0; u < 2; u++) {
       const int t = t0 + u;
       if (t >= H) break;
+      // the bulk add issued two steps ago has read the staging buffer this step refills
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
       __syncwarp();  // every lane is done with the ring slot refilled below and with the staging
       if (u == 0) {  // issue steps t + 6, t + 7, then wait for steps t, t + 1
         copy_step(t + KS - 2);
@@ -646,7 +645,7 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
         if (FULL || act[g]) {
 #pragma unroll
           for (int v = 0; v < NVS; v++) {
-            const uint32_t a = stage_s + (uint32_t)st_s[g][v];
+            const uint32_t a = sbuf + (uint32_t)st_s[g][v];
             if (!WIDE)
               sts128(a, L[g][4 * v], L[g][4 * v + 1], L[g][4 * v + 2], L[g][4 * v + 3]);
             else
@@ -655,29 +654,24 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
           }
         }
       }
+      // The run's sums go to S with one bulk reduction (two at a wrap) issued by lane 0: the
+      // tensor memory accelerator adds the staged 32-bit words (two packed u16 sums each, which
+      // cannot carry into each other, or one u32 sum when wide) into S atomically, element by
+      // element. The staging writes are made visible to that async proxy first.
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      // all staged units first (the shared loads are ordered asm), then the atomic adds
-      unsigned long long sv[NR];
-#pragma unroll
-      for (int r = 0; r < NR; r++) sv[r] = lds64(stage_s + (uint32_t)su_s[r]);
-      if (nfull && (SH0 || xs + CH <= W)) {  // every unit, contiguous run
-        uint8_t* dst = arun + 8 * lane;
-#pragma unroll
-        for (int r = 0; r < NR; r++)
-          if (FULL || su_c[r] >= 0)
-            atomicAdd(reinterpret_cast<unsigned long long*>(dst + 256 * r), sv[r]);
-      } else {
-#pragma unroll
-        for (int r = 0; r < NR; r++) {
-          if (su_c[r] >= 0) {
-            const int q = lane + 32 * r;
-            const int back_w = (!SH0 && xs + su_c[r] >= W) ? W : 0;  // wrapped to the row's start
-            atomicAdd(reinterpret_cast<unsigned long long*>(
-                          arun + (int64_t)(q - back_w * UPP) * 8),
-                      sv[r]);
-          }
-        }
+      if (lane == 0) {
+        const int n1 = (!SH0 && xs + n > W) ? W - xs : n;  // pixels before the wrap
+        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;"
+                     ::"l"(arun), "r"(sbuf), "r"(n1 * D * BPE) : "memory");
+        if (!SH0 && n1 < n)
+          asm volatile(
+              "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;"
+              ::"l"(arun - (int64_t)xs * D * BPE), "r"(sbuf + n1 * D * BPE), "r"((n - n1) * D * BPE)
+              : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       }
+      sbuf = sbuf == stage_s ? stage_s + stage_bytes : stage_s;
       arun += astride;
       if (!SH0) {
         xs += dx;
@@ -697,6 +691,8 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
     }
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // adds complete
+  __syncwarp();
 }
 
 // Warp item `item` of a pair's sheared-column work (see shear_items).

@@ -6,12 +6,12 @@
 namespace r2t {
 
 enum {
-  kStCensus = 0, kStCost = 1, kStRows = 2, kStShear = 3, kStWta = 4, kStMedian = 5,
-  kNumCounters = 6
+  kStCost = 0, kStRows = 1, kStShear = 2, kStWta = 3, kStMedian = 4,
+  kNumCounters = 5
 };
 
-// Header of the device descriptor block. It is followed by Problem[cap], int prefix[4][cap + 1]
-// (census, cost, wta, median items), then for the row and the sheared-column queue each
+// Header of the device descriptor block. It is followed by Problem[cap], int prefix[3][cap + 1]
+// (census + cost, wta, median items), then for the row and the sheared-column queue each
 // AggSeg[cap] and int seg_prefix[cap + 1].
 struct BatchHeader {
   int n;

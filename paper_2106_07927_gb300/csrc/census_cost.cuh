@@ -1,84 +1,60 @@
-// Census transform and Hamming matching cost, as block-level device routines (256 threads).
+// Census transform fused with the Hamming matching cost, as a block-level device routine (256
+// threads).
 //
 // Census (Sec. 2.1.1, Sec. 2.2.1): bit k of the descriptor of pixel (x, y) is 1 when the k-th
 // neighbour of the cw x ch window (visited row by row, left to right, centre skipped) is darker
 // than the centre; neighbours outside the image read 0 (zero-valued margin). 5x5 gives 24 bits,
-// 9x7 gives 62 bits, both stored as uint64.
+// 9x7 gives 62 bits, both kept as uint64.
 // Cost (Eq. image_matching): C(x, y, d) = popcount(CT_L(x, y) ^ CT_R(x - d, y)), 255 if x < d.
+//
+// A tile is kCostTX pixels of one row. It stages the ch image rows around the row (left segment
+// x0 - rx .. x0 + kCostTX - 1 + rx, right segment x0 - D + 1 - rx .. x0 + kCostTX - 1 + rx, zero
+// outside the image) in shared memory, computes the descriptors it needs there (kCostTX left,
+// kCostTX + D - 1 right), then all D costs of its pixels. No descriptor map goes through HBM; the
+// right descriptors shared by neighbouring tiles are computed by each of them.
 #pragma once
 #include "common.cuh"
 
 namespace r2t {
 
-constexpr int kCensusTW = 64;  // census tile: 64 x 4 pixels, one per thread
-constexpr int kCensusTH = 4;
-constexpr int kCostTX = 128;   // cost tile: 128 pixels of one row, all D disparities
+constexpr int kCostTX = 128;                 // cost tile: 128 pixels of one row, all D disparities
+constexpr int kImgW = kCostTX + 256 + 8;     // widest staged row: kCostTX + D - 1 + 2 rx, D <= 256
 
-__host__ __device__ inline int census_tiles_x(int W) { return (W + kCensusTW - 1) / kCensusTW; }
-__host__ __device__ inline int census_tiles_y(int H) { return (H + kCensusTH - 1) / kCensusTH; }
-// Work items of the census stage of one pair: both images, all tiles.
-__host__ __device__ inline int census_items(int W, int H) {
-  return 2 * census_tiles_x(W) * census_tiles_y(H);
-}
 __host__ __device__ inline int cost_items(int W, int H) { return H * ((W + kCostTX - 1) / kCostTX); }
-
-// Shared memory of the census routine (largest window 9 x 7).
-struct CensusSmem {
-  uint8_t tile[kCensusTH + 6][kCensusTW + 8];
-};
-
-template <int CW, int CH>
-__device__ __forceinline__ void census_tile(const Problem& pb, int item, CensusSmem& sm) {
-  constexpr int RX = CW / 2, RY = CH / 2;
-  constexpr int SW = kCensusTW + 2 * RX, SH = kCensusTH + 2 * RY;
-  const int ntx = census_tiles_x(pb.W), nty = census_tiles_y(pb.H);
-  const int img = item / (ntx * nty);
-  const int t = item % (ntx * nty);
-  const int x0 = (t % ntx) * kCensusTW, y0 = (t / ntx) * kCensusTH;
-  const uint8_t* src = img ? pb.right : pb.left;
-  uint64_t* dst = img ? pb.ctr : pb.ctl;
-  for (int i = threadIdx.x; i < SW * SH; i += blockDim.x) {
-    const int ty = i / SW, tx = i - ty * SW;
-    const int gx = x0 + tx - RX, gy = y0 + ty - RY;
-    uint8_t v = 0;
-    if (gx >= 0 && gx < pb.W && gy >= 0 && gy < pb.H) v = src[(int64_t)gy * pb.in_pitch + gx];
-    sm.tile[ty][tx] = v;
-  }
-  __syncthreads();
-  const int lx = threadIdx.x % kCensusTW, ly = threadIdx.x / kCensusTW;
-  const int x = x0 + lx, y = y0 + ly;
-  if (ly < kCensusTH && x < pb.W && y < pb.H) {
-    const uint32_t c = sm.tile[ly + RY][lx + RX];
-    uint64_t bits = 0;
-    int k = 0;
-#pragma unroll
-    for (int j = 0; j < CH; j++) {
-#pragma unroll
-      for (int i = 0; i < CW; i++) {
-        if (j == RY && i == RX) continue;
-        bits |= (uint64_t)(sm.tile[ly + j][lx + i] < c) << k;
-        k++;
-      }
-    }
-    dst[(int64_t)y * pb.W + x] = bits;
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void census_tile_dispatch(const Problem& pb, const Method& mt, int item,
-                                                     CensusSmem& sm) {
-  if (mt.cw == 9)
-    census_tile<9, 7>(pb, item, sm);
-  else
-    census_tile<5, 5>(pb, item, sm);
-}
 
 // CT_R(x0 - D + 1 + i) for i < kCostTX + D - 1 sits at r[i & 3][i >> 2]: the lanes of a warp read
 // i, i - 4, i - 8, ... (4 disparities apart), which this split keeps on consecutive words.
 struct CostSmem {
+  uint8_t img[2][7][kImgW];  // rows y - ry .. y + ry of the left / right segment
   uint64_t r[4][(kCostTX + 256) / 4];
   uint64_t l[kCostTX];
 };
+
+// Census descriptor of the pixel whose window starts at column i of the staged rows. Bits are
+// accumulated from the last neighbour to the first, each as the sign of (neighbour - centre)
+// shifted in from the right, so bit k ends at position k (first 32 neighbours in the low word).
+template <int CW, int CH>
+__device__ __forceinline__ uint64_t census_at(const uint8_t (*rows)[kImgW], int i) {
+  constexpr int RX = CW / 2, RY = CH / 2;
+  const int c = rows[RY][i + RX];
+  uint32_t lo = 0, hi = 0;
+#pragma unroll
+  for (int j = CH - 1; j >= 0; j--) {
+#pragma unroll
+    for (int ii = CW - 1; ii >= 0; ii--) {
+      constexpr int centre = RY * CW + RX;
+      const int n = j * CW + ii;  // window position, compile time after unrolling
+      if (n == centre) continue;
+      const int k = n < centre ? n : n - 1;                        // bit of this neighbour
+      const uint32_t b = (uint32_t)((int)rows[j][i + ii] - c) >> 31;  // 1 iff darker
+      if (k >= 32)
+        hi = (hi << 1) | b;
+      else
+        lo = (lo << 1) | b;
+    }
+  }
+  return (uint64_t)lo | ((uint64_t)hi << 32);
+}
 
 __device__ __forceinline__ uint32_t pack_bytes(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   return __byte_perm(__byte_perm(a, b, 0x0040), __byte_perm(c, d, 0x0040), 0x5410);
@@ -90,30 +66,71 @@ __device__ __forceinline__ uint32_t hamming(uint64_t a, uint64_t b) {
 }
 
 // One row segment of kCostTX pixels, all disparities, written as 4-byte words of 4 consecutive
-// disparities. The same tile of the aggregated volume is cleared here (16-byte stores) and the
-// tile's right-disparity keys are set to their maximum, so the later stages can add / atomicMin
-// into them without separate memset passes; agg_bytes_per_de is 2, or 4 when wide. CT64: the
-// census descriptors use more than 32 bits.
+// disparities, from a CW x CH census. The same tile of the aggregated volume is cleared here
+// (16-byte stores) and the tile's right-disparity keys are set to their maximum, so the later
+// stages can add / atomicMin into them without separate memset passes; agg_bytes_per_de is 2, or 4
+// when wide.
 //
 // Thread t computes word q = t % (D / 4) of pixels t / (D / 4), t / (D / 4) + 256 / (D / 4), ...
 // when D / 4 divides 256 (D = 16, 32, 64, 128, 256), so its r phases and offsets are fixed and
 // its shared-memory addresses advance by a constant; other D take a generic loop.
-template <bool CT64>
+template <int CW, int CH>
 __device__ __forceinline__ void cost_tile(const Problem& pb, int item, CostSmem& sm,
                                           int agg_bytes_per_de) {
+  constexpr int RX = CW / 2, RY = CH / 2;
+  constexpr bool CT64 = CW * CH - 1 > 32;
   const int ntx = (pb.W + kCostTX - 1) / kCostTX;
   const int y = item / ntx;
   const int x0 = (item - y * ntx) * kCostTX;
-  const int D = pb.D;
-  const int npx = min(kCostTX, pb.W - x0);
-  const uint64_t* rowr = pb.ctr + (int64_t)y * pb.W;
-  const uint64_t* rowl = pb.ctl + (int64_t)y * pb.W;
-  for (int i = threadIdx.x; i < kCostTX + D - 1; i += blockDim.x) {
-    const int xr = x0 - (D - 1) + i;
-    sm.r[i & 3][i >> 2] = (xr >= 0 && xr < pb.W) ? rowr[xr] : 0ull;
+  const int W = pb.W, H = pb.H, D = pb.D;
+  const int npx = min(kCostTX, W - x0);
+  const int nl = kCostTX + 2 * RX, nr = kCostTX + D - 1 + 2 * RX;  // staged row lengths
+  const int xl0 = x0 - RX, xr0 = x0 - (D - 1) - RX;                 // their first columns
+  {
+    // every thread (of 256) issues all of its loads, up to NQ bytes per staged row, before
+    // storing any, so their latencies overlap; nl + nr <= 2 kCostTX + 255 + 4 rx <= 256 NQ
+    constexpr int NQ = 3;
+    static_assert(2 * kCostTX + 255 + 16 <= 256 * NQ, "staged rows exceed the loads");
+    uint8_t v[CH][NQ];
+#pragma unroll
+    for (int j = 0; j < CH; j++) {
+      const int gy = y - RY + j;
+      const bool rowin = gy >= 0 && gy < H;
+      const uint8_t* lrow = pb.left + (int64_t)gy * pb.in_pitch;
+      const uint8_t* rrow = pb.right + (int64_t)gy * pb.in_pitch;
+#pragma unroll
+      for (int q = 0; q < NQ; q++) {
+        const int k = threadIdx.x + 256 * q;
+        const bool isr = k >= nl;
+        const int gx = (isr ? xr0 - nl : xl0) + k;
+        v[j][q] = 0;
+        if (k < nl + nr && rowin && gx >= 0 && gx < W) v[j][q] = __ldg(isr ? rrow + gx : lrow + gx);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < CH; j++) {
+#pragma unroll
+      for (int q = 0; q < NQ; q++) {
+        const int k = threadIdx.x + 256 * q;
+        if (k < nl + nr) {
+          if (k >= nl)
+            sm.img[1][j][k - nl] = v[j][q];
+          else
+            sm.img[0][j][k] = v[j][q];
+        }
+      }
+    }
   }
-  for (int i = threadIdx.x; i < kCostTX; i += blockDim.x)
-    sm.l[i] = (x0 + i < pb.W) ? rowl[x0 + i] : 0ull;
+  __syncthreads();
+  for (int i = threadIdx.x; i < kCostTX + (kCostTX + D - 1); i += blockDim.x) {
+    if (i < kCostTX) {
+      sm.l[i] = census_at<CW, CH>(sm.img[0], i);
+    } else {
+      const int ir = i - kCostTX;
+      const int xr = x0 - (D - 1) + ir;  // only x - d >= 0 are read, so xr < 0 stays unused
+      sm.r[ir & 3][ir >> 2] = xr >= 0 ? census_at<CW, CH>(sm.img[1], ir) : 0ull;
+    }
+  }
   __syncthreads();
   const int nq = D / 4;  // 4-disparity words per pixel
   uint32_t* out = reinterpret_cast<uint32_t*>(pb.cost + ((int64_t)y * pb.W + x0) * D);
@@ -171,13 +188,13 @@ __device__ __forceinline__ void cost_tile(const Problem& pb, int item, CostSmem&
   __syncthreads();
 }
 
-// Census descriptors of the method's window fit 32 bits when cw * ch - 1 <= 32 (5 x 5).
+// The two census windows of the method: 9 x 7 (62-bit descriptors) and 5 x 5 (24-bit).
 __device__ __forceinline__ void cost_tile_dispatch(const Problem& pb, const Method& mt, int item,
                                                    CostSmem& sm) {
-  if (mt.cw * mt.ch - 1 > 32)
-    cost_tile<true>(pb, item, sm, mt.wide ? 4 : 2);
+  if (mt.cw == 9)
+    cost_tile<9, 7>(pb, item, sm, mt.wide ? 4 : 2);
   else
-    cost_tile<false>(pb, item, sm, mt.wide ? 4 : 2);
+    cost_tile<5, 5>(pb, item, sm, mt.wide ? 4 : 2);
 }
 
 }  // namespace r2t

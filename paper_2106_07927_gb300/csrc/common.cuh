@@ -27,8 +27,6 @@ struct Problem {
   uint16_t* disp;     // final map
   int64_t out_pitch;  // bytes
   int W, H, D;
-  uint64_t* ctl;      // census descriptors of the left / right image, [H][W]
-  uint64_t* ctr;
   uint8_t* cost;      // [H][W][D]
   void* agg;          // [H][W][D], uint16 (or uint32 when wide)
   uint16_t* dl;       // [H][W] winner-takes-all map

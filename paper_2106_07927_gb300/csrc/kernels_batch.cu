@@ -28,21 +28,6 @@
 namespace r2t {
 
 
-__global__ void __launch_bounds__(256) batch_census_kernel(const BatchHeader* hd,
-                                                           const Problem* probs, const int* prefix,
-                                                           Method mt, unsigned* counters) {
-  __shared__ CensusSmem sm;
-  __shared__ int s_item;
-  const int total = hd->total[kStCensus], n = hd->n;
-  for (;;) {
-    const int item = claim_block(&counters[kStCensus], &s_item);
-    if (item >= total) break;
-    const int p = find_slot(prefix, n, item);
-    const Problem pb = probs[p];
-    census_tile_dispatch(pb, mt, item - prefix[p], sm);
-  }
-}
-
 __global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
                                                          const Problem* probs, const int* prefix,
                                                          Method mt, unsigned* counters) {
@@ -112,7 +97,7 @@ struct BatchEngine {
 static size_t probs_offset() { return (sizeof(BatchHeader) + 255) / 256 * 256; }
 static size_t prefix_offset(int cap) { return probs_offset() + (size_t)cap * sizeof(Problem); }
 static size_t segs_offset(int cap, int q) {  // q = 0 rows, 1 sheared columns
-  const size_t base = (prefix_offset(cap) + 4 * sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
+  const size_t base = (prefix_offset(cap) + 3 * sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
   const size_t per = ((size_t)cap * sizeof(AggSeg) + sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
   return base + q * per;
 }
@@ -226,7 +211,6 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   // launch shapes and attributes are settled before the capture starts
   cudaFuncSetAttribute(batch_wta_kernel<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        wta_smem);
-  const int g_census = persistent_grid(batch_census_kernel, 0);
   const int g_cost = persistent_grid(batch_cost_kernel, 0);
   const void* k_rows = batch_row_kernel_fn<WIDE>();
   const void* k_shear = batch_shear_kernel_fn<WIDE>();
@@ -246,9 +230,7 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   // an external record node, so the host can wait for the upload of each replay
   cudaEventRecordWithFlags(e->copied, cs, cudaEventRecordExternal);
   cudaMemsetAsync(e->d_counters, 0, 64, cs);
-  batch_census_kernel<<<g_census, 256, 0, cs>>>(hd, probs, prefix + 0 * stride, mt,
-                                                e->d_counters);
-  batch_cost_kernel<<<g_cost, 256, 0, cs>>>(hd, probs, prefix + 1 * stride, mt, e->d_counters);
+  batch_cost_kernel<<<g_cost, 256, 0, cs>>>(hd, probs, prefix + 0 * stride, mt, e->d_counters);
   cudaEventRecord(e->fork.fork, cs);
   cudaStreamWaitEvent(e->fork.aux, e->fork.fork, 0);
   {
@@ -264,9 +246,9 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   }
   cudaEventRecord(e->fork.join, e->fork.aux);
   cudaStreamWaitEvent(cs, e->fork.join, 0);
-  batch_wta_kernel<WIDE><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 2 * stride,
+  batch_wta_kernel<WIDE><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 1 * stride,
                                                        e->d_counters);
-  batch_median_kernel<<<g_med, 256, 0, cs>>>(hd, probs, prefix + 3 * stride, mt, e->d_counters);
+  batch_median_kernel<<<g_med, 256, 0, cs>>>(hd, probs, prefix + 2 * stride, mt, e->d_counters);
   c = cudaStreamEndCapture(cs, &g);
   if (c != cudaSuccess) return set_err(e, c, "end capture");
   c = cudaGraphInstantiate(&e->exec, g, 0);
@@ -274,7 +256,7 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   if (c != cudaSuccess) return set_err(e, c, "graph instantiate");
   e->graph_method = mt;
   e->graph_wta_smem = wta_smem;
-  e->graph_launches = 6;
+  e->graph_launches = 5;
   return 0;
 }
 
@@ -321,7 +303,7 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
   Problem* hp = reinterpret_cast<Problem*>(e->h_desc + probs_offset());
   int* prefix = reinterpret_cast<int*>(e->h_desc + prefix_offset(cap));
   const int stride = cap + 1;
-  int tot[4] = {0, 0, 0, 0};
+  int tot[3] = {0, 0, 0};
   int wta_smem = 0;
   std::vector<Keyed> lk, bk;
   lk.reserve(n);
@@ -332,28 +314,25 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
     prefix[0 * stride + p] = tot[0];
     prefix[1 * stride + p] = tot[1];
     prefix[2 * stride + p] = tot[2];
-    prefix[3 * stride + p] = tot[3];
-    tot[0] += census_items(pb.W, pb.H);
-    tot[1] += cost_items(pb.W, pb.H);
-    tot[2] += wta_items(pb.W, pb.H, wta_tile_px(pb.D));
-    tot[3] += median_items(pb.W, pb.H);
+    tot[0] += cost_items(pb.W, pb.H);
+    tot[1] += wta_items(pb.W, pb.H, wta_tile_px(pb.D));
+    tot[2] += median_items(pb.W, pb.H);
     wta_smem = std::max(wta_smem, (int)wta_smem_bytes(pb.D, wta_tile_px(pb.D)));
     const int dpl = e->dpl_by_d16[pb.D / 16];
     lk.push_back(Keyed{AggSeg{p, 0, row_units(pb.H, false), 32 / long_lanes(pb.D, dpl)}, pb.W});
     bk.push_back(Keyed{AggSeg{p, 0, shear_items(pb.W, pb.D, 16, mt.num_paths, 1), 1}, pb.H});
   }
-  for (int k = 0; k < 4; k++) prefix[k * stride + n] = tot[k];
+  for (int k = 0; k < 3; k++) prefix[k * stride + n] = tot[k];
   const int nrows = write_queue(lk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 0)),
                                 reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 0)), cap);
   const int nshear = write_queue(bk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 1)),
                                 reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 1)), cap);
   hd->n = n;
-  hd->total[kStCensus] = tot[0];
-  hd->total[kStCost] = tot[1];
+  hd->total[kStCost] = tot[0];
   hd->total[kStRows] = nrows;
   hd->total[kStShear] = nshear;
-  hd->total[kStWta] = tot[2];
-  hd->total[kStMedian] = tot[3];
+  hd->total[kStWta] = tot[1];
+  hd->total[kStMedian] = tot[2];
   memcpy(hd->dpl_by_d16, e->dpl_by_d16, sizeof(hd->dpl_by_d16));
   if (!e->exec || memcmp(&e->graph_method, &mt, sizeof(Method)) != 0 ||
       wta_smem > e->graph_wta_smem) {

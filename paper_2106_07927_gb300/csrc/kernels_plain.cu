@@ -6,11 +6,6 @@
 
 namespace r2t {
 
-__global__ void __launch_bounds__(256) census_kernel(Problem pb, Method mt) {
-  __shared__ CensusSmem sm;
-  census_tile_dispatch(pb, mt, blockIdx.x, sm);
-}
-
 __global__ void __launch_bounds__(256) cost_kernel(Problem pb, Method mt) {
   __shared__ CostSmem sm;
   cost_tile_dispatch(pb, mt, blockIdx.x, sm);
@@ -103,17 +98,13 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
   int n = 0;
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], s);
-  census_kernel<<<census_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
-  n++;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[1], s);
   cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[2], s);
+  if (ev) cudaEventRecord(ev[1], s);
   if ((e = launch_aggregate(pb, mt, tn, s, fork)) != cudaSuccess) return e;
   n += 2;
-  if (ev) cudaEventRecord(ev[3], s);
+  if (ev) cudaEventRecord(ev[2], s);
   const int T = tn.wta_chunk;  // pixels per block of 256 threads
   const size_t smem = wta_smem_bytes(pb.D, T);
   if (mt.wide)
@@ -122,11 +113,11 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
     wta_dr_kernel<false><<<wta_items(pb.W, pb.H, T), 256, smem, s>>>(pb, T);
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[4], s);
+  if (ev) cudaEventRecord(ev[3], s);
   lr_median_kernel<<<median_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[5], s);
+  if (ev) cudaEventRecord(ev[4], s);
   if (launches) *launches = n;
   return cudaSuccess;
 }

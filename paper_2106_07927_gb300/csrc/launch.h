@@ -45,10 +45,10 @@ const void* batch_row_kernel_fn();
 template <bool WIDE>
 const void* batch_shear_kernel_fn();
 
-// Plain single-pair pipeline: 5 kernel launches on stream s (census; cost + clearing of the
-// aggregated volume; aggregation; WTA + right-disparity keys; LR check + median). Returns the
-// number of launches through *launches.
-// ev: NULL, or 6 events recorded around the stages (before census, after each of the five).
+// Plain single-pair pipeline: 5 kernel launches on stream s (census + cost + clearing of the
+// aggregated volume; two aggregation kernels; WTA + right-disparity keys; LR check + median).
+// Returns the number of launches through *launches.
+// ev: NULL, or 5 events recorded around the four stages (before the cost stage, after each).
 // fork: NULL runs the two aggregation kernels one after the other on s.
 cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
                          int* launches, cudaEvent_t* ev = nullptr, const Fork* fork = nullptr);

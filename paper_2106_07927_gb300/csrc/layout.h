@@ -8,19 +8,17 @@
 namespace r2t {
 
 struct Layout {
-  size_t ctl, ctr, cost, agg, dl, dr, kr, mask, total;
+  size_t cost, agg, dl, dr, kr, mask, total;
 };
 
 inline size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Census maps 16 B/px, cost 1 B/DE, aggregated volume 2 B/DE (4 when wide), D^L and D^R
-// 2 B/px each, right-disparity keys 4 B/px, LR mask 1 B/px: 3 B per DE + 25 B per pixel.
+// Cost 1 B/DE, aggregated volume 2 B/DE (4 when wide), D^L and D^R 2 B/px each,
+// right-disparity keys 4 B/px, LR mask 1 B/px: 3 B per DE + 9 B per pixel.
 inline Layout layout_for(int W, int H, int D, bool wide) {
   const size_t npx = (size_t)W * H, nde = npx * D;
   Layout l;
   size_t o = 0;
-  l.ctl = o; o = align256(o + npx * 8);
-  l.ctr = o; o = align256(o + npx * 8);
   l.cost = o; o = align256(o + nde);
   l.agg = o; o = align256(o + nde * (wide ? 4 : 2));
   l.dl = o; o = align256(o + npx * 2);
@@ -37,8 +35,6 @@ inline Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
   pb.W = W;
   pb.H = H;
   pb.D = D;
-  pb.ctl = reinterpret_cast<uint64_t*>(base + l.ctl);
-  pb.ctr = reinterpret_cast<uint64_t*>(base + l.ctr);
   pb.cost = reinterpret_cast<uint8_t*>(base + l.cost);
   pb.agg = base + l.agg;
   pb.dl = reinterpret_cast<uint16_t*>(base + l.dl);

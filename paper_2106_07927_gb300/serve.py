@@ -5,7 +5,7 @@ Requests (stereo pairs of uneven W, H, D) arrive as a Poisson process. The serve
 streams, each with its own context whose batch engine is reserved once (res2tac_batch_reserve),
 so nothing is allocated while serving and the per-stream method parameters stay resident on the
 device. Whenever a stream is idle, it admits the waiting requests in arrival order while their
-device memory (res2tac_batch_workspace_bytes: census maps, cost and aggregated volumes, maps) fits
+device memory (res2tac_batch_workspace_bytes: cost and aggregated volumes, maps) fits
 the stream's reservation, and runs them as one res2tac_compute_batch. Requests that arrive while
 others are on the GPU join the next batch of the next free stream; batches on different streams
 overlap on the device. Latency is completion (host time at which the stream's event is observed
@@ -145,23 +145,32 @@ def summarize(requests):
 
 
 class ScenePool:
-    """Device-resident inputs of every requested shape, cropped from one generated scene per
-    (kind, D) (and one 3840x2160 scene per kind for the large pairs)."""
+    """Device-resident inputs of every requested shape, cropped from one generated 1920x1080 scene
+    per kind (disparities for D = 256). Pairs larger than that are cropped from the same scene
+    upsampled 2x in both axes, which is again a rectified pair, with twice the disparities."""
 
-    def __init__(self, torch, seed=0, big=True, master=(1920, 1080)):
+    def __init__(self, torch, seed=0, master=(1920, 1080)):
         self.torch, self.seed, self.master = torch, seed, master
         self.masters, self.cache = {}, {}
-        self.big = big
+
+    def _master(self, kind, big):
+        key = (kind, big)
+        if key not in self.masters:
+            if big:
+                L, R = self._master(kind, False)
+                up = lambda a: np.repeat(np.repeat(a, 2, axis=0), 2, axis=1)
+                self.masters[key] = (up(L), up(R))
+            else:
+                L, R, _ = scenes.make_scene(kind, self.seed + 97 * len(self.masters),
+                                            self.master[0], self.master[1], 256)
+                self.masters[key] = (L, R)
+        return self.masters[key]
 
     def get(self, kind, W, H, D):
         key = (kind, W, H, D)
         if key not in self.cache:
-            mw, mh = (3840, 2160) if (W > self.master[0] or H > self.master[1]) else self.master
-            mkey = (kind, D, mw, mh)
-            if mkey not in self.masters:
-                self.masters[mkey] = scenes.make_scene(kind, self.seed + 97 * len(self.masters),
-                                                       mw, mh, D)
-            L, R, _ = self.masters[mkey]
+            big = W > self.master[0] or H > self.master[1]
+            L, R = self._master(kind, big)
             t = self.torch
             self.cache[key] = (t.from_numpy(L[:H, :W].copy()).cuda(),
                                t.from_numpy(R[:H, :W].copy()).cuda())
