@@ -50,26 +50,33 @@ __device__ __forceinline__ void wta_load(const void* agg, int64_t vec, int D, in
 template <int NDL, bool EXACT>
 __device__ __forceinline__ void wta_keys(const Problem& pb, int64_t rowbase, int x, int px,
                                          uint32_t* keys, int lane, const uint32_t (&s)[NDL]) {
-  const int D = pb.D;
-  uint32_t* kt = keys + (px + D - 1);  // kt[-d] is the key of target x - d
-  const bool edge = x < D - 1;                // some targets x - d fall left of the image
+  const int D = EXACT ? 32 * NDL : pb.D;
+  uint32_t* kt = keys + (px + D - 1 - lane);  // kt[-32 i] is the key of target x - d
+  uint32_t key[NDL];
   uint32_t kl = 0xFFFFFFFFu;
 #pragma unroll
   for (int i = 0; i < NDL; i++) {
     const int d = lane + 32 * i;
-    if (EXACT || d < D) {
-      const uint32_t key = (s[i] << 8) | (uint32_t)d;
-      kl = min(kl, key);
-      if (!edge || d <= x) atomicMin(kt - d, key);
+    key[i] = (EXACT || d < D) ? (s[i] << 8) | (uint32_t)d : 0xFFFFFFFFu;
+    kl = min(kl, key[i]);
+  }
+  if (EXACT && x >= D - 1) {  // warp-uniform: every target x - d lies in the image
+#pragma unroll
+    for (int i = 0; i < NDL; i++) atomicMin(kt - 32 * i, key[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < NDL; i++) {
+      const int d = lane + 32 * i;
+      if ((EXACT || d < D) && d <= x) atomicMin(kt - 32 * i, key[i]);
     }
   }
   kl = __reduce_min_sync(0xffffffffu, kl);
   if (lane == 0) pb.dl[rowbase + x] = (uint16_t)(kl & 0xFFu);
 }
 
-// One tile of T pixels of a row, 256 threads: warp w takes pixels w, w + 8, ..., two at a time so
-// that both pixels' loads are in flight together. Targets whose sources all lie in the tile are
-// then stored, the others (at most D - 1 per tile side) merged with a global atomicMin.
+// One tile of T pixels of a row, 256 threads: warp w takes pixels w, w + 8, ..., PF at a time so
+// that their loads are in flight together. Targets whose sources all lie in the tile are then
+// stored, the others (at most D - 1 per tile side) merged with a global atomicMin.
 template <bool WIDE, int NDL, bool EXACT>
 __device__ __forceinline__ void wta_dr_tile_t(const Problem& pb, int item, uint32_t* keys, int T) {
   const int W = pb.W, D = pb.D;
@@ -81,13 +88,17 @@ __device__ __forceinline__ void wta_dr_tile_t(const Problem& pb, int item, uint3
   for (int i = threadIdx.x; i < ntar; i += blockDim.x) keys[i] = 0xFFFFFFFFu;
   __syncthreads();
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int px = threadIdx.x >> 5; px < n; px += 2 * nw) {
-    const int pq = px + nw;
-    uint32_t sa[NDL], sb[NDL];
-    wta_load<WIDE, NDL, EXACT>(pb.agg, (rowbase + x0 + px) * D, D, lane, sa);
-    if (pq < n) wta_load<WIDE, NDL, EXACT>(pb.agg, (rowbase + x0 + pq) * D, D, lane, sb);
-    wta_keys<NDL, EXACT>(pb, rowbase, x0 + px, px, keys, lane, sa);
-    if (pq < n) wta_keys<NDL, EXACT>(pb, rowbase, x0 + pq, pq, keys, lane, sb);
+  constexpr int PF = NDL <= 4 ? 4 : 2;  // pixels whose loads are in flight together
+  for (int px = threadIdx.x >> 5; px < n; px += PF * nw) {
+    uint32_t sv[PF][NDL];
+#pragma unroll
+    for (int u = 0; u < PF; u++)
+      if (px + u * nw < n)
+        wta_load<WIDE, NDL, EXACT>(pb.agg, (rowbase + x0 + px + u * nw) * D, D, lane, sv[u]);
+#pragma unroll
+    for (int u = 0; u < PF; u++)
+      if (px + u * nw < n)
+        wta_keys<NDL, EXACT>(pb, rowbase, x0 + px + u * nw, px + u * nw, keys, lane, sv[u]);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < ntar; i += blockDim.x) {
