@@ -229,6 +229,8 @@ def main():
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
 
     int_peak = binding.res2tac_probe_int_peak(2000, sh)  # lane-ops/s, packed u16 min + add
+    # bytes/s of TMA bulk add-reductions into a buffer the size of the aggregated volume
+    red_peak = binding.res2tac_probe_red_peak(2 * W * H * D, 16, sh)
 
     def step():
         binding.res2tac_compute(ctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, out.data_ptr(),
@@ -391,7 +393,15 @@ def main():
                      "hbm_achieved_gbs": round(bytes_agg / (agg_ms / 1e3) / 1e9, 1),
                      "hbm_peak_gbs": hbm, "traffic": _traffic(),
                      "ops_per_launch": ops_agg, "algorithmic_bytes_per_launch": bytes_agg,
-                     "dominant_stage": dominant},
+                     "dominant_stage": dominant,
+                     # the accumulation into S: every path adds 2 bytes per DE (read-modify-write
+                     # in L2), against the measured rate of bulk add-reductions
+                     "s_accumulation": {
+                         "bytes_per_launch": 2 * de * prm["num_paths"],
+                         "achieved_gbs": round(2 * de * prm["num_paths"] / (agg_ms / 1e3) / 1e9, 1),
+                         "peak_gbs": round(red_peak / 1e9, 1),
+                         "frac": round(2 * de * prm["num_paths"] / (agg_ms / 1e3) / red_peak, 3),
+                         "peak_source": "measured TMA bulk add-reduction probe, S-sized buffer"}},
         "e2e": {"value": round(ws * de * args.steps / e2e_s / 1e6, 1), "unit": "MDE/s",
                 "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
                 "ms_per_step": round(1e3 * e2e_s / args.steps, 4), "matches_device_path": e2e_ok},

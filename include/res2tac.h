@@ -178,6 +178,13 @@ int res2tac_stage_times(res2tac_t h, float* ms, int n);
  * counts two) through *lane_ops_per_s. Synchronises s. */
 int res2tac_probe_int_peak(int iters, res2tac_stream_t s, double* lane_ops_per_s);
 
+/* Reduction-throughput probe (measurement aid, not part of the method): allocates a device buffer
+ * of `bytes` bytes (>= 1024) on stream s, adds 32-bit ones into all of it `passes` times with TMA
+ * bulk add-reductions of 1 KB (the way the column / diagonal aggregation adds its runs into the
+ * aggregated volume), frees it, and returns the sustained rate in bytes reduced per second through
+ * *bytes_per_s. Synchronises s. RES2TAC_ENOMEM if the buffer does not fit. */
+int res2tac_probe_red_peak(int64_t bytes, int32_t passes, res2tac_stream_t s, double* bytes_per_s);
+
 /* No-allocation variant of res2tac_compute. The paper has no counterpart: it is an addition for
  * callers that must not allocate device memory while they run, for example an onboard stereo loop
  * that is only allowed to allocate at start-up, a plugin whose host framework owns every byte of

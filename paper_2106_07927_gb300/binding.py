@@ -27,7 +27,8 @@ EXPORTS = (
     "res2tac_debug_outputs", "res2tac_workspace_bytes", "res2tac_batch_workspace_bytes",
     "res2tac_get_tuning", "res2tac_set_tuning", "res2tac_autotune", "res2tac_last_launch_count",
     "res2tac_destroy", "res2tac_strerror", "res2tac_last_error", "res2tac_set_profiling",
-    "res2tac_stage_times", "res2tac_probe_int_peak", "res2tac_batch_reserve",
+    "res2tac_stage_times", "res2tac_probe_int_peak", "res2tac_probe_red_peak",
+    "res2tac_batch_reserve",
     "res2tac_compute_static",
 )
 RES2TAC_STATIC_SCRATCH_BYTES = 80 << 20
@@ -97,6 +98,7 @@ def load():
         "res2tac_stage_times": (ctypes.c_int, [P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
         "res2tac_probe_int_peak": (ctypes.c_int, [ctypes.c_int, P,
                                                   ctypes.POINTER(ctypes.c_double)]),
+        "res2tac_probe_red_peak": (ctypes.c_int, [I64, I32, P, ctypes.POINTER(ctypes.c_double)]),
         "res2tac_batch_reserve": (ctypes.c_int, [P, S, I32]),
         "res2tac_compute_static": (ctypes.c_int, [PP, P, P, I64, P, I64, P]),
     }
@@ -203,6 +205,12 @@ def res2tac_stage_times(h: int) -> dict:
     ms = (ctypes.c_float * len(STAGES))()
     _check(load().res2tac_stage_times(h, ms, len(STAGES)))
     return dict(zip(STAGES, [float(v) for v in ms]))
+
+
+def res2tac_probe_red_peak(nbytes: int, passes: int = 16, stream: int = 0) -> float:
+    v = ctypes.c_double()
+    _check(load().res2tac_probe_red_peak(nbytes, passes, stream, ctypes.byref(v)))
+    return v.value
 
 
 def res2tac_probe_int_peak(iters: int = 20000, stream: int = 0) -> float:

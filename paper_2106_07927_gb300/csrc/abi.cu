@@ -341,6 +341,13 @@ int res2tac_stage_times(res2tac_t h, float* ms, int n) {
   return RES2TAC_OK;
 }
 
+int res2tac_probe_red_peak(int64_t bytes, int32_t passes, res2tac_stream_t s, double* bytes_per_s) {
+  if (bytes < 1024 || passes < 1 || !bytes_per_s) return fail(RES2TAC_EINVAL, "bad probe arguments");
+  cudaError_t e = r2t::probe_red_peak(bytes, passes, (cudaStream_t)s, bytes_per_s);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_probe_red_peak");
+  return RES2TAC_OK;
+}
+
 int res2tac_probe_int_peak(int iters, res2tac_stream_t s, double* lane_ops_per_s) {
   if (iters < 1 || !lane_ops_per_s) return fail(RES2TAC_EINVAL, "bad probe arguments");
   cudaError_t e = r2t::probe_int_peak(iters, (cudaStream_t)s, lane_ops_per_s);

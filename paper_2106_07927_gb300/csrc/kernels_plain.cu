@@ -183,4 +183,63 @@ cudaError_t probe_int_peak(int iters, cudaStream_t s, double* lane_ops_per_s) {
   return cudaStreamSynchronize(s);
 }
 
+// Reduction-throughput probe: every warp stages 1 KB of 32-bit ones in shared memory once, then
+// adds it into the buffer's 1 KB runs with TMA bulk reductions (4 per group, at most two groups
+// reading shared memory at a time), the way the sheared aggregation kernel adds its runs into S.
+__global__ void __launch_bounds__(256) red_probe_kernel(uint8_t* buf, int64_t runs, int passes) {
+  __shared__ __align__(16) uint32_t stage[8][256];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  for (int i = lane; i < 256; i += 32) stage[wib][i] = 1u;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    const uint32_t src = (uint32_t)__cvta_generic_to_shared(stage[wib]);
+    int k = 0;
+    for (int p = 0; p < passes; p++) {
+      for (int64_t r = w; r < runs; r += nw) {
+        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], 1024;"
+                     ::"l"(buf + r * 1024), "r"(src) : "memory");
+        if (++k == 4) {
+          k = 0;
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        }
+      }
+    }
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+  __syncwarp();
+}
+
+cudaError_t probe_red_peak(int64_t bytes, int passes, cudaStream_t s, double* bytes_per_s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t runs = bytes / 1024;
+  uint8_t* buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, runs * 1024, s);
+  if (e != cudaSuccess) return e;
+  cudaMemsetAsync(buf, 0, runs * 1024, s);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int grid = sms * 4;
+  red_probe_kernel<<<grid, 256, 0, s>>>(buf, runs, 1);  // warm-up
+  cudaEventRecord(e0, s);
+  red_probe_kernel<<<grid, 256, 0, s>>>(buf, runs, passes);
+  cudaEventRecord(e1, s);
+  e = cudaEventSynchronize(e1);
+  float ms = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(buf, s);
+  if (e != cudaSuccess) return e;
+  *bytes_per_s = (double)runs * 1024.0 * passes / (ms * 1e-3);
+  return cudaStreamSynchronize(s);
+}
+
 }  // namespace r2t

@@ -59,6 +59,10 @@ int report_error(int code, const char* msg);
 // Packed-u16 integer throughput probe: lane operations per second.
 cudaError_t probe_int_peak(int iters, cudaStream_t s, double* lane_ops_per_s);
 
+// Reduction-throughput probe: bytes per second that TMA bulk add-reductions achieve into a buffer
+// of `bytes` bytes, `passes` passes.
+cudaError_t probe_red_peak(int64_t bytes, int passes, cudaStream_t s, double* bytes_per_s);
+
 // Copies the aggregated volume as saturated uint16 / the cost volume, both in natural order.
 cudaError_t copy_agg_u16(const Problem& pb, bool wide, uint16_t* dst, cudaStream_t s);
 cudaError_t copy_cost(const Problem& pb, uint8_t* dst, cudaStream_t s);
