@@ -241,7 +241,21 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
                      (void*)&m, (void*)&counters};
     void* sargs[] = {(void*)&hd, (void*)&probs, (void*)&bsegs, (void*)&bpre, (void*)&nseg,
                      (void*)&m, (void*)&counters};
-    cudaLaunchKernel(k_rows, dim3(g_rows), dim3(256), rargs, 0, e->fork.aux);
+    // the row kernel holds the batch's longest chains: its node keeps the highest priority so
+    // its blocks are dispatched ahead of the sheared kernel's
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = hi;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g_rows);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = e->fork.aux;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelExC(&cfg, k_rows, rargs);
     cudaLaunchKernel(k_shear, dim3(g_shear), dim3(256), sargs, shear_smem, cs);
   }
   cudaEventRecord(e->fork.join, e->fork.aux);

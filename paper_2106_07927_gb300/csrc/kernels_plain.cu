@@ -61,8 +61,11 @@ cudaError_t fork_create(Fork* f) {
   int lo = 0, hi = 0;
   cudaDeviceGetStreamPriorityRange(&lo, &hi);
   cudaError_t e = cudaStreamCreateWithPriority(&f->aux, cudaStreamNonBlocking, hi);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->join, cudaEventDisableTiming);
+  // Timing-enabled events: measured with steps queued back to back, fork/join events created
+  // with cudaEventDisableTiming left about one step in five at 0.73 ms instead of 0.39 ms (the
+  // two aggregation kernels stopped overlapping); with timing enabled every step overlapped.
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->fork, cudaEventDefault);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f->join, cudaEventDefault);
   return e;
 }
 
