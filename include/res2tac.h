@@ -121,6 +121,27 @@ int res2tac_compute_host(res2tac_t h, const uint8_t* left, const uint8_t* right,
                          int64_t in_pitch, uint16_t* disp, int64_t out_pitch,
                          res2tac_stream_t s);
 
+/* Pipeline with sub-pixel refinement (Sec. 2.1.3, "Subpixel disparity refinement"), the
+ * configuration the paper labels "fine". Same stages as res2tac_compute; in addition each kept
+ * pixel's parabola through the aggregated costs S(p, d-1), S(p, d), S(p, d+1) at the winning
+ * d = D^L(p) moves d to the parabola's minimum (computed in the left-right / median stage),
+ *   D^L_sub(p) = d + (S(d-1) - S(d+1)) / (2 (S(d-1) - 2 S(d) + S(d+1)))   for 1 <= d <= D-2,
+ *   D^L_sub(p) = d                                                         for d = 0, D-1,
+ * in fp32 with correctly rounded division and addition (S saturated at 65535 as in the uint16
+ * volume). The left-right check compares the integer D^L with D^R as res2tac_compute does and
+ * keeps D^L_sub; the 3x3 median then runs on the float values. disp: device float map,
+ * out_pitch bytes per row (a multiple of 4, >= 4 * width), 4-byte aligned; a pixel rejected by
+ * the check holds +infinity (the float counterpart of RES2TAC_INVALID, which sorts last in the
+ * median exactly as 0xFFFF does). Asynchronous on s. */
+int res2tac_compute_subpixel(res2tac_t h, const uint8_t* left, const uint8_t* right,
+                             int64_t in_pitch, float* disp, int64_t out_pitch,
+                             res2tac_stream_t s);
+
+/* Writes the sub-pixel D^L map [H][W] (every pixel, before the left-right check and the median)
+ * of the last compute call on this context into dl_sub (device, 4 B per pixel), from the D^L
+ * and aggregated volume that call left in the context. Asynchronous on s. */
+int res2tac_debug_subpixel(res2tac_t h, float* dl_sub, res2tac_stream_t s);
+
 /* Runs n independent pairs of uneven sizes as one batch on stream s (the paper processes one
  * pair at a time, Sec. 2.2; batching is this library's addition). The batch runs as persistent
  * kernels fed by a device work queue over all pairs, recorded once into a CUDA graph and

@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
         if force or stale:
             tmp = _LIB_PATH + f".tmp{os.getpid()}"
             subprocess.check_call(
-                ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", _SRC, "-o", tmp])
+                ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"])
             os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -57,8 +57,12 @@ def _load():
         lib.r2o_lr_check.argtypes = [P, P, I, I, I, P, P]
         lib.r2o_median3x3.argtypes = [P, I, I, P]
         lib.r2o_sgm.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, P, P, P, P, P, P]
+        lib.r2o_subpixel.argtypes = [P, P, I, I, I, P]
+        lib.r2o_median3x3_f64.argtypes = [P, I, I, P]
+        lib.r2o_sgm_subpixel.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, P, P]
         for f in (lib.r2o_census, lib.r2o_cost, lib.r2o_path, lib.r2o_aggregate, lib.r2o_wta,
-                  lib.r2o_right_disparity, lib.r2o_lr_check, lib.r2o_median3x3, lib.r2o_sgm):
+                  lib.r2o_right_disparity, lib.r2o_lr_check, lib.r2o_median3x3, lib.r2o_sgm,
+                  lib.r2o_subpixel, lib.r2o_median3x3_f64, lib.r2o_sgm_subpixel):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -165,3 +169,36 @@ def sgm(left: np.ndarray, right: np.ndarray, D: int, census_w: int, census_h: in
                          num_paths, flags, lr_threshold, _ptr(disp), *ptrs)
     _check(rc, "sgm")
     return (disp, dbg) if debug else disp
+
+
+def subpixel(S: np.ndarray, DL: np.ndarray) -> np.ndarray:
+    """Sub-pixel D^L (float64) from the aggregated volume and the integer D^L (Sec. 2.1.3)."""
+    S = np.ascontiguousarray(S, dtype=np.uint16)
+    DL = np.ascontiguousarray(DL, dtype=np.uint16)
+    H, W, D = S.shape
+    out = np.empty((H, W), np.float64)
+    _check(_load().r2o_subpixel(_ptr(S), _ptr(DL), W, H, D, _ptr(out)), "subpixel")
+    return out
+
+
+def median3x3_f64(Din: np.ndarray) -> np.ndarray:
+    Din = np.ascontiguousarray(Din, dtype=np.float64)
+    H, W = Din.shape
+    out = np.empty((H, W), np.float64)
+    _check(_load().r2o_median3x3_f64(_ptr(Din), W, H, _ptr(out)), "median3x3_f64")
+    return out
+
+
+def sgm_subpixel(left: np.ndarray, right: np.ndarray, D: int, census_w: int, census_h: int,
+                 P1: int, P2: int, num_paths: int, flags: int, lr_threshold: int = 1):
+    """Whole pipeline with the sub-pixel refinement. Returns (final map, refined D^L), float64,
+    +inf where invalid."""
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    right = np.ascontiguousarray(right, dtype=np.uint8)
+    H, W = left.shape
+    disp = np.empty((H, W), np.float64)
+    ref = np.empty((H, W), np.float64)
+    rc = _load().r2o_sgm_subpixel(_ptr(left), _ptr(right), W, W, H, D, census_w, census_h, P1,
+                                  P2, num_paths, flags, lr_threshold, _ptr(disp), _ptr(ref))
+    _check(rc, "sgm_subpixel")
+    return disp, ref

@@ -25,6 +25,14 @@
  *                       the image and invalid pixels count as 0xFFFF; the output is element [4]
  *                       of the 9 sorted values (what five bubble-sort passes leave, App. D).
  *   r2o_sgm             the whole chain above, in the order of Sec. 2.1.
+ *   r2o_subpixel        sub-pixel refinement, Sec. 2.1.3 ("Subpixel disparity refinement"): the
+ *                       parabola through the aggregated costs at D^L(p) - 1, D^L(p), D^L(p) + 1,
+ *                       fitted by solving its 3 x 3 system in fp64; D^L(p) moves to the abscissa
+ *                       of its minimum. D^L = 0 and D^L = D - 1 have one neighbour and stay.
+ *   r2o_median3x3_f64   the 3x3 median above on a double map (+infinity = invalid).
+ *   r2o_sgm_subpixel    the chain with the refinement ("fine" in Tab. throughput): the check
+ *                       compares the integer D^L with D^R, keeps the refined value, and the
+ *                       median runs on the refined values.
  *
  * Conventions where the paper is silent (each is a reading, listed in the design doc):
  *   - census bit = [neighbour < centre], row-major over the window (rows outer), LSB first;
@@ -33,6 +41,7 @@
  *
  * Return value of every function: 0 on success, -1 on an invalid argument.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -294,5 +303,152 @@ int r2o_sgm(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int
   free(DR);
   free(Dlr);
   free(mask);
+  return rc;
+}
+
+/* Solves the 3 x 3 system M c = v in place by Gaussian elimination with partial pivoting;
+ * returns -1 if M is singular. */
+static int solve3(double M[3][3], double v[3], double c[3]) {
+  for (int k = 0; k < 3; k++) {
+    int piv = k;
+    for (int i = k + 1; i < 3; i++)
+      if (fabs(M[i][k]) > fabs(M[piv][k])) piv = i;
+    if (M[piv][k] == 0.0) return -1;
+    if (piv != k) {
+      for (int j = 0; j < 3; j++) {
+        double t = M[k][j];
+        M[k][j] = M[piv][j];
+        M[piv][j] = t;
+      }
+      double t = v[k];
+      v[k] = v[piv];
+      v[piv] = t;
+    }
+    for (int i = k + 1; i < 3; i++) {
+      double f = M[i][k] / M[k][k];
+      for (int j = k; j < 3; j++) M[i][j] -= f * M[k][j];
+      v[i] -= f * v[k];
+    }
+  }
+  for (int i = 2; i >= 0; i--) {
+    double t = v[i];
+    for (int j = i + 1; j < 3; j++) t -= M[i][j] * c[j];
+    c[i] = t / M[i][i];
+  }
+  return 0;
+}
+
+/* Sub-pixel refinement of D^L (Sec. 2.1.3). For each pixel with 1 <= d = D^L(p) <= D - 2, the
+ * parabola s(t) = c0 t^2 + c1 t + c2 through (-1, S(p, d-1)), (0, S(p, d)), (1, S(p, d+1)), t
+ * measured from d, is solved for, and the abscissa of its minimum, -c1 / (2 c0), is added to d.
+ * A parabola that does not open upwards has no minimum; the WTA winner makes that impossible
+ * (S(d-1) > S(d) <= S(d+1)), and such a pixel is reported as an error. Other pixels keep d. */
+int r2o_subpixel(const uint16_t* S, const uint16_t* DL, int W, int H, int D, double* out) {
+  if (!S || !DL || !out || W < 1 || H < 1 || D < 1) return -1;
+  for (int64_t p = 0; p < (int64_t)W * H; p++) {
+    int d = DL[p];
+    if (d >= D) return -1;
+    out[p] = (double)d;
+    if (d < 1 || d > D - 2) continue;
+    double M[3][3], v[3], c[3];
+    for (int k = 0; k < 3; k++) {
+      double t = (double)(k - 1);
+      M[k][0] = t * t;
+      M[k][1] = t;
+      M[k][2] = 1.0;
+      v[k] = (double)S[p * D + d - 1 + k];
+    }
+    if (solve3(M, v, c) != 0 || !(c[0] > 0.0)) return -1;
+    out[p] = (double)d + -c[1] / (2.0 * c[0]);
+  }
+  return 0;
+}
+
+/* 3x3 median of a double map: for each valid (finite) pixel, element [4] of its sorted 3x3
+ * neighbourhood, where pixels outside the image and invalid pixels read +infinity; invalid
+ * pixels stay +infinity. */
+int r2o_median3x3_f64(const double* Din, int W, int H, double* Dout) {
+  if (!Din || !Dout || W < 1 || H < 1 || Din == Dout) return -1;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      int64_t p = (int64_t)y * W + x;
+      if (isinf(Din[p])) {
+        Dout[p] = INFINITY;
+        continue;
+      }
+      double v[9];
+      int n = 0;
+      for (int j = -1; j <= 1; j++)
+        for (int i = -1; i <= 1; i++) {
+          int xx = x + i, yy = y + j;
+          v[n++] = (xx >= 0 && xx < W && yy >= 0 && yy < H) ? Din[(int64_t)yy * W + xx]
+                                                            : INFINITY;
+        }
+      for (int a = 1; a < 9; a++) { /* insertion sort */
+        double t = v[a];
+        int b = a - 1;
+        while (b >= 0 && v[b] > t) {
+          v[b + 1] = v[b];
+          b--;
+        }
+        v[b + 1] = t;
+      }
+      Dout[p] = v[4];
+    }
+  return 0;
+}
+
+/* Whole pipeline with the sub-pixel refinement (flags as r2o_sgm). disp receives the final
+ * double map (+infinity where invalid); refined (may be NULL) the refined D^L before the check. */
+int r2o_sgm_subpixel(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int H,
+                     int D, int cw, int ch, int P1, int P2, int R, int flags, int lr_threshold,
+                     double* disp, double* refined) {
+  if (!left || !right || !disp || W < 1 || H < 1 || D < 1 || D > 256) return -1;
+  int64_t npx = (int64_t)W * H, nde = npx * D;
+  uint64_t* ctl = (uint64_t*)malloc((size_t)npx * 8);
+  uint64_t* ctr = (uint64_t*)malloc((size_t)npx * 8);
+  uint8_t* cost = (uint8_t*)malloc((size_t)nde);
+  uint16_t* S = (uint16_t*)malloc((size_t)nde * 2);
+  uint16_t* DL = (uint16_t*)malloc((size_t)npx * 2);
+  uint16_t* DR = (uint16_t*)malloc((size_t)npx * 2);
+  uint16_t* Dlr = (uint16_t*)malloc((size_t)npx * 2);
+  uint8_t* mask = (uint8_t*)malloc((size_t)npx);
+  double* ref = (double*)malloc((size_t)npx * 8);
+  double* chk = (double*)malloc((size_t)npx * 8);
+  int rc = -1;
+  if (ctl && ctr && cost && S && DL && DR && Dlr && mask && ref && chk) {
+    rc = r2o_census(left, pitch, W, H, cw, ch, ctl);
+    if (!rc) rc = r2o_census(right, pitch, W, H, cw, ch, ctr);
+    if (!rc) rc = r2o_cost(ctl, ctr, W, H, D, cost);
+    if (!rc) rc = r2o_aggregate(cost, W, H, D, R, P1, P2, S);
+    if (!rc) rc = r2o_wta(S, W, H, D, DL);
+    if (!rc) rc = r2o_right_disparity(S, W, H, D, DR);
+    if (!rc) rc = r2o_subpixel(S, DL, W, H, D, ref);
+    if (!rc) {
+      if (flags & 1) {
+        rc = r2o_lr_check(DL, DR, W, H, lr_threshold, Dlr, mask);
+      } else {
+        memset(mask, 1, (size_t)npx);
+      }
+    }
+    if (!rc) {
+      for (int64_t p = 0; p < npx; p++) chk[p] = mask[p] ? ref[p] : INFINITY;
+      if (flags & 2)
+        rc = r2o_median3x3_f64(chk, W, H, disp);
+      else
+        memcpy(disp, chk, (size_t)npx * 8);
+    }
+    if (!rc && refined) memcpy(refined, ref, (size_t)npx * 8);
+  }
+  free(ctl);
+  free(ctr);
+  free(cost);
+  free(S);
+  free(DL);
+  free(DR);
+  free(Dlr);
+  free(mask);
+  free(ref);
+  free(chk);
   return rc;
 }

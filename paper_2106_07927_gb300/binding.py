@@ -30,6 +30,7 @@ EXPORTS = (
     "res2tac_stage_times", "res2tac_probe_int_peak", "res2tac_probe_red_peak",
     "res2tac_batch_reserve",
     "res2tac_compute_static",
+    "res2tac_compute_subpixel", "res2tac_debug_subpixel",
 )
 RES2TAC_STATIC_SCRATCH_BYTES = 80 << 20
 STAGES = ("census_cost", "aggregate", "wta_dr", "lr_median")
@@ -101,6 +102,8 @@ def load():
         "res2tac_probe_red_peak": (ctypes.c_int, [I64, I32, P, ctypes.POINTER(ctypes.c_double)]),
         "res2tac_batch_reserve": (ctypes.c_int, [P, S, I32]),
         "res2tac_compute_static": (ctypes.c_int, [PP, P, P, I64, P, I64, P]),
+        "res2tac_compute_subpixel": (ctypes.c_int, [P, P, P, I64, P, I64, P]),
+        "res2tac_debug_subpixel": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -142,6 +145,16 @@ def res2tac_compute(h: int, left: int, right: int, in_pitch: int, disp: int, out
 def res2tac_compute_host(h: int, left: int, right: int, in_pitch: int, disp: int, out_pitch: int,
                          stream: int = 0) -> None:
     _check(load().res2tac_compute_host(h, left, right, in_pitch, disp, out_pitch, stream))
+
+
+def res2tac_compute_subpixel(h: int, left: int, right: int, in_pitch: int, disp: int,
+                             out_pitch: int, stream: int = 0) -> None:
+    """Pipeline with sub-pixel refinement; disp is a device float map (+inf = invalid)."""
+    _check(load().res2tac_compute_subpixel(h, left, right, in_pitch, disp, out_pitch, stream))
+
+
+def res2tac_debug_subpixel(h: int, dl_sub: int, stream: int = 0) -> None:
+    _check(load().res2tac_debug_subpixel(h, dl_sub, stream))
 
 
 def res2tac_compute_static(params: res2tac_params, left: int, right: int, in_pitch: int,
@@ -269,6 +282,27 @@ class Stereo:
         res2tac_compute(self.handle, left.data_ptr(), right.data_ptr(), left.stride(0),
                         out.data_ptr(), out.stride(0) * 2, self._stream())
         return out
+
+    def compute_subpixel(self, left, right, out=None):
+        """As compute, with sub-pixel refinement: returns a float32 [H, W] map, +inf where the
+        left-right check rejected the pixel."""
+        import torch
+        H, W = self.params.height, self.params.width
+        assert left.is_cuda and left.dtype == torch.uint8 and tuple(left.shape) == (H, W)
+        assert right.stride() == left.stride() and left.stride(1) == 1
+        if out is None:
+            out = torch.empty((H, W), dtype=torch.float32, device=left.device)
+        res2tac_compute_subpixel(self.handle, left.data_ptr(), right.data_ptr(), left.stride(0),
+                                 out.data_ptr(), out.stride(0) * 4, self._stream())
+        return out
+
+    def debug_subpixel(self):
+        """Sub-pixel D^L (before the check and the median) of the last compute_subpixel."""
+        import torch
+        H, W = self.params.height, self.params.width
+        o = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        res2tac_debug_subpixel(self.handle, o.data_ptr(), self._stream())
+        return o
 
     def debug_outputs(self):
         import torch

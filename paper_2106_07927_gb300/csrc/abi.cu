@@ -210,6 +210,39 @@ int res2tac_compute_host(res2tac_t h, const uint8_t* left, const uint8_t* right,
   return RES2TAC_OK;
 }
 
+int res2tac_compute_subpixel(res2tac_t h, const uint8_t* left, const uint8_t* right,
+                             int64_t in_pitch, float* disp, int64_t out_pitch,
+                             res2tac_stream_t s) {
+  if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
+  if (!left || !right || !disp) return fail(RES2TAC_EINVAL, "NULL image or output pointer");
+  if (in_pitch < h->p.width) return fail(RES2TAC_EINVAL, "in_pitch < width");
+  if (out_pitch < 4 * (int64_t)h->p.width || (out_pitch & 3))
+    return fail(RES2TAC_EINVAL, "out_pitch must be a multiple of 4 and >= 4 * width");
+  if ((reinterpret_cast<uintptr_t>(disp) & 3) != 0)
+    return fail(RES2TAC_EINVAL, "disp must be 4-byte aligned");
+  r2t::Problem pb = problem_at(h->scratch, h->lay, h->p.width, h->p.height, h->p.max_disp);
+  pb.left = left;
+  pb.right = right;
+  pb.in_pitch = in_pitch;
+  pb.disp = nullptr;
+  pb.disp_f = disp;
+  pb.out_pitch = out_pitch;
+  int n = 0;
+  cudaError_t e = r2t::run_pipeline(pb, h->method, h->tuning, (cudaStream_t)s, &n,
+                                    h->profiling ? h->ev : nullptr, &h->fork);
+  h->last_launches = n;
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_compute_subpixel launch");
+  return RES2TAC_OK;
+}
+
+int res2tac_debug_subpixel(res2tac_t h, float* dl_sub, res2tac_stream_t s) {
+  if (!h || !dl_sub) return fail(RES2TAC_EINVAL, "NULL argument");
+  r2t::Problem pb = problem_at(h->scratch, h->lay, h->p.width, h->p.height, h->p.max_disp);
+  cudaError_t e = r2t::copy_subpixel(pb, h->method.wide != 0, dl_sub, (cudaStream_t)s);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_debug_subpixel");
+  return RES2TAC_OK;
+}
+
 int res2tac_debug_outputs(res2tac_t h, uint8_t* cost, uint16_t* agg, uint16_t* dl, uint16_t* dr,
                           uint8_t* mask, res2tac_stream_t s) {
   if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");

@@ -33,6 +33,7 @@ struct Problem {
   uint16_t* dr;       // [H][W] approximate right map
   uint32_t* kr;       // [H][W] right-disparity keys S << 8 | d, reduced with atomicMin
   uint8_t* mask;      // [H][W] 1 = kept by the left-right check
+  float* disp_f;      // sub-pixel final map (caller's, out_pitch bytes per row); NULL: uint16 map
 };
 
 // Method parameters shared by every pair of a call.

@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(256) batch_median_kernel(const BatchHeader* hd
     if (item >= total) break;
     const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
-    lr_median_tile(pb, mt, item - prefix[p], sm);
+    lr_median_tile<false, false>(pb, mt, item - prefix[p], sm);
   }
 }
 

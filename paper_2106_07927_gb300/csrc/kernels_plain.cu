@@ -17,9 +17,27 @@ __global__ void __launch_bounds__(256) wta_dr_kernel(Problem pb, int T) {
   wta_dr_tile<WIDE>(pb, blockIdx.x, wkeys, T);
 }
 
+template <bool SUB, bool WIDE>
 __global__ void __launch_bounds__(256) lr_median_kernel(Problem pb, Method mt) {
-  __shared__ MedianSmem sm;
-  lr_median_tile(pb, mt, blockIdx.x, sm);
+  __shared__ MedianSmemT<SUB> sm;
+  lr_median_tile<SUB, WIDE>(pb, mt, blockIdx.x, sm);
+}
+
+// Debug map of the sub-pixel D^L (before the left-right check).
+template <bool WIDE>
+__global__ void subpixel_map_kernel(Problem pb, float* out) {
+  const int64_t n = (int64_t)pb.W * pb.H;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = refine_subpixel<WIDE>(pb, i, pb.dl[i]);
+}
+
+cudaError_t copy_subpixel(const Problem& pb, bool wide, float* dst, cudaStream_t s) {
+  if (wide)
+    subpixel_map_kernel<true><<<608, 256, 0, s>>>(pb, dst);
+  else
+    subpixel_map_kernel<false><<<608, 256, 0, s>>>(pb, dst);
+  return cudaGetLastError();
 }
 
 // Debug copy of the aggregated volume, sums saturated to uint16.
@@ -110,14 +128,21 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
   if (ev) cudaEventRecord(ev[2], s);
   const int T = tn.wta_chunk;  // pixels per block of 256 threads
   const size_t smem = wta_smem_bytes(pb.D, T);
+  const int nw = wta_items(pb.W, pb.H, T);
   if (mt.wide)
-    wta_dr_kernel<true><<<wta_items(pb.W, pb.H, T), 256, smem, s>>>(pb, T);
+    wta_dr_kernel<true><<<nw, 256, smem, s>>>(pb, T);
   else
-    wta_dr_kernel<false><<<wta_items(pb.W, pb.H, T), 256, smem, s>>>(pb, T);
+    wta_dr_kernel<false><<<nw, 256, smem, s>>>(pb, T);
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], s);
-  lr_median_kernel<<<median_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
+  const int nm = median_items(pb.W, pb.H);
+  if (pb.disp_f == nullptr)  // uint16 map
+    lr_median_kernel<false, false><<<nm, 256, 0, s>>>(pb, mt);
+  else if (mt.wide)          // sub-pixel float map
+    lr_median_kernel<true, true><<<nm, 256, 0, s>>>(pb, mt);
+  else
+    lr_median_kernel<true, false><<<nm, 256, 0, s>>>(pb, mt);
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[4], s);

@@ -66,5 +66,7 @@ cudaError_t probe_red_peak(int64_t bytes, int passes, cudaStream_t s, double* by
 // Copies the aggregated volume as saturated uint16 / the cost volume, both in natural order.
 cudaError_t copy_agg_u16(const Problem& pb, bool wide, uint16_t* dst, cudaStream_t s);
 cudaError_t copy_cost(const Problem& pb, uint8_t* dst, cudaStream_t s);
+// Writes the sub-pixel D^L map of the last sub-pixel run (float [H][W]).
+cudaError_t copy_subpixel(const Problem& pb, bool wide, float* dst, cudaStream_t s);
 
 }  // namespace r2t

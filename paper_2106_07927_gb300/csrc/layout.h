@@ -41,6 +41,7 @@ inline Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
   pb.dr = reinterpret_cast<uint16_t*>(base + l.dr);
   pb.kr = reinterpret_cast<uint32_t*>(base + l.kr);
   pb.mask = reinterpret_cast<uint8_t*>(base + l.mask);
+  pb.disp_f = nullptr;
   return pb;
 }
 

@@ -8,6 +8,13 @@
 // for every target x' = x - d. The paper gathers S for D^R with strided, uncoalesced reads
 // (Sec. 2.2.3); here every source is read once and each of its keys is scattered to its target.
 // Keys are S << 8 | d, so the minimum key carries the least S and, among equal S, the smallest d.
+// Sub-pixel refinement (Sec. 2.1.3): the parabola through S(x, d-1), S(x, d), S(x, d+1) at
+// d = D^L(x) has its minimum at d + delta with
+//   delta = (a - b) / (2 (a + b)),  a = S(d-1) - S(d),  b = S(d+1) - S(d),
+// taken in fp32 with correctly rounded division and addition; D^L = 0 and D^L = D - 1 have one
+// neighbour only and stay integral. a > 0 because d is the smallest minimiser and b >= 0, so the
+// denominator is positive and delta lies in (-1/2, 1/2]. It runs in the left-right / median
+// stage, one thread per pixel, which reads the three costs (adjacent in the volume) directly.
 //
 // lr_median_tile: the left-right check of Eq. (LR_check) (App. B) for a tile and its 1-pixel
 // frame, then the 3x3 median of the valid pixels (Sec. 2.1.3): element [4] of the nine sorted
@@ -16,6 +23,8 @@
 // of medians, min of maxima}) selects the same element as the paper's five bubble-sort passes
 // with fewer comparators.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace r2t {
@@ -72,6 +81,31 @@ __device__ __forceinline__ void wta_keys(const Problem& pb, int64_t rowbase, int
   }
   kl = __reduce_min_sync(0xffffffffu, kl);
   if (lane == 0) pb.dl[rowbase + x] = (uint16_t)(kl & 0xFFu);
+}
+
+// Sub-pixel D^L of pixel p (Sec. 2.1.3) from its integer D^L d and the aggregated costs at d - 1,
+// d, d + 1 (saturated to 16 bits as in the uint16 volume).
+template <bool WIDE>
+__device__ __forceinline__ float refine_subpixel(const Problem& pb, int64_t p, int d) {
+  float v = (float)d;
+  if (d >= 1 && d <= pb.D - 2) {
+    const int64_t i = p * pb.D + d;
+    uint32_t sm, s0, sp;
+    if (WIDE) {
+      const uint32_t* S = reinterpret_cast<const uint32_t*>(pb.agg);
+      sm = min(S[i - 1], 65535u);
+      s0 = min(S[i], 65535u);
+      sp = min(S[i + 1], 65535u);
+    } else {
+      const uint16_t* S = reinterpret_cast<const uint16_t*>(pb.agg);
+      sm = S[i - 1];
+      s0 = S[i];
+      sp = S[i + 1];
+    }
+    const int a = (int)(sm - s0), b = (int)(sp - s0);  // a > 0, b >= 0
+    v = __fadd_rn(v, __fdiv_rn((float)(a - b), (float)(2 * (a + b))));
+  }
+  return v;
 }
 
 // One tile of T pixels of a row, 256 threads: warp w takes pixels w, w + 8, ..., PF at a time so
@@ -144,9 +178,14 @@ constexpr int kMedTH = 4;
 __host__ __device__ inline int median_items(int W, int H) {
   return ((W + kMedTW - 1) / kMedTW) * ((H + kMedTH - 1) / kMedTH);
 }
-struct MedianSmem {
-  uint16_t t[kMedTH + 2][kMedTW + 2];
+// Tile plus frame of checked disparities: uint16 values, or (sub-pixel) the bit patterns of
+// non-negative floats, which order as unsigned integers do, with +infinity as the invalid value.
+template <bool SUB>
+struct MedianSmemT {
+  typename std::conditional<SUB, uint32_t, uint16_t>::type t[kMedTH + 2][kMedTW + 2];
 };
+using MedianSmem = MedianSmemT<false>;
+constexpr uint32_t kInvalidF = 0x7F800000u;  // +infinity
 
 __device__ __forceinline__ void sort2(uint32_t& a, uint32_t& b) {
   const uint32_t lo = min(a, b), hi = max(a, b);
@@ -162,21 +201,29 @@ __device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c) {
   return max(min(a, b), min(max(a, b), c));
 }
 
-// Disparity of pixel (x, y) after the left-right check (or D^L when the check is off).
+// Disparity of pixel (x, y) after the left-right check (or D^L when the check is off). The check
+// always compares the integer D^L with D^R; SUB returns the bits of the sub-pixel D^L it kept.
+template <bool SUB, bool WIDE>
 __device__ __forceinline__ uint32_t checked_disp(const Problem& pb, const Method& mt, int x, int y) {
+  constexpr uint32_t inv = SUB ? kInvalidF : kInvalid;
   const int64_t row = (int64_t)y * pb.W;
   const int dl = pb.dl[row + x];
-  if (!(mt.flags & 1)) return (uint32_t)dl;
-  if (x - dl < 0) return kInvalid;
-  const int dr = (int)(pb.kr[row + x - dl] & 0xFFu);
-  const int diff = dl - dr;
-  return (diff < 0 ? -diff : diff) <= mt.lr_threshold ? (uint32_t)dl : kInvalid;
+  if (mt.flags & 1) {
+    if (x - dl < 0) return inv;
+    const int dr = (int)(pb.kr[row + x - dl] & 0xFFu);
+    const int diff = dl - dr;
+    if ((diff < 0 ? -diff : diff) > mt.lr_threshold) return inv;
+  }
+  return SUB ? __float_as_uint(refine_subpixel<WIDE>(pb, row + x, dl)) : (uint32_t)dl;
 }
 
 // Final map of one 64 x 4 tile: LR check (+ median when flags & 2), plus the debug maps D^R and
-// the LR mask of the tile's own pixels.
+// the LR mask of the tile's own pixels. SUB writes the float map pb.disp_f (+infinity where
+// invalid) from the sub-pixel D^L instead of the uint16 map (WIDE: uint32 aggregated sums).
+template <bool SUB, bool WIDE>
 __device__ __forceinline__ void lr_median_tile(const Problem& pb, const Method& mt, int item,
-                                               MedianSmem& sm) {
+                                               MedianSmemT<SUB>& sm) {
+  constexpr uint32_t inv = SUB ? kInvalidF : kInvalid;
   const int W = pb.W, H = pb.H;
   const int ntx = (W + kMedTW - 1) / kMedTW;
   const int x0 = (item % ntx) * kMedTW, y0 = (item / ntx) * kMedTH;
@@ -186,7 +233,7 @@ __device__ __forceinline__ void lr_median_tile(const Problem& pb, const Method& 
       const int ty = i / (kMedTW + 2), tx = i % (kMedTW + 2);
       const int gx = x0 + tx - 1, gy = y0 + ty - 1;
       sm.t[ty][tx] =
-          (gx >= 0 && gx < W && gy >= 0 && gy < H) ? (uint16_t)checked_disp(pb, mt, gx, gy) : kInvalid;
+          (gx >= 0 && gx < W && gy >= 0 && gy < H) ? checked_disp<SUB, WIDE>(pb, mt, gx, gy) : inv;
     }
     __syncthreads();
   }
@@ -197,7 +244,7 @@ __device__ __forceinline__ void lr_median_tile(const Problem& pb, const Method& 
     uint32_t out;
     if (median) {
       out = sm.t[ly + 1][lx + 1];
-      if (out != kInvalid) {
+      if (out != inv) {
         uint32_t a0 = sm.t[ly][lx], a1 = sm.t[ly][lx + 1], a2 = sm.t[ly][lx + 2];
         uint32_t b0 = sm.t[ly + 1][lx], b1 = out, b2 = sm.t[ly + 1][lx + 2];
         uint32_t c0 = sm.t[ly + 2][lx], c1 = sm.t[ly + 2][lx + 1], c2 = sm.t[ly + 2][lx + 2];
@@ -209,14 +256,18 @@ __device__ __forceinline__ void lr_median_tile(const Problem& pb, const Method& 
         const uint32_t hi = min(min(a2, b2), c2);
         out = med3(lo, mid, hi);
       }
-      pb.mask[p] = sm.t[ly + 1][lx + 1] != kInvalid ? 1 : 0;
+      pb.mask[p] = sm.t[ly + 1][lx + 1] != inv ? 1 : 0;
     } else {
-      out = checked_disp(pb, mt, x, y);
-      pb.mask[p] = out != kInvalid ? 1 : 0;
+      out = checked_disp<SUB, WIDE>(pb, mt, x, y);
+      pb.mask[p] = out != inv ? 1 : 0;
     }
     pb.dr[p] = (uint16_t)(pb.kr[p] & 0xFFu);
-    *reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(pb.disp) + (int64_t)y * pb.out_pitch +
-                                 2 * (int64_t)x) = (uint16_t)out;
+    if (SUB)
+      *reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(pb.disp_f) +
+                                   (int64_t)y * pb.out_pitch + 4 * (int64_t)x) = out;
+    else
+      *reinterpret_cast<uint16_t*>(reinterpret_cast<uint8_t*>(pb.disp) +
+                                   (int64_t)y * pb.out_pitch + 2 * (int64_t)x) = (uint16_t)out;
   }
   if (median) __syncthreads();
 }

@@ -326,3 +326,91 @@ def test_occluded_band_is_invalidated():
     assert occl.mean() < 0.2
     assert vis.mean() > 0.95
     assert np.all(out[8:H - 8, 40:x1 - 20][vis.astype(bool)] == 4)
+
+
+# ------------------------------------------------------------------ sub-pixel refinement (Sec. 2.1.3)
+def _parabola_volume(rng, H, W, D):
+    """S(p, d) = A (d - d*)^2 + B with d* = k + j/4: integral at integer d when 16 | A, so the
+    parabola through any three samples is the generating one and its minimum lies at d*."""
+    k = rng.integers(1, D - 1, size=(H, W))
+    j = rng.integers(-1, 2, size=(H, W))          # d* - k in {-1/4, 0, 1/4}
+    A = 16 * rng.integers(1, 4, size=(H, W))
+    B = rng.integers(0, 200, size=(H, W))
+    d = np.arange(D)[None, None, :]
+    dstar4 = 4 * k + j                             # 4 d*
+    S4 = A[..., None] * (4 * d - dstar4[..., None]) ** 2  # 16 A (d - d*)^2
+    S = S4 // 16 + B[..., None]
+    assert np.all(S4 % 16 == 0) and S.max() < 65535
+    return S.astype(np.uint16), dstar4 / 4.0
+
+
+def test_subpixel_recovers_parabola_vertex():
+    rng = np.random.default_rng(11)
+    S, dstar = _parabola_volume(rng, 6, 9, 32)
+    DL = oracle.wta(S)
+    assert np.array_equal(DL, np.round(dstar).astype(np.uint16))
+    ref = oracle.subpixel(S, DL)
+    assert np.array_equal(ref, dstar)  # exact: a sign or index error moves it by 1/2
+
+
+def test_subpixel_half_pixel_tie_and_edges():
+    D = 8
+    S = np.full((1, 5, D), 500, np.uint16)
+    S[0, 0, :] = [9, 5, 5, 9, 20, 30, 40, 50]       # tie d = 1, 2: WTA takes 1, vertex at 1.5
+    S[0, 1, :] = [3, 8, 9, 9, 9, 9, 9, 9]           # D^L = 0: stays integral
+    S[0, 2, :] = [9, 9, 9, 9, 9, 9, 8, 3]           # D^L = D - 1: stays integral
+    S[0, 3, :] = [65535, 0, 65535, 1, 1, 1, 1, 1]   # saturated neighbours: symmetric, delta 0
+    S[0, 4, :] = [100, 10, 40, 60, 70, 80, 90, 95]  # a = 90, b = 30: delta = 60 / 240
+    DL = oracle.wta(S)
+    ref = oracle.subpixel(S, DL)
+    assert list(DL[0]) == [1, 0, 7, 1, 1]
+    assert list(ref[0]) == [1.5, 0.0, 7.0, 1.0, 1.25]
+
+
+def test_subpixel_invariant_under_offset_and_scale():
+    rng = np.random.default_rng(5)
+    S = rng.integers(0, 3000, size=(4, 7, 24)).astype(np.int64)
+    DL = oracle.wta(S.astype(np.uint16))
+    base = oracle.subpixel(S.astype(np.uint16), DL)
+    for a, b in ((1, 77), (3, 0), (5, 1000)):
+        T = (a * S + b).astype(np.uint16)
+        assert np.array_equal(oracle.wta(T), DL)
+        assert np.allclose(oracle.subpixel(T, DL), base, rtol=0, atol=1e-12)
+    assert np.all(np.abs(base - DL) <= 0.5)
+
+
+def test_median_f64_matches_integer_median_and_sort():
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        H, W = rng.integers(1, 9, size=2)
+        Din = rng.integers(0, 40, size=(H, W)).astype(np.uint16)
+        Din[rng.random((H, W)) < 0.3] = oracle.INVALID
+        F = np.where(Din == oracle.INVALID, np.inf, Din.astype(np.float64))
+        want = oracle.median3x3(Din)
+        got = oracle.median3x3_f64(F)
+        assert np.array_equal(np.where(want == oracle.INVALID, np.inf, want), got)
+        # non-integral values: element [4] of the sorted 9-neighbourhood (numpy sort)
+        G = np.where(np.isinf(F), np.inf, F + rng.random((H, W)) * 0.9)
+        pad = np.pad(G, 1, constant_values=np.inf)
+        got = oracle.median3x3_f64(G)
+        for y in range(H):
+            for x in range(W):
+                want_v = np.inf if np.isinf(G[y, x]) else np.sort(pad[y:y + 3, x:x + 3].ravel())[4]
+                assert got[y, x] == want_v
+
+
+@pytest.mark.parametrize("flags", [0, 1, 3])
+def test_sgm_subpixel_within_half_pixel_of_integer_pipeline(flags):
+    from paper_2106_07927_gb300 import scenes
+    L, R, _, prm = scenes.single_pair("320x240_d64_ct5x5_r4", 1)
+    L, R = L[:60, :120], R[:60, :120]
+    D = prm["max_disp"]
+    integer = oracle.sgm(L, R, D, 5, 5, 10, 120, 4, flags)
+    sub, ref = oracle.sgm_subpixel(L, R, D, 5, 5, 10, 120, 4, flags)
+    inv = integer == oracle.INVALID
+    assert np.array_equal(inv, np.isinf(sub))  # validity is decided on the integer maps
+    # every refined value lies within 1/2 of its integer one; the median is 1-Lipschitz
+    assert np.all(np.abs(sub[~inv] - integer[~inv]) <= 0.5)
+    _, dbg = oracle.sgm(L, R, D, 5, 5, 10, 120, 4, flags, debug=True)
+    assert np.all(np.abs(ref - dbg["dl"]) <= 0.5)
+    assert np.array_equal(ref, oracle.subpixel(dbg["agg"], dbg["dl"]))
