@@ -299,6 +299,40 @@ def main():
             if (~inv).any() else 0.0,
         }
 
+        # exact consistency check ("exact-cc", Sec. 3.2.3): D^R from a second full matching of
+        # the swapped, flipped pair
+        xprm = dict(prm, flags=prm["flags"] | binding.RES2TAC_EXACT_CC)
+        xctx = binding.Stereo(xprm)
+        outx = torch.empty((H, W), dtype=torch.int16, device="cuda")
+
+        def step_exact():
+            binding.res2tac_compute(xctx.handle, Ld.data_ptr(), Rd.data_ptr(), W,
+                                    outx.data_ptr(), 2 * W, sh)
+
+        for _ in range(3):
+            flush.zero_()
+            step_exact()
+        torch.cuda.synchronize()
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()
+            ev0[i].record(stream)
+            step_exact()
+            ev1[i].record(stream)
+        barrier()
+        torch.cuda.synchronize()
+        x_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / args.steps)
+        launches += binding.res2tac_last_launch_count(xctx.handle) * args.steps
+        xo = binding.u16(outx)
+        exact_cc = {
+            "value": round(ws * de / (x_ms / 1e3) / 1e6, 1), "unit": "MDE/s",
+            "ms_per_step": round(x_ms, 4),
+            "valid_fraction": round(float((xo != binding.RES2TAC_INVALID).mean()), 4),
+            "valid_fraction_approximate_check": round(
+                float((binding.u16(out) != binding.RES2TAC_INVALID).mean()), 4),
+        }
+        xctx.close()
+
         # end to end through the host-buffer entry point (pinned memory)
         hl = torch.from_numpy(left).pin_memory()
         hr = torch.from_numpy(right).pin_memory()
@@ -405,6 +439,7 @@ def main():
     mean_ms = max_over_ranks(sum(step_ms) / len(step_ms))
     value = ws * de / (mean_ms / 1e3) / 1e6
     subpixel["throughput_vs_integer_step"] = round(mean_ms / subpixel["ms_per_step"], 3)
+    exact_cc["throughput_vs_integer_step"] = round(mean_ms / exact_cc["ms_per_step"], 3)
     agg_ms = stage["aggregate"] / args.steps
     # algorithmic operations and bytes of the aggregation per launch (16-bit lane operations):
     # 9 per DE and path (8 of the recurrence, 1 accumulation) + 2 per DE (cost xor/popcount read)
@@ -426,6 +461,7 @@ def main():
         "fps": round(1e3 / mean_ms * ws, 1),
         "stage_ms": {k: round(v / args.steps, 4) for k, v in stage.items()},
         "subpixel": subpixel,
+        "exact_cc": exact_cc,
         "roofline": {"kernel": "aggregate (SGM paths)", "bound": "alu",
                      "achieved": round(achieved / 1e12, 3),
                      "peak": round(int_peak / 1e12, 3), "unit": "T lane-ops/s",

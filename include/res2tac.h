@@ -37,6 +37,11 @@ extern "C" {
 /* flags */
 #define RES2TAC_LR_CHECK 1 /* approximate left-right consistency check, Eq. (LR_check) */
 #define RES2TAC_MEDIAN 2   /* 3x3 median over the valid pixels, Sec. 2.1.3 */
+/* exact consistency check (Sec. 3.2.3, "exact-cc" in Tab. throughput): D^R for the check is the
+ * full matching of the swapped, horizontally flipped pair (census, cost, aggregation and WTA
+ * again, read back mirrored) instead of the approximation of Eq. (right_disparity); about twice
+ * the work. Single pairs only: res2tac_compute_batch rejects it. */
+#define RES2TAC_EXACT_CC 4
 
 #define RES2TAC_INVALID 0xFFFF /* disparity of a pixel rejected by the left-right check */
 
@@ -52,7 +57,8 @@ typedef void* res2tac_stream_t; /* a cudaStream_t */
  *                  (Sec. 2.2.1).
  *   p1, p2         SGM penalties of Eq. (sgm_path), 0 <= p1 <= p2 <= 16384.
  *   num_paths      4 (LR, RL, TB, BT) or 8 (plus the four diagonals), Sec. 3.2.
- *   flags          RES2TAC_LR_CHECK | RES2TAC_MEDIAN (0 = winner-takes-all only).
+ *   flags          RES2TAC_LR_CHECK | RES2TAC_MEDIAN | RES2TAC_EXACT_CC (0 = winner-takes-all
+ *                  only; RES2TAC_EXACT_CC changes D^R, so it matters with RES2TAC_LR_CHECK).
  *   lr_threshold   largest accepted |D^L - D^R| of the left-right check (the paper uses 1). */
 typedef struct res2tac_params {
   int32_t width, height;
@@ -155,7 +161,8 @@ int res2tac_compute_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res
 /* Copies the intermediates of the last res2tac_compute on this context into caller buffers
  * (device pointers; any may be NULL): cost [H][W][D] uint8 (Eq. image_matching, 255 where
  * x - d < 0), agg [H][W][D] uint16 (S-bar of Eq. sgm_path_aggr, saturated at 65535),
- * dl / dr [H][W] uint16 (Eqs. wta and right_disparity), mask [H][W] uint8 (1 where the
+ * dl / dr [H][W] uint16 (Eq. wta; Eq. right_disparity, or the exact D^R with
+ * RES2TAC_EXACT_CC), mask [H][W] uint8 (1 where the
  * left-right check kept the pixel, all 1 without RES2TAC_LR_CHECK). Asynchronous on s. */
 int res2tac_debug_outputs(res2tac_t h, uint8_t* cost, uint16_t* agg, uint16_t* dl, uint16_t* dr,
                           uint8_t* mask, res2tac_stream_t s);
@@ -189,7 +196,8 @@ int res2tac_last_launch_count(res2tac_t h);
 /* Per-stage timing. With profiling enabled, res2tac_compute records a CUDA event on the caller's
  * stream before and after each stage. res2tac_stage_times waits for the last call and writes up
  * to n durations in milliseconds: [0] census + cost (+ clearing of the aggregated volume),
- * [1] path aggregation, [2] WTA + right-disparity keys, [3] LR check + median. */
+ * [1] path aggregation, [2] WTA + right-disparity keys, [3] LR check + median. With
+ * RES2TAC_EXACT_CC, [0] .. [2] add up both passes (and [0] the flip of the pair). */
 int res2tac_set_profiling(res2tac_t h, int enable);
 int res2tac_stage_times(res2tac_t h, float* ms, int n);
 
@@ -218,7 +226,8 @@ int res2tac_probe_red_peak(int64_t bytes, int32_t passes, res2tac_stream_t s, do
  * RES2TAC_STATIC_SCRATCH_BYTES compiled into the library; every GPU that loads the library holds
  * that array until the process exits.
  * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 9 B per pixel,
- * 5 B per W*H*D when num_paths * (255 + p2) > 65535) is rejected with RES2TAC_ENOMEM and a
+ * 5 B per W*H*D when num_paths * (255 + p2) > 65535, 4 B more per pixel with RES2TAC_EXACT_CC)
+ * is rejected with RES2TAC_ENOMEM and a
  * message giving both sizes; 640 x 480 with D = 64 fits.
  * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.

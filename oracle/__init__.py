@@ -25,6 +25,7 @@ DIRECTIONS = ((1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, 1), (1, -1), (-1, -
 INVALID = 0xFFFF
 FLAG_LR_CHECK = 1
 FLAG_MEDIAN = 2
+FLAG_EXACT_CC = 4
 
 
 def build(force: bool = False) -> str:
@@ -58,11 +59,13 @@ def _load():
         lib.r2o_median3x3.argtypes = [P, I, I, P]
         lib.r2o_sgm.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, P, P, P, P, P, P]
         lib.r2o_subpixel.argtypes = [P, P, I, I, I, P]
+        lib.r2o_cost_right.argtypes = [P, P, I, I, I, P]
         lib.r2o_median3x3_f64.argtypes = [P, I, I, P]
         lib.r2o_sgm_subpixel.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, P, P]
         for f in (lib.r2o_census, lib.r2o_cost, lib.r2o_path, lib.r2o_aggregate, lib.r2o_wta,
                   lib.r2o_right_disparity, lib.r2o_lr_check, lib.r2o_median3x3, lib.r2o_sgm,
-                  lib.r2o_subpixel, lib.r2o_median3x3_f64, lib.r2o_sgm_subpixel):
+                  lib.r2o_subpixel, lib.r2o_median3x3_f64, lib.r2o_sgm_subpixel,
+                  lib.r2o_cost_right):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -91,6 +94,16 @@ def cost(ctl: np.ndarray, ctr: np.ndarray, D: int) -> np.ndarray:
     H, W = ctl.shape
     out = np.empty((H, W, D), np.uint8)
     _check(_load().r2o_cost(_ptr(ctl), _ptr(ctr), W, H, D, _ptr(out)), "cost")
+    return out
+
+
+def cost_right(ctl: np.ndarray, ctr: np.ndarray, D: int) -> np.ndarray:
+    """Right-reference cost C^R(x, y, d) = popcount(CT_R(x, y) ^ CT_L(x + d, y)), 255 outside."""
+    ctl = np.ascontiguousarray(ctl, dtype=np.uint64)
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint64)
+    H, W = ctl.shape
+    out = np.empty((H, W, D), np.uint8)
+    _check(_load().r2o_cost_right(_ptr(ctl), _ptr(ctr), W, H, D, _ptr(out)), "cost_right")
     return out
 
 

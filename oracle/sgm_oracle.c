@@ -24,7 +24,15 @@
  *   r2o_median3x3       3x3 median of the valid pixels, Sec. 2.1.3 / Sec. 2.2.4: pixels outside
  *                       the image and invalid pixels count as 0xFFFF; the output is element [4]
  *                       of the 9 sorted values (what five bubble-sort passes leave, App. D).
- *   r2o_sgm             the whole chain above, in the order of Sec. 2.1.
+ *   r2o_cost_right      matching cost with the right image as reference, for the exact
+ *                       consistency check (Sec. 3.2.3): C^R(x,y,d) = Hamming distance between
+ *                       CT_R(x,y) and CT_L(x+d,y); 255 when x + d > W - 1.
+ *   r2o_sgm             the whole chain above, in the order of Sec. 2.1. With flag 4 (exact
+ *                       check) D^R is the WTA of the right-reference volume aggregated from C^R
+ *                       over the same paths, instead of Eq. (right_disparity). The paper gets it
+ *                       by swapping and mirroring the pair and matching again; since mirroring
+ *                       maps the path set onto itself and permutes both descriptors' bits alike,
+ *                       that is the same map (a pin checks the two against each other).
  *   r2o_subpixel        sub-pixel refinement, Sec. 2.1.3 ("Subpixel disparity refinement"): the
  *                       parabola through the aggregated costs at D^L(p) - 1, D^L(p), D^L(p) + 1,
  *                       fitted by solving its 3 x 3 system in fp64; D^L(p) moves to the abscissa
@@ -142,6 +150,22 @@ int r2o_path(const uint8_t* cost, int W, int H, int D, int dx, int dy, int P1, i
   return 0;
 }
 
+/* Matching cost with the right image as reference (exact consistency check, Sec. 3.2.3):
+ * C^R(x,y,d) = Hamming distance between CT_R(x,y) and CT_L(x+d,y); 255 when x + d > W - 1. */
+int r2o_cost_right(const uint64_t* ctl, const uint64_t* ctr, int W, int H, int D, uint8_t* cost) {
+  if (!ctl || !ctr || !cost || W < 1 || H < 1 || D < 1) return -1;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++)
+      for (int d = 0; d < D; d++) {
+        int64_t p = ((int64_t)y * W + x) * D + d;
+        if (x + d > W - 1)
+          cost[p] = 255;
+        else
+          cost[p] = (uint8_t)popcount64(ctr[(int64_t)y * W + x] ^ ctl[(int64_t)y * W + x + d]);
+      }
+  return 0;
+}
+
 /* Aggregated volume S(p,d) = min(65535, sum_r L_r(p,d)) over the first R directions (R = 4 or 8). */
 int r2o_aggregate(const uint8_t* cost, int W, int H, int D, int R, int P1, int P2, uint16_t* S) {
   if (!cost || !S || (R != 4 && R != 8) || W < 1 || H < 1 || D < 1 || D > 256) return -1;
@@ -250,7 +274,25 @@ int r2o_median3x3(const uint16_t* Din, int W, int H, uint16_t* Dout) {
   return 0;
 }
 
-/* Whole pipeline (Sec. 2.1). flags: bit 0 = left-right check, bit 1 = median.
+/* Exact right disparity map (Sec. 3.2.3): WTA of the volume aggregated from C^R. */
+static int r2o_exact_right(const uint64_t* ctl, const uint64_t* ctr, int W, int H, int D, int R,
+                           int P1, int P2, uint16_t* DR) {
+  int64_t nde = (int64_t)W * H * D;
+  uint8_t* cost = (uint8_t*)malloc((size_t)nde);
+  uint16_t* S = (uint16_t*)malloc((size_t)nde * 2);
+  int rc = -1;
+  if (cost && S) {
+    rc = r2o_cost_right(ctl, ctr, W, H, D, cost);
+    if (!rc) rc = r2o_aggregate(cost, W, H, D, R, P1, P2, S);
+    if (!rc) rc = r2o_wta(S, W, H, D, DR);
+  }
+  free(cost);
+  free(S);
+  return rc;
+}
+
+/* Whole pipeline (Sec. 2.1). flags: bit 0 = left-right check, bit 1 = median, bit 2 = exact D^R
+ * (Sec. 3.2.3).
  * The optional outputs (may be NULL): cost [H][W][D] uint8, S [H][W][D] uint16, D^L, D^R,
  * the left-right mask. disp receives the final map. */
 int r2o_sgm(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int H, int D,
@@ -274,7 +316,8 @@ int r2o_sgm(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int
     if (!rc) rc = r2o_cost(ctl, ctr, W, H, D, cost);
     if (!rc) rc = r2o_aggregate(cost, W, H, D, R, P1, P2, S);
     if (!rc) rc = r2o_wta(S, W, H, D, DL);
-    if (!rc) rc = r2o_right_disparity(S, W, H, D, DR);
+    if (!rc) rc = (flags & 4) ? r2o_exact_right(ctl, ctr, W, H, D, R, P1, P2, DR)
+                              : r2o_right_disparity(S, W, H, D, DR);
     if (!rc) {
       if (flags & 1) {
         rc = r2o_lr_check(DL, DR, W, H, lr_threshold, Dlr, mask);
@@ -422,7 +465,8 @@ int r2o_sgm_subpixel(const uint8_t* left, const uint8_t* right, int64_t pitch, i
     if (!rc) rc = r2o_cost(ctl, ctr, W, H, D, cost);
     if (!rc) rc = r2o_aggregate(cost, W, H, D, R, P1, P2, S);
     if (!rc) rc = r2o_wta(S, W, H, D, DL);
-    if (!rc) rc = r2o_right_disparity(S, W, H, D, DR);
+    if (!rc) rc = (flags & 4) ? r2o_exact_right(ctl, ctr, W, H, D, R, P1, P2, DR)
+                              : r2o_right_disparity(S, W, H, D, DR);
     if (!rc) rc = r2o_subpixel(S, DL, W, H, D, ref);
     if (!rc) {
       if (flags & 1) {

@@ -43,7 +43,8 @@ const char* params_error(const res2tac_params* p) {
     return "census window must be 5x5 or 9x7";
   if (p->p1 < 0 || p->p2 < p->p1 || p->p2 > 16384) return "need 0 <= p1 <= p2 <= 16384";
   if (p->num_paths != 4 && p->num_paths != 8) return "num_paths must be 4 or 8";
-  if (p->flags & ~(RES2TAC_LR_CHECK | RES2TAC_MEDIAN)) return "unknown flag bits";
+  if (p->flags & ~(RES2TAC_LR_CHECK | RES2TAC_MEDIAN | RES2TAC_EXACT_CC))
+    return "unknown flag bits";
   if (p->lr_threshold < 0 || p->lr_threshold > 255) return "lr_threshold must be in 0..255";
   return nullptr;
 }
@@ -86,7 +87,7 @@ struct res2tac_ctx {
   int last_launches;
   r2t::BatchEngine* batch;
   int profiling;
-  cudaEvent_t ev[5];  // stage boundaries of the last profiled compute
+  cudaEvent_t ev[8];  // stage boundaries of the last profiled compute (8 with the exact check)
   r2t::Fork fork;     // second stream for the concurrent aggregation kernels
 };
 
@@ -108,8 +109,9 @@ const char* res2tac_last_error(void) { return g_err; }
 size_t res2tac_workspace_bytes(const res2tac_params* p) {
   if (params_error(p)) return 0;
   const size_t npx = (size_t)p->width * p->height;
-  return layout_for(p->width, p->height, p->max_disp, needs_wide(p)).total + npx * 2 + npx * 2 +
-         1024;
+  return layout_for(p->width, p->height, p->max_disp, needs_wide(p),
+                    (p->flags & RES2TAC_EXACT_CC) != 0).total +
+         npx * 2 + npx * 2 + 1024;
 }
 
 int res2tac_create(const res2tac_params* p, res2tac_t* out) {
@@ -127,7 +129,8 @@ int res2tac_create(const res2tac_params* p, res2tac_t* out) {
     delete h;
     return fail_cuda(e, "cudaGetDevice");
   }
-  h->lay = layout_for(p->width, p->height, p->max_disp, h->method.wide != 0);
+  h->lay = layout_for(p->width, p->height, p->max_disp, h->method.wide != 0,
+                      (p->flags & RES2TAC_EXACT_CC) != 0);
   const size_t npx = (size_t)p->width * p->height;
   e = cudaMalloc(&h->scratch, h->lay.total);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_in, align_up(npx * 2, 256));
@@ -149,7 +152,7 @@ void res2tac_destroy(res2tac_t h) {
   if (cur != h->device) cudaSetDevice(h->device);
   r2t::batch_destroy(h->batch);
   r2t::fork_destroy(&h->fork);
-  for (int i = 0; i < 5; i++)
+  for (int i = 0; i < 8; i++)
     if (h->ev[i]) cudaEventDestroy(h->ev[i]);
   cudaFree(h->scratch);
   cudaFree(h->stage_in);
@@ -351,7 +354,7 @@ int res2tac_last_launch_count(res2tac_t h) { return h ? h->last_launches : 0; }
 int res2tac_set_profiling(res2tac_t h, int enable) {
   if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
   if (enable && !h->ev[0]) {
-    for (int i = 0; i < 5; i++) {
+    for (int i = 0; i < 8; i++) {
       cudaError_t e = cudaEventCreate(&h->ev[i]);
       if (e != cudaSuccess) return fail_cuda(e, "cudaEventCreate");
     }
@@ -363,13 +366,22 @@ int res2tac_set_profiling(res2tac_t h, int enable) {
 int res2tac_stage_times(res2tac_t h, float* ms, int n) {
   if (!h || !ms || n < 0) return fail(RES2TAC_EINVAL, "NULL argument");
   if (!h->profiling || !h->ev[0]) return fail(RES2TAC_EINVAL, "profiling is not enabled");
-  cudaError_t e = cudaEventSynchronize(h->ev[4]);
+  const bool exact = (h->method.flags & RES2TAC_EXACT_CC) != 0;
+  cudaError_t e = cudaEventSynchronize(h->ev[exact ? 7 : 4]);
   if (e != cudaSuccess) return fail_cuda(e, "cudaEventSynchronize");
+  // event intervals of each stage; with the exact check a stage runs once per pass (the flip
+  // counts to the first cost stage)
+  static const int kPlain[4][4] = {{0, 1, -1, -1}, {1, 2, -1, -1}, {2, 3, -1, -1}, {3, 4, -1, -1}};
+  static const int kExact[4][4] = {{0, 1, 3, 4}, {1, 2, 4, 5}, {2, 3, 5, 6}, {6, 7, -1, -1}};
+  const int(*iv)[4] = exact ? kExact : kPlain;
   for (int i = 0; i < n && i < 4; i++) {
-    float t = 0;
-    e = cudaEventElapsedTime(&t, h->ev[i], h->ev[i + 1]);
-    if (e != cudaSuccess) return fail_cuda(e, "cudaEventElapsedTime");
-    ms[i] = t;
+    ms[i] = 0;
+    for (int k = 0; k < 4 && iv[i][k] >= 0; k += 2) {
+      float t = 0;
+      e = cudaEventElapsedTime(&t, h->ev[iv[i][k]], h->ev[iv[i][k + 1]]);
+      if (e != cudaSuccess) return fail_cuda(e, "cudaEventElapsedTime");
+      ms[i] += t;
+    }
   }
   return RES2TAC_OK;
 }
@@ -411,6 +423,8 @@ int res2tac_batch_reserve(res2tac_t h, size_t scratch_bytes, int32_t max_pairs) 
 int res2tac_compute_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res2tac_stream_t s) {
   if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
   if (!pairs || n < 1) return fail(RES2TAC_EINVAL, "empty batch");
+  if (h->method.flags & RES2TAC_EXACT_CC)
+    return fail(RES2TAC_EINVAL, "the exact consistency check runs per pair (res2tac_compute)");
   std::vector<r2t::Problem> probs((size_t)n);
   std::vector<size_t> offs((size_t)n);
   size_t total = 0;

@@ -34,6 +34,8 @@ struct Problem {
   uint32_t* kr;       // [H][W] right-disparity keys S << 8 | d, reduced with atomicMin
   uint8_t* mask;      // [H][W] 1 = kept by the left-right check
   float* disp_f;      // sub-pixel final map (caller's, out_pitch bytes per row); NULL: uint16 map
+  uint8_t* flip;      // [2][H][W] right and left image, each flipped horizontally (exact check)
+  uint16_t* dp;       // [H][W] D^L of that swapped, flipped pair (exact check); NULL: approximate
 };
 
 // Method parameters shared by every pair of a call.
@@ -41,7 +43,7 @@ struct Method {
   int cw, ch;       // census window
   int P1, P2;
   int num_paths;    // 4 or 8
-  int flags;        // 1 = LR check, 2 = median
+  int flags;        // 1 = LR check, 2 = median, 4 = exact D^R for the check
   int lr_threshold;
   int wide;         // aggregated sums kept in uint32 (needed when 8 (255 + P2) > 65535)
 };

@@ -1,4 +1,6 @@
 // Plain single-pair launches of the SGM stages (one kernel per stage, all on the caller's stream).
+#include <algorithm>
+
 #include "aggregate.cuh"
 #include "census_cost.cuh"
 #include "launch.h"
@@ -114,18 +116,16 @@ static cudaError_t launch_aggregate(const Problem& pb, const Method& mt, const T
   return cudaGetLastError();
 }
 
-cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
-                         int* launches, cudaEvent_t* ev, const Fork* fork) {
-  int n = 0;
+// Census + cost, aggregation and WTA (with the right-disparity keys) of the pair pb.left /
+// pb.right into pb.dl: 4 launches. ev: NULL, or 3 events recorded after each of the 3 stages.
+static cudaError_t run_pass(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
+                            cudaEvent_t* ev, const Fork* fork) {
   cudaError_t e;
-  if (ev) cudaEventRecord(ev[0], s);
   cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
-  n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[1], s);
+  if (ev) cudaEventRecord(ev[0], s);
   if ((e = launch_aggregate(pb, mt, tn, s, fork)) != cudaSuccess) return e;
-  n += 2;
-  if (ev) cudaEventRecord(ev[2], s);
+  if (ev) cudaEventRecord(ev[1], s);
   const int T = tn.wta_chunk;  // pixels per block of 256 threads
   const size_t smem = wta_smem_bytes(pb.D, T);
   const int nw = wta_items(pb.W, pb.H, T);
@@ -133,9 +133,52 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
     wta_dr_kernel<true><<<nw, 256, smem, s>>>(pb, T);
   else
     wta_dr_kernel<false><<<nw, 256, smem, s>>>(pb, T);
-  n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[3], s);
+  if (ev) cudaEventRecord(ev[2], s);
+  return cudaSuccess;
+}
+
+// The swapped, horizontally flipped pair of the exact consistency check (Sec. 3.2.3): the new
+// reference is the right image mirrored, the new matching image the left one mirrored.
+__global__ void flip_pair_kernel(Problem pb) {
+  const int W = pb.W;
+  const int64_t n = (int64_t)W * pb.H;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = i / W;
+    const int x = (int)(i - y * W);
+    const int64_t src = y * pb.in_pitch + (W - 1 - x);
+    pb.flip[i] = pb.right[src];
+    pb.flip[n + i] = pb.left[src];
+  }
+}
+
+cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
+                         int* launches, cudaEvent_t* ev, const Fork* fork) {
+  const bool exact = (mt.flags & 4) != 0;
+  if (exact && (!pb.flip || !pb.dp)) return cudaErrorInvalidValue;
+  int n = 0;
+  cudaError_t e;
+  if (ev) cudaEventRecord(ev[0], s);
+  if (exact) {
+    // D^R from scratch: the whole matching of the swapped, flipped pair; its D^L read mirrored
+    // is D^R of the original pair
+    const int64_t npx = (int64_t)pb.W * pb.H;
+    const int grid = (int)std::min<int64_t>((npx + 255) / 256, 1216);
+    flip_pair_kernel<<<grid, 256, 0, s>>>(pb);
+    n++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    Problem pf = pb;
+    pf.left = pb.flip;
+    pf.right = pb.flip + npx;
+    pf.in_pitch = pb.W;
+    pf.dl = pb.dp;
+    if ((e = run_pass(pf, mt, tn, s, ev ? ev + 1 : nullptr, fork)) != cudaSuccess) return e;
+    n += 4;
+  }
+  if ((e = run_pass(pb, mt, tn, s, ev ? ev + (exact ? 4 : 1) : nullptr, fork)) != cudaSuccess)
+    return e;
+  n += 4;
   const int nm = median_items(pb.W, pb.H);
   if (pb.disp_f == nullptr)  // uint16 map
     lr_median_kernel<false, false><<<nm, 256, 0, s>>>(pb, mt);
@@ -145,7 +188,7 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
     lr_median_kernel<true, false><<<nm, 256, 0, s>>>(pb, mt);
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[4], s);
+  if (ev) cudaEventRecord(ev[exact ? 7 : 4], s);
   if (launches) *launches = n;
   return cudaSuccess;
 }

@@ -47,8 +47,12 @@ const void* batch_shear_kernel_fn();
 
 // Plain single-pair pipeline: 5 kernel launches on stream s (census + cost + clearing of the
 // aggregated volume; two aggregation kernels; WTA + right-disparity keys; LR check + median).
+// With the exact check (mt.flags & 4; pb.flip and pb.dp set) first a flip kernel and the first
+// four launches again on the swapped, flipped pair: 10 launches.
 // Returns the number of launches through *launches.
-// ev: NULL, or 5 events recorded around the four stages (before the cost stage, after each).
+// ev: NULL, or events recorded around the stages: 5 (before the cost stage, after each of the
+// four), with the exact check 8 (before the flip; after the cost, aggregation and WTA of each
+// pass; after the LR check + median).
 // fork: NULL runs the two aggregation kernels one after the other on s.
 cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
                          int* launches, cudaEvent_t* ev = nullptr, const Fork* fork = nullptr);

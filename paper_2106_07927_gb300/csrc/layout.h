@@ -8,14 +8,15 @@
 namespace r2t {
 
 struct Layout {
-  size_t cost, agg, dl, dr, kr, mask, total;
+  size_t cost, agg, dl, dr, kr, mask, flip, dp, total;  // flip, dp: 0 without the exact check
 };
 
 inline size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Cost 1 B/DE, aggregated volume 2 B/DE (4 when wide), D^L and D^R 2 B/px each,
-// right-disparity keys 4 B/px, LR mask 1 B/px: 3 B per DE + 9 B per pixel.
-inline Layout layout_for(int W, int H, int D, bool wide) {
+// right-disparity keys 4 B/px, LR mask 1 B/px: 3 B per DE + 9 B per pixel. The exact
+// consistency check adds the swapped, flipped pair (2 B/px) and its D^L (2 B/px).
+inline Layout layout_for(int W, int H, int D, bool wide, bool exact = false) {
   const size_t npx = (size_t)W * H, nde = npx * D;
   Layout l;
   size_t o = 0;
@@ -25,6 +26,11 @@ inline Layout layout_for(int W, int H, int D, bool wide) {
   l.dr = o; o = align256(o + npx * 2);
   l.kr = o; o = align256(o + npx * 4);
   l.mask = o; o = align256(o + npx);
+  l.flip = l.dp = 0;
+  if (exact) {
+    l.flip = o; o = align256(o + npx * 2);
+    l.dp = o; o = align256(o + npx * 2);
+  }
   l.total = o;
   return l;
 }
@@ -42,6 +48,8 @@ inline Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
   pb.kr = reinterpret_cast<uint32_t*>(base + l.kr);
   pb.mask = reinterpret_cast<uint8_t*>(base + l.mask);
   pb.disp_f = nullptr;
+  pb.flip = l.flip ? reinterpret_cast<uint8_t*>(base + l.flip) : nullptr;
+  pb.dp = l.dp ? reinterpret_cast<uint16_t*>(base + l.dp) : nullptr;
   return pb;
 }
 

@@ -210,7 +210,9 @@ __device__ __forceinline__ uint32_t checked_disp(const Problem& pb, const Method
   const int dl = pb.dl[row + x];
   if (mt.flags & 1) {
     if (x - dl < 0) return inv;
-    const int dr = (int)(pb.kr[row + x - dl] & 0xFFu);
+    // exact check: D^R(x') = D^L of the swapped, flipped pair at W - 1 - x'
+    const int dr =
+        pb.dp ? (int)pb.dp[row + pb.W - 1 - (x - dl)] : (int)(pb.kr[row + x - dl] & 0xFFu);
     const int diff = dl - dr;
     if ((diff < 0 ? -diff : diff) > mt.lr_threshold) return inv;
   }
@@ -261,7 +263,7 @@ __device__ __forceinline__ void lr_median_tile(const Problem& pb, const Method& 
       out = checked_disp<SUB, WIDE>(pb, mt, x, y);
       pb.mask[p] = out != inv ? 1 : 0;
     }
-    pb.dr[p] = (uint16_t)(pb.kr[p] & 0xFFu);
+    pb.dr[p] = pb.dp ? pb.dp[(int64_t)y * W + W - 1 - x] : (uint16_t)(pb.kr[p] & 0xFFu);
     if (SUB)
       *reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(pb.disp_f) +
                                    (int64_t)y * pb.out_pitch + 4 * (int64_t)x) = out;

@@ -170,3 +170,56 @@ def test_invalid_pointers_and_pitch_rejected():
     with pytest.raises(binding.Res2tacError):
         binding.res2tac_compute(st.handle, x.data_ptr(), x.data_ptr(), 64, out.data_ptr(), 127, 0)
     st.close()
+
+
+# ------------------------------------------------------- exact consistency check (Sec. 3.2.3)
+EXACT = scenes.FLAG_LR_CHECK | 4
+
+
+@pytest.mark.parametrize("name", list(scenes.SINGLE))
+def test_exact_check_full_size_workloads(name):
+    left, right, _, prm = scenes.single_pair(name, 0)
+    prm = dict(prm, flags=prm["flags"] | EXACT)
+    _assert_same(left, right, prm)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_exact_check_tiny_random_shapes(seed):
+    rng = np.random.default_rng(500 + seed)
+    W = int(rng.integers(1, 70))
+    H = int(rng.integers(1, 40))
+    D = int(rng.choice([16, 32, 64, 128, 256]))
+    cw, ch = ((5, 5), (9, 7))[seed % 2]
+    R = (4, 8)[(seed // 2) % 2]
+    left = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    right = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    prm = scenes.params(W, H, D, cw, ch, 10, 120, R, EXACT | (seed % 2) * 2, seed % 3)
+    _assert_same(left, right, prm)
+
+
+def test_exact_check_saturated_sums_padded_pitches():
+    rng = np.random.default_rng(6)
+    W, H, D = 150, 90, 128
+    left = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    right = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    _assert_same(left, right, scenes.params(W, H, D, 5, 5, 100, 16384, 8, EXACT | 2), in_pad=9,
+                 out_pad=3)
+
+
+def test_exact_check_launches_stages_and_batch_rejection():
+    import torch
+    left, right, _, prm = scenes.single_pair("320x240_d64_ct5x5_r4", 0)
+    prm = dict(prm, flags=EXACT | 2)
+    st = binding.Stereo(prm)
+    binding.res2tac_set_profiling(st.handle, True)
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    st.compute(L, R)
+    times = binding.res2tac_stage_times(st.handle)
+    assert binding.res2tac_last_launch_count(st.handle) == 10
+    assert all(v > 0 for v in times.values())
+    o = torch.empty_like(L, dtype=torch.int16)
+    pair = binding.res2tac_pair(L.data_ptr(), R.data_ptr(), L.shape[1], o.data_ptr(),
+                                2 * L.shape[1], L.shape[1], L.shape[0], prm["max_disp"], 0)
+    with pytest.raises(binding.Res2tacError):
+        binding.res2tac_compute_batch(st.handle, [pair], 0)
+    st.close()

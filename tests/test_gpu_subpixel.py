@@ -43,7 +43,7 @@ def _check(left, right, prm, **kw):
     want, want_ref = oracle.sgm_subpixel(left, right, prm["max_disp"], prm["census_w"],
                                          prm["census_h"], prm["p1"], prm["p2"], prm["num_paths"],
                                          prm["flags"], prm["lr_threshold"])
-    assert launches == 5
+    assert launches == (10 if prm["flags"] & 4 else 5)
     err = np.abs(ref - want_ref)
     assert err.max() <= TOL, f"refined D^L: max error {err.max()} at {np.argmax(err)}"
     inv = np.isinf(want)
@@ -96,6 +96,11 @@ def test_subpixel_saturated_sums_and_padded_output():
     left = rng.integers(0, 256, (H, W)).astype(np.uint8)
     right = rng.integers(0, 256, (H, W)).astype(np.uint8)
     _check(left, right, scenes.params(W, H, D, 5, 5, 100, 16384, 8, 3), out_pad=5)
+
+
+def test_subpixel_with_exact_check():
+    left, right, _ = scenes.make_scene("road", 21, 240, 96, 128)
+    _check(left, right, scenes.params(240, 96, 128, 9, 7, 10, 120, 8, 3 | 4))
 
 
 def test_subpixel_invalid_pitch_and_alignment_rejected():

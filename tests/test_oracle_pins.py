@@ -414,3 +414,42 @@ def test_sgm_subpixel_within_half_pixel_of_integer_pipeline(flags):
     _, dbg = oracle.sgm(L, R, D, 5, 5, 10, 120, 4, flags, debug=True)
     assert np.all(np.abs(ref - dbg["dl"]) <= 0.5)
     assert np.array_equal(ref, oracle.subpixel(dbg["agg"], dbg["dl"]))
+
+
+# ------------------------------------------------------- exact consistency check (Sec. 3.2.3)
+@pytest.mark.parametrize("cw,ch,R,seed", [(5, 5, 4, 0), (9, 7, 8, 1), (9, 7, 4, 2)])
+def test_exact_right_disparity_equals_swap_and_flip(cw, ch, R, seed):
+    # The paper builds the exact D^R by swapping the images, mirroring both and matching again.
+    # The oracle computes it from the right-reference cost directly; the two must agree.
+    rng = np.random.default_rng(40 + seed)
+    H, W, D = 23, 57, 32
+    L = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    R_img = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    flags = oracle.FLAG_LR_CHECK | oracle.FLAG_EXACT_CC
+    _, dbg = oracle.sgm(L, R_img, D, cw, ch, 10, 120, R, flags, debug=True)
+    dflip = oracle.sgm(R_img[:, ::-1], L[:, ::-1], D, cw, ch, 10, 120, R, 0)
+    assert np.array_equal(dbg["dr"], dflip[:, ::-1])
+    # and the cost it starts from is the definition: CT_R(x) against CT_L(x + d), 255 outside
+    ctl, ctr = oracle.census(L, cw, ch), oracle.census(R_img, cw, ch)
+    cr = oracle.cost_right(ctl, ctr, D)
+    x, d = 11, 5
+    assert cr[3, x, d] == bin(int(ctr[3, x]) ^ int(ctl[3, x + d])).count("1")
+    assert np.all(cr[:, W - 1, 1:] == 255) and np.all(cr[:, W - D:, :][:, :, -1][:, 1:] == 255)
+
+
+@pytest.mark.parametrize("cw,ch,R", [(5, 5, 4), (9, 7, 8)])
+def test_exact_check_keeps_constant_shift_to_the_border(cw, ch, R):
+    # R(x) = L(x + s): the exact D^R is s wherever x + s stays inside and the window sees the
+    # same texture, so the check keeps D^L = s from x = s + rx on, where the approximate D^R of
+    # Eq. (right_disparity) is still biased (see the test above it)
+    rng = np.random.default_rng(11)
+    W, H, D, s = 96, 40, 32, 7
+    from paper_2106_07927_gb300 import scenes
+    L = scenes._to_u8(scenes._blur(rng.random((H, W)), 1.0))
+    R_img = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    R_img[:, :W - s] = L[:, s:]
+    flags = oracle.FLAG_LR_CHECK | oracle.FLAG_EXACT_CC
+    disp, dbg = oracle.sgm(L, R_img, D, cw, ch, 10, 120, R, flags, debug=True)
+    rx = cw // 2
+    assert np.all(dbg["dr"][:, rx:W - D] == s)
+    assert np.all(disp[:, s + rx:W - D] == s)

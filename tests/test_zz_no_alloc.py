@@ -57,6 +57,17 @@ def test_static_entry_matches_context_entry_on_two_calls_in_a_row():
     assert np.array_equal(binding.u16(got3), expected[0])
 
 
+def test_static_entry_exact_check_matches_context_entry():
+    import torch
+    left, right, _ = scenes.make_scene("nadir", 4, 180, 120, 64)
+    prm = scenes.params(180, 120, 64, 9, 7, 10, 120, 8,
+                        scenes.FLAG_LR_CHECK | scenes.FLAG_MEDIAN | binding.RES2TAC_EXACT_CC)
+    expected = _with_context(left, right, prm)
+    got = _static_call(left, right, prm)
+    torch.cuda.synchronize()
+    assert np.array_equal(binding.u16(got), expected)
+
+
 def test_static_entry_rejects_a_problem_larger_than_its_array():
     import torch
     prm = scenes.params(1242, 375, 128, 9, 7, 10, 120, 8, 3)  # needs about 190 MB
