@@ -26,6 +26,7 @@ INVALID = 0xFFFF
 FLAG_LR_CHECK = 1
 FLAG_MEDIAN = 2
 FLAG_EXACT_CC = 4
+FLAG_NCC = 8
 
 
 def build(force: bool = False) -> str:
@@ -60,12 +61,14 @@ def _load():
         lib.r2o_sgm.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, P, P, P, P, P, P]
         lib.r2o_subpixel.argtypes = [P, P, I, I, I, P]
         lib.r2o_cost_right.argtypes = [P, P, I, I, I, P]
+        lib.r2o_ncc_cost.argtypes = [P, P, I64, I, I, I, I, P]
+        lib.r2o_ncc_cost_right.argtypes = [P, P, I64, I, I, I, I, P]
         lib.r2o_median3x3_f64.argtypes = [P, I, I, P]
         lib.r2o_sgm_subpixel.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, P, P]
         for f in (lib.r2o_census, lib.r2o_cost, lib.r2o_path, lib.r2o_aggregate, lib.r2o_wta,
                   lib.r2o_right_disparity, lib.r2o_lr_check, lib.r2o_median3x3, lib.r2o_sgm,
                   lib.r2o_subpixel, lib.r2o_median3x3_f64, lib.r2o_sgm_subpixel,
-                  lib.r2o_cost_right):
+                  lib.r2o_cost_right, lib.r2o_ncc_cost, lib.r2o_ncc_cost_right):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -104,6 +107,19 @@ def cost_right(ctl: np.ndarray, ctr: np.ndarray, D: int) -> np.ndarray:
     H, W = ctl.shape
     out = np.empty((H, W, D), np.uint8)
     _check(_load().r2o_cost_right(_ptr(ctl), _ptr(ctr), W, H, D, _ptr(out)), "cost_right")
+    return out
+
+
+def ncc_cost(left: np.ndarray, right: np.ndarray, D: int, n: int,
+             right_reference: bool = False) -> np.ndarray:
+    """Inverted, truncated NCC cost on 0..255 over n x n patches (left image as reference, or
+    the right one for the exact consistency check)."""
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    right = np.ascontiguousarray(right, dtype=np.uint8)
+    H, W = left.shape
+    out = np.empty((H, W, D), np.uint8)
+    f = _load().r2o_ncc_cost_right if right_reference else _load().r2o_ncc_cost
+    _check(f(_ptr(left), _ptr(right), W, W, H, D, n, _ptr(out)), "ncc_cost")
     return out
 
 

@@ -27,6 +27,11 @@
  *   r2o_cost_right      matching cost with the right image as reference, for the exact
  *                       consistency check (Sec. 3.2.3): C^R(x,y,d) = Hamming distance between
  *                       CT_R(x,y) and CT_L(x+d,y); 255 when x + d > W - 1.
+ *   r2o_ncc_cost        the second matching cost, Sec. 2.1.1 and Sec. 2.2.1 ("Inverted and
+ *                       truncated version of the normalized cross-correlation"):
+ *                       s = 1 - max(0, Phi) with Phi the zero-mean NCC of the n x n patches
+ *                       around (x, y) in the reference and (x -/+ d, y) in the matching image
+ *                       (zero margin as for the census), scaled to 0..255 (see the function).
  *   r2o_sgm             the whole chain above, in the order of Sec. 2.1. With flag 4 (exact
  *                       check) D^R is the WTA of the right-reference volume aggregated from C^R
  *                       over the same paths, instead of Eq. (right_disparity). The paper gets it
@@ -166,6 +171,75 @@ int r2o_cost_right(const uint64_t* ctl, const uint64_t* ctr, int W, int H, int D
   return 0;
 }
 
+/* Pixel of an image with the zero-valued margin. */
+static int px_or_zero(const uint8_t* img, int64_t pitch, int W, int H, int x, int y) {
+  if (x < 0 || x >= W || y < 0 || y >= H) return 0;
+  return img[(int64_t)y * pitch + x];
+}
+
+/* Inverted, truncated NCC cost of one patch pair: reference patch centred at (xa, y) of A,
+ * matching patch centred at (xb, y) of B, n x n, N = n^2 pixels, zero margin.
+ *   sA = sum a, sB = sum b, sAA = sum a^2, sBB = sum b^2, sAB = sum a b   (exact integers)
+ *   vA = N sAA - sA^2,  vB = N sBB - sB^2,  cov = N sAB - sA sB           (N^2 (co)variances)
+ *   Phi = cov / sqrt(vA vB), taken as 0 when vA or vB is 0 (a constant patch);
+ *   cost = 255 - clamp(round(255 max(0, Phi)), 0, 255), the truncated 1 - max(0, Phi) on 0..255.
+ * The scaling to an 8-bit cost decides an integer in floating point, so it follows one fixed
+ * sequence of correctly rounded fp32 operations (the precision of the GPU path):
+ *   iA = 1 / sqrt(float(vA)) (0 when vA = 0), iB likewise,
+ *   q = ((float(cov) * iA) * iB) * 255,  cost = 255 - clamp(rint(q), 0, 255)  (rint: ties to even).
+ * A cov <= 0 gives q <= 0 and so 255 (the max(0, .) truncation). */
+static uint8_t ncc_pair_cost(const uint8_t* A, const uint8_t* B, int64_t pitch, int W, int H,
+                             int xa, int xb, int y, int n) {
+  int r = n / 2, N = n * n;
+  int64_t sA = 0, sB = 0, sAA = 0, sBB = 0, sAB = 0;
+  for (int j = -r; j <= r; j++)
+    for (int i = -r; i <= r; i++) {
+      int a = px_or_zero(A, pitch, W, H, xa + i, y + j);
+      int b = px_or_zero(B, pitch, W, H, xb + i, y + j);
+      sA += a;
+      sB += b;
+      sAA += a * a;
+      sBB += b * b;
+      sAB += a * b;
+    }
+  int64_t vA = N * sAA - sA * sA, vB = N * sBB - sB * sB, cov = N * sAB - sA * sB;
+  volatile float iA = vA > 0 ? 1.0f / sqrtf((float)vA) : 0.0f;
+  volatile float iB = vB > 0 ? 1.0f / sqrtf((float)vB) : 0.0f;
+  volatile float q = (float)cov * iA;
+  q = q * iB;
+  q = q * 255.0f;
+  float k = rintf(q);
+  if (k < 0.0f) k = 0.0f;
+  if (k > 255.0f) k = 255.0f;
+  return (uint8_t)(255 - (int)k);
+}
+
+/* NCC cost volume with the left image as reference: C(x,y,d) = ncc_pair_cost(left patch at x,
+ * right patch at x - d); 255 when x - d < 0. n = 5 or 9. */
+int r2o_ncc_cost(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int H, int D,
+                 int n, uint8_t* cost) {
+  if (!left || !right || !cost || W < 1 || H < 1 || D < 1 || n < 1 || !(n & 1)) return -1;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++)
+      for (int d = 0; d < D; d++)
+        cost[((int64_t)y * W + x) * D + d] =
+            x - d < 0 ? 255 : ncc_pair_cost(left, right, pitch, W, H, x, x - d, y, n);
+  return 0;
+}
+
+/* NCC cost volume with the right image as reference (exact consistency check):
+ * C^R(x,y,d) = ncc_pair_cost(right patch at x, left patch at x + d); 255 when x + d > W - 1. */
+int r2o_ncc_cost_right(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int H,
+                       int D, int n, uint8_t* cost) {
+  if (!left || !right || !cost || W < 1 || H < 1 || D < 1 || n < 1 || !(n & 1)) return -1;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++)
+      for (int d = 0; d < D; d++)
+        cost[((int64_t)y * W + x) * D + d] =
+            x + d > W - 1 ? 255 : ncc_pair_cost(right, left, pitch, W, H, x, x + d, y, n);
+  return 0;
+}
+
 /* Aggregated volume S(p,d) = min(65535, sum_r L_r(p,d)) over the first R directions (R = 4 or 8). */
 int r2o_aggregate(const uint8_t* cost, int W, int H, int D, int R, int P1, int P2, uint16_t* S) {
   if (!cost || !S || (R != 4 && R != 8) || W < 1 || H < 1 || D < 1 || D > 256) return -1;
@@ -274,15 +348,39 @@ int r2o_median3x3(const uint16_t* Din, int W, int H, uint16_t* Dout) {
   return 0;
 }
 
+/* Matching cost volume of the method selected by flags: bit 3 = NCC over cw x ch (= n x n),
+ * else census over cw x ch and its Hamming distance. right_ref: the right image is the reference
+ * (exact consistency check). */
+static int method_cost(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int H,
+                       int D, int cw, int ch, int flags, int right_ref, uint8_t* cost) {
+  if (flags & 8)
+    return right_ref ? r2o_ncc_cost_right(left, right, pitch, W, H, D, cw, cost)
+                     : r2o_ncc_cost(left, right, pitch, W, H, D, cw, cost);
+  int64_t npx = (int64_t)W * H;
+  uint64_t* ctl = (uint64_t*)malloc((size_t)npx * 8);
+  uint64_t* ctr = (uint64_t*)malloc((size_t)npx * 8);
+  int rc = -1;
+  if (ctl && ctr) {
+    rc = r2o_census(left, pitch, W, H, cw, ch, ctl);
+    if (!rc) rc = r2o_census(right, pitch, W, H, cw, ch, ctr);
+    if (!rc)
+      rc = right_ref ? r2o_cost_right(ctl, ctr, W, H, D, cost) : r2o_cost(ctl, ctr, W, H, D, cost);
+  }
+  free(ctl);
+  free(ctr);
+  return rc;
+}
+
 /* Exact right disparity map (Sec. 3.2.3): WTA of the volume aggregated from C^R. */
-static int r2o_exact_right(const uint64_t* ctl, const uint64_t* ctr, int W, int H, int D, int R,
-                           int P1, int P2, uint16_t* DR) {
+static int r2o_exact_right(const uint8_t* left, const uint8_t* right, int64_t pitch, int W,
+                           int H, int D, int cw, int ch, int P1, int P2, int R, int flags,
+                           uint16_t* DR) {
   int64_t nde = (int64_t)W * H * D;
   uint8_t* cost = (uint8_t*)malloc((size_t)nde);
   uint16_t* S = (uint16_t*)malloc((size_t)nde * 2);
   int rc = -1;
   if (cost && S) {
-    rc = r2o_cost_right(ctl, ctr, W, H, D, cost);
+    rc = method_cost(left, right, pitch, W, H, D, cw, ch, flags, 1, cost);
     if (!rc) rc = r2o_aggregate(cost, W, H, D, R, P1, P2, S);
     if (!rc) rc = r2o_wta(S, W, H, D, DR);
   }
@@ -292,7 +390,7 @@ static int r2o_exact_right(const uint64_t* ctl, const uint64_t* ctr, int W, int 
 }
 
 /* Whole pipeline (Sec. 2.1). flags: bit 0 = left-right check, bit 1 = median, bit 2 = exact D^R
- * (Sec. 3.2.3).
+ * (Sec. 3.2.3), bit 3 = NCC cost over a cw x ch (n x n) patch instead of the census.
  * The optional outputs (may be NULL): cost [H][W][D] uint8, S [H][W][D] uint16, D^L, D^R,
  * the left-right mask. disp receives the final map. */
 int r2o_sgm(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int H, int D,
@@ -301,8 +399,6 @@ int r2o_sgm(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int
             uint8_t* mask_out) {
   if (!left || !right || !disp || W < 1 || H < 1 || D < 1 || D > 256) return -1;
   int64_t npx = (int64_t)W * H, nde = npx * D;
-  uint64_t* ctl = (uint64_t*)malloc((size_t)npx * 8);
-  uint64_t* ctr = (uint64_t*)malloc((size_t)npx * 8);
   uint8_t* cost = (uint8_t*)malloc((size_t)nde);
   uint16_t* S = (uint16_t*)malloc((size_t)nde * 2);
   uint16_t* DL = (uint16_t*)malloc((size_t)npx * 2);
@@ -310,13 +406,12 @@ int r2o_sgm(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int
   uint16_t* Dlr = (uint16_t*)malloc((size_t)npx * 2);
   uint8_t* mask = (uint8_t*)malloc((size_t)npx);
   int rc = -1;
-  if (ctl && ctr && cost && S && DL && DR && Dlr && mask) {
-    rc = r2o_census(left, pitch, W, H, cw, ch, ctl);
-    if (!rc) rc = r2o_census(right, pitch, W, H, cw, ch, ctr);
-    if (!rc) rc = r2o_cost(ctl, ctr, W, H, D, cost);
+  if (cost && S && DL && DR && Dlr && mask) {
+    rc = method_cost(left, right, pitch, W, H, D, cw, ch, flags, 0, cost);
     if (!rc) rc = r2o_aggregate(cost, W, H, D, R, P1, P2, S);
     if (!rc) rc = r2o_wta(S, W, H, D, DL);
-    if (!rc) rc = (flags & 4) ? r2o_exact_right(ctl, ctr, W, H, D, R, P1, P2, DR)
+    if (!rc) rc = (flags & 4) ? r2o_exact_right(left, right, pitch, W, H, D, cw, ch, P1, P2, R,
+                                                flags, DR)
                               : r2o_right_disparity(S, W, H, D, DR);
     if (!rc) {
       if (flags & 1) {
@@ -338,8 +433,6 @@ int r2o_sgm(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int
     if (!rc && DR_out) memcpy(DR_out, DR, (size_t)npx * 2);
     if (!rc && mask_out) memcpy(mask_out, mask, (size_t)npx);
   }
-  free(ctl);
-  free(ctr);
   free(cost);
   free(S);
   free(DL);
@@ -448,8 +541,6 @@ int r2o_sgm_subpixel(const uint8_t* left, const uint8_t* right, int64_t pitch, i
                      double* disp, double* refined) {
   if (!left || !right || !disp || W < 1 || H < 1 || D < 1 || D > 256) return -1;
   int64_t npx = (int64_t)W * H, nde = npx * D;
-  uint64_t* ctl = (uint64_t*)malloc((size_t)npx * 8);
-  uint64_t* ctr = (uint64_t*)malloc((size_t)npx * 8);
   uint8_t* cost = (uint8_t*)malloc((size_t)nde);
   uint16_t* S = (uint16_t*)malloc((size_t)nde * 2);
   uint16_t* DL = (uint16_t*)malloc((size_t)npx * 2);
@@ -459,13 +550,12 @@ int r2o_sgm_subpixel(const uint8_t* left, const uint8_t* right, int64_t pitch, i
   double* ref = (double*)malloc((size_t)npx * 8);
   double* chk = (double*)malloc((size_t)npx * 8);
   int rc = -1;
-  if (ctl && ctr && cost && S && DL && DR && Dlr && mask && ref && chk) {
-    rc = r2o_census(left, pitch, W, H, cw, ch, ctl);
-    if (!rc) rc = r2o_census(right, pitch, W, H, cw, ch, ctr);
-    if (!rc) rc = r2o_cost(ctl, ctr, W, H, D, cost);
+  if (cost && S && DL && DR && Dlr && mask && ref && chk) {
+    rc = method_cost(left, right, pitch, W, H, D, cw, ch, flags, 0, cost);
     if (!rc) rc = r2o_aggregate(cost, W, H, D, R, P1, P2, S);
     if (!rc) rc = r2o_wta(S, W, H, D, DL);
-    if (!rc) rc = (flags & 4) ? r2o_exact_right(ctl, ctr, W, H, D, R, P1, P2, DR)
+    if (!rc) rc = (flags & 4) ? r2o_exact_right(left, right, pitch, W, H, D, cw, ch, P1, P2, R,
+                                                flags, DR)
                               : r2o_right_disparity(S, W, H, D, DR);
     if (!rc) rc = r2o_subpixel(S, DL, W, H, D, ref);
     if (!rc) {
@@ -484,8 +574,6 @@ int r2o_sgm_subpixel(const uint8_t* left, const uint8_t* right, int64_t pitch, i
     }
     if (!rc && refined) memcpy(refined, ref, (size_t)npx * 8);
   }
-  free(ctl);
-  free(ctr);
   free(cost);
   free(S);
   free(DL);

@@ -453,3 +453,89 @@ def test_exact_check_keeps_constant_shift_to_the_border(cw, ch, R):
     rx = cw // 2
     assert np.all(dbg["dr"][:, rx:W - D] == s)
     assert np.all(disp[:, s + rx:W - D] == s)
+
+
+# -------------------------------------------- NCC matching cost (Sec. 2.1.1, Sec. 2.2.1 "NCC")
+def _ncc_expected(L, R, x, y, d, n):
+    """255 - round(255 max(0, Phi)) with Phi from numpy's corrcoef on zero-padded patches;
+    None when 255 Phi lies within 1e-3 of a rounding boundary (fp32 may go either way)."""
+    r = n // 2
+    Lp = np.pad(L.astype(np.float64), r)
+    Rp = np.pad(R.astype(np.float64), r)
+    a = Lp[y:y + n, x:x + n].ravel()
+    b = Rp[y:y + n, x - d:x - d + n].ravel()
+    if a.std() == 0 or b.std() == 0:
+        return 255
+    phi = np.corrcoef(a, b)[0, 1]
+    v = 255 * max(0.0, phi)
+    if abs(v - np.floor(v) - 0.5) < 1e-3:
+        return None
+    return 255 - int(np.floor(v + 0.5))
+
+
+@pytest.mark.parametrize("n", [5, 9])
+def test_ncc_cost_matches_numpy_corrcoef(n):
+    rng = np.random.default_rng(70 + n)
+    H, W, D = 17, 29, 16
+    L = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    R = np.clip(L.astype(int) + rng.integers(-40, 41, (H, W)), 0, 255).astype(np.uint8)
+    R[5:9, 3:12] = 77  # a constant area: zero variance somewhere
+    C = oracle.ncc_cost(L, R, D, n)
+    checked = 0
+    for y in range(H):
+        for x in range(W):
+            for d in range(D):
+                if x - d < 0:
+                    assert C[y, x, d] == 255
+                    continue
+                want = _ncc_expected(L, R, x, y, d, n)
+                if want is not None:
+                    assert C[y, x, d] == want, (y, x, d)
+                    checked += 1
+    assert checked > 0.95 * H * W * D / 2
+
+
+@pytest.mark.parametrize("n", [5, 9])
+def test_ncc_cost_special_cases(n):
+    rng = np.random.default_rng(80 + n)
+    H, W, D, s = 24, 60, 16, 6
+    r = n // 2
+    L = rng.integers(0, 200, (H, W)).astype(np.uint8)
+    inner = (slice(r, H - r), slice(s + r, W - r))
+    # right = left shifted by s: Phi = 1 at d = s away from the borders
+    R = np.zeros_like(L)
+    R[:, :W - s] = L[:, s:]
+    C = oracle.ncc_cost(L, R, D, n)
+    assert np.all(C[:, :, s][inner][:, :W - s - 2 * r - s] == 0)
+    # a brightness offset keeps Phi = 1; an inverted image gives Phi = -1, cost 255
+    C = oracle.ncc_cost(L, (L + 40).astype(np.uint8), D, n)
+    assert np.all(C[r:H - r, r:W - r, 0] == 0)
+    C = oracle.ncc_cost(L, (255 - L).astype(np.uint8), D, n)
+    assert np.all(C[r:H - r, r:W - r, 0] == 255)
+    # a constant reference patch (window inside the image) has no variance: cost 255
+    C = oracle.ncc_cost(np.full((H, W), 9, np.uint8), L, D, n)
+    assert np.all(C[r:H - r, r:W - r] == 255)
+
+
+@pytest.mark.parametrize("n,R", [(5, 4), (9, 8)])
+def test_ncc_exact_right_equals_swap_and_flip(n, R):
+    rng = np.random.default_rng(90 + n)
+    H, W, D = 19, 41, 16
+    L = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    R_img = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    flags = oracle.FLAG_LR_CHECK | oracle.FLAG_EXACT_CC | oracle.FLAG_NCC
+    _, dbg = oracle.sgm(L, R_img, D, n, n, 90, 880, R, flags, debug=True)
+    dflip = oracle.sgm(R_img[:, ::-1], L[:, ::-1], D, n, n, 90, 880, R, oracle.FLAG_NCC)
+    assert np.array_equal(dbg["dr"], dflip[:, ::-1])
+    assert np.array_equal(dbg["cost"], oracle.ncc_cost(L, R_img, D, n))
+
+
+def test_ncc_pipeline_recovers_constant_shift():
+    rng = np.random.default_rng(13)
+    W, H, D, s = 96, 40, 32, 7
+    from paper_2106_07927_gb300 import scenes
+    L = scenes._to_u8(scenes._blur(rng.random((H, W)), 1.0))
+    R_img = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    R_img[:, :W - s] = L[:, s:]
+    _, dbg = oracle.sgm(L, R_img, D, 5, 5, 90, 880, 8, oracle.FLAG_NCC, debug=True)
+    assert np.all(dbg["dl"][:, s + 2:W - D] == s)
