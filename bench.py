@@ -266,72 +266,66 @@ def main():
             for k, v in st.items():
                 stage[k] += v
 
+        def time_variant(handle, step_fn):
+            """Mean device ms of step_fn over the timed steps (same flush and events as the
+            plain step), then the stage times of one more profiled pass."""
+            nonlocal launches
+            binding.res2tac_set_profiling(handle, False)
+            for _ in range(3):
+                flush.zero_()
+                step_fn()
+            torch.cuda.synchronize()
+            barrier()
+            for i in range(args.steps):
+                flush.zero_()
+                ev0[i].record(stream)
+                step_fn()
+                ev1[i].record(stream)
+            barrier()
+            torch.cuda.synchronize()
+            ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / args.steps)
+            launches += binding.res2tac_last_launch_count(handle) * args.steps
+            binding.res2tac_set_profiling(handle, True)
+            flush.zero_()
+            step_fn()
+            st = binding.res2tac_stage_times(handle)
+            binding.res2tac_set_profiling(handle, False)
+            return ms, {k: round(v, 4) for k, v in st.items()}
+
         # the same step with sub-pixel refinement ("fine", Sec. 2.1.3): float map out
         outf = torch.empty((H, W), dtype=torch.float32, device="cuda")
-        binding.res2tac_set_profiling(ctx.handle, False)
-
-        def step_sub():
-            binding.res2tac_compute_subpixel(ctx.handle, Ld.data_ptr(), Rd.data_ptr(), W,
-                                             outf.data_ptr(), 4 * W, sh)
-
-        for _ in range(3):
-            flush.zero_()
-            step_sub()
-        torch.cuda.synchronize()
-        barrier()
-        for i in range(args.steps):
-            flush.zero_()
-            ev0[i].record(stream)
-            step_sub()
-            ev1[i].record(stream)
-        barrier()
-        torch.cuda.synchronize()
-        sub_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / args.steps)
-        launches += binding.res2tac_last_launch_count(ctx.handle) * args.steps
+        sub_ms, sub_st = time_variant(ctx.handle, lambda: binding.res2tac_compute_subpixel(
+            ctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, outf.data_ptr(), 4 * W, sh))
         fo = outf.cpu().numpy()
         io = binding.u16(out)
         inv = io == binding.RES2TAC_INVALID
         subpixel = {
             "value": round(ws * de / (sub_ms / 1e3) / 1e6, 1), "unit": "MDE/s",
-            "ms_per_step": round(sub_ms, 4),
+            "ms_per_step": round(sub_ms, 4), "stage_ms": sub_st,
             "same_validity_as_integer_map": bool(np.array_equal(np.isinf(fo), inv)),
             "max_abs_diff_to_integer_map": float(np.abs(fo[~inv] - io[~inv]).max())
             if (~inv).any() else 0.0,
         }
 
+        def variant(flags, **over):
+            vctx = binding.Stereo(dict(prm, flags=prm["flags"] | flags, **over))
+            o = torch.empty((H, W), dtype=torch.int16, device="cuda")
+            ms, st = time_variant(vctx.handle, lambda: binding.res2tac_compute(
+                vctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, o.data_ptr(), 2 * W, sh))
+            res = binding.u16(o)
+            vctx.close()
+            return {"value": round(ws * de / (ms / 1e3) / 1e6, 1), "unit": "MDE/s",
+                    "ms_per_step": round(ms, 4), "stage_ms": st,
+                    "valid_fraction": round(float((res != binding.RES2TAC_INVALID).mean()), 4)}
+
         # exact consistency check ("exact-cc", Sec. 3.2.3): D^R from a second full matching of
         # the swapped, flipped pair
-        xprm = dict(prm, flags=prm["flags"] | binding.RES2TAC_EXACT_CC)
-        xctx = binding.Stereo(xprm)
-        outx = torch.empty((H, W), dtype=torch.int16, device="cuda")
-
-        def step_exact():
-            binding.res2tac_compute(xctx.handle, Ld.data_ptr(), Rd.data_ptr(), W,
-                                    outx.data_ptr(), 2 * W, sh)
-
-        for _ in range(3):
-            flush.zero_()
-            step_exact()
-        torch.cuda.synchronize()
-        barrier()
-        for i in range(args.steps):
-            flush.zero_()
-            ev0[i].record(stream)
-            step_exact()
-            ev1[i].record(stream)
-        barrier()
-        torch.cuda.synchronize()
-        x_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / args.steps)
-        launches += binding.res2tac_last_launch_count(xctx.handle) * args.steps
-        xo = binding.u16(outx)
-        exact_cc = {
-            "value": round(ws * de / (x_ms / 1e3) / 1e6, 1), "unit": "MDE/s",
-            "ms_per_step": round(x_ms, 4),
-            "valid_fraction": round(float((xo != binding.RES2TAC_INVALID).mean()), 4),
-            "valid_fraction_approximate_check": round(
-                float((binding.u16(out) != binding.RES2TAC_INVALID).mean()), 4),
-        }
-        xctx.close()
+        exact_cc = variant(binding.RES2TAC_EXACT_CC)
+        exact_cc["valid_fraction_approximate_check"] = round(
+            float((binding.u16(out) != binding.RES2TAC_INVALID).mean()), 4)
+        # NCC matching cost (Sec. 2.2.1), 5 x 5 and 9 x 9 patches, the paper's NCC penalties
+        ncc = {f"{n}x{n}": variant(binding.RES2TAC_NCC, census_w=n, census_h=n, p1=90, p2=880)
+               for n in (5, 9)}
 
         # end to end through the host-buffer entry point (pinned memory)
         hl = torch.from_numpy(left).pin_memory()
@@ -440,6 +434,8 @@ def main():
     value = ws * de / (mean_ms / 1e3) / 1e6
     subpixel["throughput_vs_integer_step"] = round(mean_ms / subpixel["ms_per_step"], 3)
     exact_cc["throughput_vs_integer_step"] = round(mean_ms / exact_cc["ms_per_step"], 3)
+    for v in ncc.values():
+        v["throughput_vs_census_step"] = round(mean_ms / v["ms_per_step"], 3)
     agg_ms = stage["aggregate"] / args.steps
     # algorithmic operations and bytes of the aggregation per launch (16-bit lane operations):
     # 9 per DE and path (8 of the recurrence, 1 accumulation) + 2 per DE (cost xor/popcount read)
@@ -462,6 +458,7 @@ def main():
         "stage_ms": {k: round(v / args.steps, 4) for k, v in stage.items()},
         "subpixel": subpixel,
         "exact_cc": exact_cc,
+        "ncc": ncc,
         "roofline": {"kernel": "aggregate (SGM paths)", "bound": "alu",
                      "achieved": round(achieved / 1e12, 3),
                      "peak": round(int_peak / 1e12, 3), "unit": "T lane-ops/s",

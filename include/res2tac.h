@@ -42,6 +42,14 @@ extern "C" {
  * again, read back mirrored) instead of the approximation of Eq. (right_disparity); about twice
  * the work. Single pairs only: res2tac_compute_batch rejects it. */
 #define RES2TAC_EXACT_CC 4
+/* NCC matching cost (Sec. 2.1.1, Sec. 2.2.1 "Inverted and truncated version of the normalized
+ * cross-correlation") instead of the census: s = 1 - max(0, Phi) with Phi the zero-mean NCC of
+ * the census_w x census_h patches (5 x 5 or 9 x 9; zero margin outside the image), on the same
+ * 8-bit cost scale: cost = 255 - clamp(rint(q), 0, 255), q = ((float(cov) * iA) * iB) * 255 in
+ * correctly rounded fp32 steps, where for N = n^2 the integers cov = N sum ab - sum a sum b,
+ * vA = N sum a^2 - (sum a)^2 (vB likewise) and iA = 1 / sqrt(float(vA)), 0 when vA = 0 (a constant
+ * patch: cost 255). 255 where x - d < 0. Single pairs only: res2tac_compute_batch rejects it. */
+#define RES2TAC_NCC 8
 
 #define RES2TAC_INVALID 0xFFFF /* disparity of a pixel rejected by the left-right check */
 
@@ -54,11 +62,12 @@ typedef void* res2tac_stream_t; /* a cudaStream_t */
  *                  Sec. 2.1.1 with d_min = 0); 16 <= D <= 256, D % 16 == 0 (Sec. 3.1.2 caps D
  *                  at 256).
  *   census_w/_h    census window: 5 x 5 (24-bit descriptor) or 9 x 7 (62-bit), width first
- *                  (Sec. 2.2.1).
+ *                  (Sec. 2.2.1); with RES2TAC_NCC the NCC patch, 5 x 5 or 9 x 9.
  *   p1, p2         SGM penalties of Eq. (sgm_path), 0 <= p1 <= p2 <= 16384.
  *   num_paths      4 (LR, RL, TB, BT) or 8 (plus the four diagonals), Sec. 3.2.
- *   flags          RES2TAC_LR_CHECK | RES2TAC_MEDIAN | RES2TAC_EXACT_CC (0 = winner-takes-all
- *                  only; RES2TAC_EXACT_CC changes D^R, so it matters with RES2TAC_LR_CHECK).
+ *   flags          RES2TAC_LR_CHECK | RES2TAC_MEDIAN | RES2TAC_EXACT_CC | RES2TAC_NCC (0 =
+ *                  census cost, winner-takes-all only; RES2TAC_EXACT_CC changes D^R, so it
+ *                  matters with RES2TAC_LR_CHECK).
  *   lr_threshold   largest accepted |D^L - D^R| of the left-right check (the paper uses 1). */
 typedef struct res2tac_params {
   int32_t width, height;
@@ -226,7 +235,8 @@ int res2tac_probe_red_peak(int64_t bytes, int32_t passes, res2tac_stream_t s, do
  * RES2TAC_STATIC_SCRATCH_BYTES compiled into the library; every GPU that loads the library holds
  * that array until the process exits.
  * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 9 B per pixel,
- * 5 B per W*H*D when num_paths * (255 + p2) > 65535, 4 B more per pixel with RES2TAC_EXACT_CC)
+ * 5 B per W*H*D when num_paths * (255 + p2) > 65535, 4 B more per pixel with RES2TAC_EXACT_CC,
+ * 16 B more per pixel with RES2TAC_NCC)
  * is rejected with RES2TAC_ENOMEM and a
  * message giving both sizes; 640 x 480 with D = 64 fits.
  * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)

@@ -20,6 +20,7 @@ RES2TAC_ETIMEOUT = -4
 RES2TAC_LR_CHECK = 1
 RES2TAC_MEDIAN = 2
 RES2TAC_EXACT_CC = 4
+RES2TAC_NCC = 8
 RES2TAC_INVALID = 0xFFFF
 
 # Every symbol include/res2tac.h declares (checked by the tests).

@@ -39,11 +39,15 @@ const char* params_error(const res2tac_params* p) {
   if (!p) return "params is NULL";
   if (!shape_ok(p->width, p->height, p->max_disp))
     return "need 1 <= width, height <= 16384 and 16 <= max_disp <= 256, max_disp % 16 == 0";
-  if (!((p->census_w == 5 && p->census_h == 5) || (p->census_w == 9 && p->census_h == 7)))
+  if (p->flags & RES2TAC_NCC) {
+    if (!((p->census_w == 5 && p->census_h == 5) || (p->census_w == 9 && p->census_h == 9)))
+      return "NCC patch must be 5x5 or 9x9";
+  } else if (!((p->census_w == 5 && p->census_h == 5) || (p->census_w == 9 && p->census_h == 7))) {
     return "census window must be 5x5 or 9x7";
+  }
   if (p->p1 < 0 || p->p2 < p->p1 || p->p2 > 16384) return "need 0 <= p1 <= p2 <= 16384";
   if (p->num_paths != 4 && p->num_paths != 8) return "num_paths must be 4 or 8";
-  if (p->flags & ~(RES2TAC_LR_CHECK | RES2TAC_MEDIAN | RES2TAC_EXACT_CC))
+  if (p->flags & ~(RES2TAC_LR_CHECK | RES2TAC_MEDIAN | RES2TAC_EXACT_CC | RES2TAC_NCC))
     return "unknown flag bits";
   if (p->lr_threshold < 0 || p->lr_threshold > 255) return "lr_threshold must be in 0..255";
   return nullptr;
@@ -110,7 +114,7 @@ size_t res2tac_workspace_bytes(const res2tac_params* p) {
   if (params_error(p)) return 0;
   const size_t npx = (size_t)p->width * p->height;
   return layout_for(p->width, p->height, p->max_disp, needs_wide(p),
-                    (p->flags & RES2TAC_EXACT_CC) != 0).total +
+                    (p->flags & RES2TAC_EXACT_CC) != 0, (p->flags & RES2TAC_NCC) != 0).total +
          npx * 2 + npx * 2 + 1024;
 }
 
@@ -130,7 +134,7 @@ int res2tac_create(const res2tac_params* p, res2tac_t* out) {
     return fail_cuda(e, "cudaGetDevice");
   }
   h->lay = layout_for(p->width, p->height, p->max_disp, h->method.wide != 0,
-                      (p->flags & RES2TAC_EXACT_CC) != 0);
+                      (p->flags & RES2TAC_EXACT_CC) != 0, (p->flags & RES2TAC_NCC) != 0);
   const size_t npx = (size_t)p->width * p->height;
   e = cudaMalloc(&h->scratch, h->lay.total);
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_in, align_up(npx * 2, 256));
@@ -423,8 +427,9 @@ int res2tac_batch_reserve(res2tac_t h, size_t scratch_bytes, int32_t max_pairs) 
 int res2tac_compute_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res2tac_stream_t s) {
   if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
   if (!pairs || n < 1) return fail(RES2TAC_EINVAL, "empty batch");
-  if (h->method.flags & RES2TAC_EXACT_CC)
-    return fail(RES2TAC_EINVAL, "the exact consistency check runs per pair (res2tac_compute)");
+  if (h->method.flags & (RES2TAC_EXACT_CC | RES2TAC_NCC))
+    return fail(RES2TAC_EINVAL,
+                "the exact consistency check and the NCC cost run per pair (res2tac_compute)");
   std::vector<r2t::Problem> probs((size_t)n);
   std::vector<size_t> offs((size_t)n);
   size_t total = 0;

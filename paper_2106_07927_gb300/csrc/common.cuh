@@ -36,6 +36,8 @@ struct Problem {
   float* disp_f;      // sub-pixel final map (caller's, out_pitch bytes per row); NULL: uint16 map
   uint8_t* flip;      // [2][H][W] right and left image, each flipped horizontally (exact check)
   uint16_t* dp;       // [H][W] D^L of that swapped, flipped pair (exact check); NULL: approximate
+  int32_t* nsum;      // [2][H][W] patch sums of the reference / matching image (NCC cost)
+  float* ninv;        // [2][H][W] 1 / sqrt(patch variance numerator) of both images (NCC cost)
 };
 
 // Method parameters shared by every pair of a call.
@@ -43,7 +45,8 @@ struct Method {
   int cw, ch;       // census window
   int P1, P2;
   int num_paths;    // 4 or 8
-  int flags;        // 1 = LR check, 2 = median, 4 = exact D^R for the check
+  int flags;        // 1 = LR check, 2 = median, 4 = exact D^R for the check, 8 = NCC cost
+  //                   (cw = ch = n: the NCC patch)
   int lr_threshold;
   int wide;         // aggregated sums kept in uint32 (needed when 8 (255 + P2) > 65535)
 };

@@ -116,13 +116,20 @@ static cudaError_t launch_aggregate(const Problem& pb, const Method& mt, const T
   return cudaGetLastError();
 }
 
-// Census + cost, aggregation and WTA (with the right-disparity keys) of the pair pb.left /
-// pb.right into pb.dl: 4 launches. ev: NULL, or 3 events recorded after each of the 3 stages.
+// Census + cost (or the NCC cost), aggregation and WTA (with the right-disparity keys) of the
+// pair pb.left / pb.right into pb.dl; adds its launches to *n. ev: NULL, or 3 events recorded
+// after each of the 3 stages.
 static cudaError_t run_pass(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
-                            cudaEvent_t* ev, const Fork* fork) {
+                            cudaEvent_t* ev, const Fork* fork, int* n) {
   cudaError_t e;
-  cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (mt.flags & 8) {
+    if ((e = launch_ncc_cost(pb, mt, s)) != cudaSuccess) return e;
+    *n += 3;
+  } else {
+    cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    *n += 1;
+  }
   if (ev) cudaEventRecord(ev[0], s);
   if ((e = launch_aggregate(pb, mt, tn, s, fork)) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
@@ -135,6 +142,7 @@ static cudaError_t run_pass(const Problem& pb, const Method& mt, const Tuning& t
     wta_dr_kernel<false><<<nw, 256, smem, s>>>(pb, T);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
+  *n += 3;
   return cudaSuccess;
 }
 
@@ -173,12 +181,11 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
     pf.right = pb.flip + npx;
     pf.in_pitch = pb.W;
     pf.dl = pb.dp;
-    if ((e = run_pass(pf, mt, tn, s, ev ? ev + 1 : nullptr, fork)) != cudaSuccess) return e;
-    n += 4;
+    if ((e = run_pass(pf, mt, tn, s, ev ? ev + 1 : nullptr, fork, &n)) != cudaSuccess) return e;
   }
-  if ((e = run_pass(pb, mt, tn, s, ev ? ev + (exact ? 4 : 1) : nullptr, fork)) != cudaSuccess)
+  if ((e = run_pass(pb, mt, tn, s, ev ? ev + (exact ? 4 : 1) : nullptr, fork, &n)) !=
+      cudaSuccess)
     return e;
-  n += 4;
   const int nm = median_items(pb.W, pb.H);
   if (pb.disp_f == nullptr)  // uint16 map
     lr_median_kernel<false, false><<<nm, 256, 0, s>>>(pb, mt);

@@ -48,7 +48,8 @@ const void* batch_shear_kernel_fn();
 // Plain single-pair pipeline: 5 kernel launches on stream s (census + cost + clearing of the
 // aggregated volume; two aggregation kernels; WTA + right-disparity keys; LR check + median).
 // With the exact check (mt.flags & 4; pb.flip and pb.dp set) first a flip kernel and the first
-// four launches again on the swapped, flipped pair: 10 launches.
+// four launches again on the swapped, flipped pair: 10 launches. The NCC cost (mt.flags & 8)
+// takes 3 launches instead of 1 per pass.
 // Returns the number of launches through *launches.
 // ev: NULL, or events recorded around the stages: 5 (before the cost stage, after each of the
 // four), with the exact check 8 (before the flip; after the cost, aggregation and WTA of each
@@ -56,6 +57,10 @@ const void* batch_shear_kernel_fn();
 // fork: NULL runs the two aggregation kernels one after the other on s.
 cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
                          int* launches, cudaEvent_t* ev = nullptr, const Fork* fork = nullptr);
+
+// NCC matching cost (mt.flags & 8, patch mt.cw x mt.cw, pb.nsum / pb.ninv set): patch statistics
+// of both images, then the cost volume with the clearing of the aggregated sums; 3 launches.
+cudaError_t launch_ncc_cost(const Problem& pb, const Method& mt, cudaStream_t s);
 
 // Sets the calling thread's res2tac_last_error message; returns code.
 int report_error(int code, const char* msg);

@@ -8,15 +8,16 @@
 namespace r2t {
 
 struct Layout {
-  size_t cost, agg, dl, dr, kr, mask, flip, dp, total;  // flip, dp: 0 without the exact check
+  size_t cost, agg, dl, dr, kr, mask, flip, dp, nsum, ninv, total;  // 0: buffer not used
 };
 
 inline size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Cost 1 B/DE, aggregated volume 2 B/DE (4 when wide), D^L and D^R 2 B/px each,
 // right-disparity keys 4 B/px, LR mask 1 B/px: 3 B per DE + 9 B per pixel. The exact
-// consistency check adds the swapped, flipped pair (2 B/px) and its D^L (2 B/px).
-inline Layout layout_for(int W, int H, int D, bool wide, bool exact = false) {
+// consistency check adds the swapped, flipped pair (2 B/px) and its D^L (2 B/px); the NCC cost
+// the patch statistics of both images (16 B/px).
+inline Layout layout_for(int W, int H, int D, bool wide, bool exact = false, bool ncc = false) {
   const size_t npx = (size_t)W * H, nde = npx * D;
   Layout l;
   size_t o = 0;
@@ -30,6 +31,11 @@ inline Layout layout_for(int W, int H, int D, bool wide, bool exact = false) {
   if (exact) {
     l.flip = o; o = align256(o + npx * 2);
     l.dp = o; o = align256(o + npx * 2);
+  }
+  l.nsum = l.ninv = 0;
+  if (ncc) {
+    l.nsum = o; o = align256(o + npx * 8);
+    l.ninv = o; o = align256(o + npx * 8);
   }
   l.total = o;
   return l;
@@ -50,6 +56,8 @@ inline Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
   pb.disp_f = nullptr;
   pb.flip = l.flip ? reinterpret_cast<uint8_t*>(base + l.flip) : nullptr;
   pb.dp = l.dp ? reinterpret_cast<uint16_t*>(base + l.dp) : nullptr;
+  pb.nsum = l.nsum ? reinterpret_cast<int32_t*>(base + l.nsum) : nullptr;
+  pb.ninv = l.ninv ? reinterpret_cast<float*>(base + l.ninv) : nullptr;
   return pb;
 }
 

@@ -46,7 +46,8 @@ extern "C" int res2tac_compute_static(const res2tac_params* p, const uint8_t* le
   const int W = p->width, H = p->height, D = p->max_disp;
   const bool wide = p->num_paths * (255 + p->p2) > 65535;
   // the same buffers a context allocates, at their offsets inside the array
-  const r2t::Layout lay = r2t::layout_for(W, H, D, wide, (p->flags & RES2TAC_EXACT_CC) != 0);
+  const r2t::Layout lay = r2t::layout_for(W, H, D, wide, (p->flags & RES2TAC_EXACT_CC) != 0,
+                                          (p->flags & RES2TAC_NCC) != 0);
   if (lay.total > RES2TAC_STATIC_SCRATCH_BYTES)
     return reject(RES2TAC_ENOMEM,
                   "res2tac_compute_static: %dx%d with D=%d needs %zu bytes of scratch, more than "

@@ -27,8 +27,8 @@ def test_library_exports_every_declared_symbol(cuda_lib):
 
 @pytest.mark.parametrize("bad", [
     dict(width=0), dict(height=16385), dict(max_disp=8), dict(max_disp=264), dict(max_disp=40),
-    dict(census_w=7), dict(p1=20, p2=10), dict(p2=20000), dict(num_paths=6), dict(flags=8),
-    dict(lr_threshold=-1),
+    dict(census_w=7), dict(p1=20, p2=10), dict(p2=20000), dict(num_paths=6), dict(flags=16),
+    dict(flags=8, census_w=9, census_h=7), dict(census_w=9, census_h=9), dict(lr_threshold=-1),
 ])
 def test_invalid_params_rejected(cuda_lib, bad):
     d = dict(width=64, height=32, max_disp=32, census_w=9, census_h=7, p1=10, p2=120,

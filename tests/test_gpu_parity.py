@@ -223,3 +223,67 @@ def test_exact_check_launches_stages_and_batch_rejection():
     with pytest.raises(binding.Res2tacError):
         binding.res2tac_compute_batch(st.handle, [pair], 0)
     st.close()
+
+
+# ------------------------------------------------------------------------- NCC matching cost
+NCC = 8
+
+
+@pytest.mark.parametrize("n", [5, 9])
+def test_ncc_full_size_road_pair(n):
+    # the 1242 x 375 workload with the paper's NCC penalties (P1 = 90, P2 = 880)
+    left, right, _, prm = scenes.single_pair("1242x375_d128_ct9x7_r8", 0)
+    if n == 9:
+        left, right = left[:160], right[:160]
+    prm = dict(prm, census_w=n, census_h=n, p1=90, p2=880, flags=prm["flags"] | NCC,
+               height=left.shape[0])
+    _assert_same(left, right, prm)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_ncc_tiny_random_shapes(seed):
+    rng = np.random.default_rng(700 + seed)
+    W = int(rng.integers(1, 90))
+    H = int(rng.integers(1, 50))
+    D = int(rng.choice([16, 32, 48, 64, 80, 128, 256]))
+    n = (5, 9)[seed % 2]
+    R = (4, 8)[(seed // 2) % 2]
+    left = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    right = np.clip(left.astype(int) + rng.integers(-30, 31, (H, W)), 0, 255).astype(np.uint8)
+    if seed % 3 == 0:
+        right[: H // 2] = 128  # constant region: zero variance
+    flags = NCC | (seed % 4) | (4 if seed >= 6 else 0)
+    prm = scenes.params(W, H, D, n, n, int(rng.integers(0, 100)), 880, R, flags, seed % 3)
+    _assert_same(left, right, prm)
+
+
+@pytest.mark.parametrize("W,H,D,n", [(200, 37, 64, 5), (97, 61, 128, 9), (130, 33, 256, 9)])
+def test_ncc_ragged_tiles(W, H, D, n):
+    left, right, _ = scenes.make_scene("road", W + H + n, W, H, D)
+    _assert_same(left, right, scenes.params(W, H, D, n, n, 90, 880, 8, 3 | NCC))
+
+
+def test_ncc_saturated_sums_exact_check_padded_pitches():
+    rng = np.random.default_rng(8)
+    W, H, D = 140, 70, 64
+    left = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    right = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    _assert_same(left, right, scenes.params(W, H, D, 5, 5, 100, 16384, 8, 3 | 4 | NCC),
+                 in_pad=5, out_pad=2)
+
+
+def test_ncc_launches_and_rejections():
+    import torch
+    left, right, _, prm = scenes.single_pair("320x240_d64_ct5x5_r4", 0)
+    st = binding.Stereo(dict(prm, flags=3 | NCC))
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    st.compute(L, R)
+    assert binding.res2tac_last_launch_count(st.handle) == 7
+    o = torch.empty_like(L, dtype=torch.int16)
+    pair = binding.res2tac_pair(L.data_ptr(), R.data_ptr(), L.shape[1], o.data_ptr(),
+                                2 * L.shape[1], L.shape[1], L.shape[0], prm["max_disp"], 0)
+    with pytest.raises(binding.Res2tacError):
+        binding.res2tac_compute_batch(st.handle, [pair], 0)
+    st.close()
+    with pytest.raises(binding.Res2tacError):  # 9 x 7 is a census window, not an NCC patch
+        binding.Stereo(dict(prm, census_w=9, census_h=7, flags=NCC))
