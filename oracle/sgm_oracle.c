@@ -185,8 +185,8 @@ static int px_or_zero(const uint8_t* img, int64_t pitch, int W, int H, int x, in
  *   cost = 255 - clamp(round(255 max(0, Phi)), 0, 255), the truncated 1 - max(0, Phi) on 0..255.
  * The scaling to an 8-bit cost decides an integer in floating point, so it follows one fixed
  * sequence of correctly rounded fp32 operations (the precision of the GPU path):
- *   iA = 1 / sqrt(float(vA)) (0 when vA = 0), iB likewise,
- *   q = ((float(cov) * iA) * iB) * 255,  cost = 255 - clamp(rint(q), 0, 255)  (rint: ties to even).
+ *   iA = 1 / sqrt(float(vA)) (0 when vA = 0), iB likewise, jB = 255 * iB,
+ *   q = (float(cov) * iA) * jB,  cost = 255 - clamp(rint(q), 0, 255)  (rint: ties to even).
  * A cov <= 0 gives q <= 0 and so 255 (the max(0, .) truncation). */
 static uint8_t ncc_pair_cost(const uint8_t* A, const uint8_t* B, int64_t pitch, int W, int H,
                              int xa, int xb, int y, int n) {
@@ -205,9 +205,9 @@ static uint8_t ncc_pair_cost(const uint8_t* A, const uint8_t* B, int64_t pitch, 
   int64_t vA = N * sAA - sA * sA, vB = N * sBB - sB * sB, cov = N * sAB - sA * sB;
   volatile float iA = vA > 0 ? 1.0f / sqrtf((float)vA) : 0.0f;
   volatile float iB = vB > 0 ? 1.0f / sqrtf((float)vB) : 0.0f;
+  volatile float jB = 255.0f * iB;
   volatile float q = (float)cov * iA;
-  q = q * iB;
-  q = q * 255.0f;
+  q = q * jB;
   float k = rintf(q);
   if (k < 0.0f) k = 0.0f;
   if (k > 255.0f) k = 255.0f;
