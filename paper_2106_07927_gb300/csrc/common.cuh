@@ -36,8 +36,7 @@ struct Problem {
   float* disp_f;      // sub-pixel final map (caller's, out_pitch bytes per row); NULL: uint16 map
   uint8_t* flip;      // [2][H][W] right and left image, each flipped horizontally (exact check)
   uint16_t* dp;       // [H][W] D^L of that swapped, flipped pair (exact check); NULL: approximate
-  int32_t* nsum;      // [2][H][W] patch sums of the reference / matching image (NCC cost)
-  float* ninv;        // [2][H][W] 1 / sqrt(patch variance numerator) of both images (NCC cost)
+  uint2* nst;         // [2][H][W] patch sum and factor of the reference / matching image (NCC)
 };
 
 // Method parameters shared by every pair of a call.

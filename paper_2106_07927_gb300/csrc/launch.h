@@ -58,7 +58,7 @@ const void* batch_shear_kernel_fn();
 cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
                          int* launches, cudaEvent_t* ev = nullptr, const Fork* fork = nullptr);
 
-// NCC matching cost (mt.flags & 8, patch mt.cw x mt.cw, pb.nsum / pb.ninv set): patch statistics
+// NCC matching cost (mt.flags & 8, patch mt.cw x mt.cw, pb.nst set): patch statistics
 // of both images, then the cost volume with the clearing of the aggregated sums; 3 launches.
 cudaError_t launch_ncc_cost(const Problem& pb, const Method& mt, cudaStream_t s);
 

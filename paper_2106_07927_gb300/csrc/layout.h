@@ -8,7 +8,7 @@
 namespace r2t {
 
 struct Layout {
-  size_t cost, agg, dl, dr, kr, mask, flip, dp, nsum, ninv, total;  // 0: buffer not used
+  size_t cost, agg, dl, dr, kr, mask, flip, dp, nst, total;  // 0: buffer not used
 };
 
 inline size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -32,10 +32,9 @@ inline Layout layout_for(int W, int H, int D, bool wide, bool exact = false, boo
     l.flip = o; o = align256(o + npx * 2);
     l.dp = o; o = align256(o + npx * 2);
   }
-  l.nsum = l.ninv = 0;
-  if (ncc) {
-    l.nsum = o; o = align256(o + npx * 8);
-    l.ninv = o; o = align256(o + npx * 8);
+  l.nst = 0;
+  if (ncc) {  // 2 KB of slack in front (reads at a matching pixel x - d < 0 stay inside)
+    l.nst = o + 2048; o = align256(o + 2048 + npx * 16);
   }
   l.total = o;
   return l;
@@ -56,8 +55,7 @@ inline Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
   pb.disp_f = nullptr;
   pb.flip = l.flip ? reinterpret_cast<uint8_t*>(base + l.flip) : nullptr;
   pb.dp = l.dp ? reinterpret_cast<uint16_t*>(base + l.dp) : nullptr;
-  pb.nsum = l.nsum ? reinterpret_cast<int32_t*>(base + l.nsum) : nullptr;
-  pb.ninv = l.ninv ? reinterpret_cast<float*>(base + l.ninv) : nullptr;
+  pb.nst = l.nst ? reinterpret_cast<uint2*>(base + l.nst) : nullptr;
   return pb;
 }
 

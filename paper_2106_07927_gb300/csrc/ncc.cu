@@ -7,9 +7,11 @@
 //   Phi = cov / sqrt(vA vB)  (0 when vA or vB is 0)
 // and the 8-bit cost 255 - clamp(rint(255 max(0, Phi)), 0, 255), scaled in a fixed sequence of
 // correctly rounded fp32 operations: iA = 1 / sqrt(float(vA)) (0 when vA = 0), iB likewise,
-// q = ((float(cov) * iA) * iB) * 255, cost = 255 - clamp(rint(q), 0, 255). A cov <= 0 gives 255.
+// jB = 255 iB, q = (float(cov) * iA) * jB, cost = 255 - clamp(rint(q), 0, 255). A cov <= 0
+// gives 255.
 //
-// ncc_stats_kernel: per pixel of both images, sum a over the patch and iA.
+// ncc_stats_kernel: per pixel, the patch sum and the factor (iA for the reference image, jB for
+// the matching one), as one 8-byte pair.
 // ncc_cost_kernel: a band of kNccTY rows x TX pixels x all D per block of 256 threads; thread
 // (x, g) owns disparities 4g .. 4g + 3 of pixel x. Down the band it forms, per image row, the
 // dot products of the patch rows (dp4a over byte words realigned from shared memory) and keeps
@@ -31,18 +33,19 @@ constexpr int kNccRStride = 288;                  // >= TX + D - 1 + 2r + 3 + 8 
 
 __host__ __device__ inline int ncc_tx(int D) { return 256 / (D / 4); }  // pixels per block
 
-// Sum a and 1 / sqrt(vA) of the n x n patch around every pixel of one image (blocks of 32 x 8).
+// Patch sum and factor of every pixel of one image (blocks of 32 x 8): {sum a, bits of f} with
+// f = 1 / sqrt(float(vA)) (reference image) or 255 / ... as fl(255 * f) (matching image, scale255).
 template <int N_>
 __global__ void __launch_bounds__(256) ncc_stats_kernel(const uint8_t* img, int64_t pitch, int W,
-                                                        int H, int32_t* sum, float* inv) {
-  constexpr int R = N_ / 2;
-  __shared__ uint8_t t[8 + 2 * R][32 + 2 * R];
+                                                        int H, uint2* st, bool scale255) {
+  constexpr int R = N_ / 2, TW = 32 + 2 * R;
+  __shared__ uint8_t t[8 + 2 * R][TW];
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
-  for (int i = threadIdx.x; i < (8 + 2 * R) * (32 + 2 * R); i += 256) {
-    const int ty = i / (32 + 2 * R), tx = i % (32 + 2 * R);
-    const int gx = x0 + tx - R, gy = y0 + ty - R;
-    t[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(int64_t)gy * pitch + gx] : 0;
-  }
+  for (int ty = 0; ty < 8 + 2 * R; ty++)
+    for (int tx = threadIdx.x; tx < TW; tx += 256) {
+      const int gx = x0 + tx - R, gy = y0 + ty - R;
+      t[ty][tx] = (gx >= 0 && gx < W && gy >= 0 && gy < H) ? img[(int64_t)gy * pitch + gx] : 0;
+    }
   __syncthreads();
   const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
   const int x = x0 + lx, y = y0 + ly;
@@ -57,25 +60,23 @@ __global__ void __launch_bounds__(256) ncc_stats_kernel(const uint8_t* img, int6
       s2 += v * v;
     }
   const int v = N_ * N_ * s2 - s1 * s1;  // <= N^2 255^2 / 4 < 2^27
-  const int64_t p = (int64_t)y * W + x;
-  sum[p] = s1;
-  inv[p] = v > 0 ? __fdiv_rn(1.0f, __fsqrt_rn(__int2float_rn(v))) : 0.0f;
+  float f = v > 0 ? __fdiv_rn(1.0f, __fsqrt_rn(__int2float_rn(v))) : 0.0f;
+  if (scale255) f = __fmul_rn(255.0f, f);
+  st[(int64_t)y * W + x] = make_uint2((uint32_t)s1, __float_as_uint(f));
 }
 
-// The 8-bit cost of one patch pair from its sums.
-__device__ __forceinline__ uint32_t ncc_cost_of(int nn, int sab, int sa, int sb, float ia,
-                                                float ib) {
-  const int cov = nn * sab - sa * sb;  // |cov| < 2^29
-  float q = __fmul_rn(__int2float_rn(cov), ia);
-  q = __fmul_rn(q, ib);
-  q = __fmul_rn(q, 255.0f);
-  const int k = min(max(__float2int_rn(q), 0), 255);
-  return (uint32_t)(255 - k);
+// The 8-bit cost of one patch pair from its sums: 255 - sat_u8(rint((cov * iA) * jB)).
+__device__ __forceinline__ uint32_t ncc_cost_of(int nn, int sab, int sa, float ia, uint2 mb) {
+  const int cov = nn * sab - sa * (int)mb.x;  // |cov| < 2^29
+  const float q = __fmul_rn(__fmul_rn(__int2float_rn(cov), ia), __uint_as_float(mb.y));
+  uint32_t k;
+  asm("cvt.rni.sat.u8.f32 %0, %1;" : "=r"(k) : "f"(q));  // rint, then clamp to 0 .. 255
+  return 255u - k;
 }
 
 template <int N_>
-__global__ void __launch_bounds__(256) ncc_cost_kernel(Problem pb, int agg_bytes_per_de,
-                                                       const int32_t* sum, const float* inv) {
+__global__ void __launch_bounds__(256, N_ == 5 ? 4 : 2)
+    ncc_cost_kernel(Problem pb, int agg_bytes_per_de, const uint2* st) {
   constexpr int R = N_ / 2;
   constexpr int NW = (N_ + 3) / 4;  // dot-product words of a patch row
   __shared__ __align__(16) uint8_t sl[kNccMaxRows][kNccLStride];
@@ -88,29 +89,73 @@ __global__ void __launch_bounds__(256) ncc_cost_kernel(Problem pb, int agg_bytes
   const int lbase = x0 - R;                       // image column of sl[.][0]
   const int rbase = x0 - (D - 1) - R - 3;         // image column of sr[.][0]
   const int lw = TX + 2 * R + 8, rw = TX + D - 1 + 2 * R + 3 + 8;
-  for (int i = threadIdx.x; i < nrows * (lw + rw); i += 256) {
-    const int row = i / (lw + rw), c = i % (lw + rw);
-    const int gy = y0 - R + row;
-    const bool isr = c >= lw;
-    const int gx = isr ? rbase + (c - lw) : lbase + c;
-    uint8_t v = 0;
-    if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-      v = (isr ? pb.right : pb.left)[(int64_t)gy * pb.in_pitch + gx];
-    if (isr)
-      sr[row][c - lw] = v;
-    else
-      sl[row][c] = v;
+  // staged columns c < lw are the left segment, c >= lw the right one (lw + rw <= 2 * 256)
+  for (int r0 = 0; r0 < nrows; r0 += 4) {
+    uint8_t v[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const int gy = y0 - R + r0 + u;
+      const bool rowin = r0 + u < nrows && gy >= 0 && gy < H;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int c = threadIdx.x + 256 * h;
+        const bool isr = c >= lw;
+        const int gx = isr ? rbase + (c - lw) : lbase + c;
+        v[u][h] = 0;
+        if (rowin && c < lw + rw && gx >= 0 && gx < W)
+          v[u][h] = __ldg((isr ? pb.right : pb.left) + (int64_t)gy * pb.in_pitch + gx);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int c = threadIdx.x + 256 * h;
+        if (r0 + u < nrows && c < lw + rw) {
+          if (c >= lw)
+            sr[r0 + u][c - lw] = v[u][h];
+          else
+            sl[r0 + u][c] = v[u][h];
+        }
+      }
   }
   __syncthreads();
 
+  // clear the aggregated sums and reset the right-disparity keys of the tile's pixels: per row
+  // one contiguous run of nx pixels (16-byte pieces, D % 16 == 0)
+  {
+    const int ny = min(kNccTY, H - y0), nx = min(TX, W - x0);
+    const int pieces = nx * D * agg_bytes_per_de / 16;
+    for (int row = 0; row < ny; row++) {
+      const int64_t p = (int64_t)(y0 + row) * W + x0;
+      uint4* z = reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(pb.agg) +
+                                          p * D * agg_bytes_per_de);
+      for (int i = threadIdx.x; i < pieces; i += 256) z[i] = make_uint4(0, 0, 0, 0);
+      if (threadIdx.x < nx) pb.kr[p + threadIdx.x] = 0xFFFFFFFFu;
+    }
+  }
   const int g = threadIdx.x % G, xl = threadIdx.x / G;
   const int x = x0 + xl;
-  const bool active = xl < TX && x < W;
+  if (xl >= TX || x >= W) return;  // no barrier follows
   const int nn = N_ * N_;
+  const int64_t npx = (int64_t)W * H;
   // this thread's windows: left bytes [xl, xl + N_) of sl; right bytes [s0, s0 + N_ + 3) of sr
   // hold the windows of d = 4g + 3, 4g + 2, 4g + 1, 4g (d = 4g + k starts at s0 + 3 - k)
   const int s0 = xl + D - 1 - 4 * g;
+  const int lsh = 8 * (xl & 3), rsh = 8 * (s0 & 3);
   const uint32_t lmask = (N_ % 4) ? (0xFFFFFFFFu >> (8 * (4 - N_ % 4))) : 0xFFFFFFFFu;
+  const uint32_t* lrow = reinterpret_cast<const uint32_t*>(&sl[0][xl & ~3]);
+  const uint32_t* rrow = reinterpret_cast<const uint32_t*>(&sr[0][s0 & ~3]);
+  // statistics: the reference pixel, and the matching pixels x - 4g - k (k = 0 .. 3); the
+  // buffer has 256 entries of slack in front, so x - 4g - k < 0 still reads inside it
+  // (pointer of the next output row, advanced by one image row per output row)
+  const uint2* sa_p = st + (int64_t)y0 * W + x;
+  const int64_t mo = npx - 4 * g;  // matching pixel x - 4g, same row
+  uint32_t* out = reinterpret_cast<uint32_t*>(pb.cost + ((int64_t)y0 * W + x) * D) + g;
+  const int out_row = W * D / 4;  // uint32 words per image row
+  bool inside[4];                 // x - d >= 0 for d = 4g + k
+#pragma unroll
+  for (int k = 0; k < 4; k++) inside[k] = x - 4 * g - k >= 0;
   int ring[N_][4];
   int vs[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -118,93 +163,75 @@ __global__ void __launch_bounds__(256) ncc_cost_kernel(Problem pb, int agg_bytes
 #pragma unroll
     for (int k = 0; k < 4; k++) ring[j][k] = 0;
 
-  for (int t0 = 0; t0 < nrows; t0 += N_) {
+  // one staged row t: its four row dot products enter the ring (slot j = t mod N_); from
+  // t = 2R on, the patch of output row t - 2R is complete and its costs are written
+  auto row_step = [&](int t, int j) {
+    uint32_t lwd[NW], rwd[NW + 1];
+    {
+      uint32_t raw[NW + 1];
 #pragma unroll
-    for (int j = 0; j < N_; j++) {
-      const int t = t0 + j;  // staged row
-      if (t < nrows && active) {
-        // left words, realigned to start at xl
-        uint32_t lwd[NW];
-        {
-          const uint32_t* p = reinterpret_cast<const uint32_t*>(&sl[t][xl & ~3]);
-          uint32_t raw[NW + 1];
+      for (int m = 0; m <= NW; m++) raw[m] = lrow[t * (kNccLStride / 4) + m];
 #pragma unroll
-          for (int m = 0; m <= NW; m++) raw[m] = p[m];
-#pragma unroll
-          for (int m = 0; m < NW; m++) lwd[m] = __funnelshift_r(raw[m], raw[m + 1], 8 * (xl & 3));
-          lwd[NW - 1] &= lmask;
-        }
-        // right words, realigned to start at s0
-        uint32_t rwd[NW + 1];
-        {
-          const uint32_t* p = reinterpret_cast<const uint32_t*>(&sr[t][s0 & ~3]);
-          uint32_t raw[NW + 2];
-#pragma unroll
-          for (int m = 0; m <= NW + 1; m++) raw[m] = p[m];
-#pragma unroll
-          for (int m = 0; m <= NW; m++) rwd[m] = __funnelshift_r(raw[m], raw[m + 1], 8 * (s0 & 3));
-        }
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          const int o = 3 - k;  // byte offset of the window of d = 4g + k
-          uint32_t h = 0;
-#pragma unroll
-          for (int m = 0; m < NW; m++)
-            h = __dp4a(lwd[m], o ? __funnelshift_r(rwd[m], rwd[m + 1], 8 * o) : rwd[m], h);
-          vs[k] += (int)h - ring[j][k];
-          ring[j][k] = (int)h;
-        }
-      }
-      if (t < nrows && t >= 2 * R && active) {
-        const int y = y0 + t - 2 * R;  // the patch rows y - R .. y + R are all in the ring
-        const int64_t p = (int64_t)y * W + x;
-        const int sa = sum[p];
-        const float ia = inv[p];
-        uint32_t c[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-          const int d = 4 * g + k;
-          c[k] = kCostOutside;
-          if (x - d >= 0) {
-            const int64_t q = p - d + (int64_t)W * H;  // matching image's statistics
-            c[k] = ncc_cost_of(nn, vs[k], sa, sum[q], ia, inv[q]);
-          }
-        }
-        reinterpret_cast<uint32_t*>(pb.cost + p * D)[g] =
-            c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
-      }
+      for (int m = 0; m < NW; m++) lwd[m] = __funnelshift_r(raw[m], raw[m + 1], lsh);
+      lwd[NW - 1] &= lmask;
     }
+    {
+      uint32_t raw[NW + 2];
+#pragma unroll
+      for (int m = 0; m <= NW + 1; m++) raw[m] = rrow[t * (kNccRStride / 4) + m];
+#pragma unroll
+      for (int m = 0; m <= NW; m++) rwd[m] = __funnelshift_r(raw[m], raw[m + 1], rsh);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const int o = 3 - k;  // byte offset of the window of d = 4g + k
+      uint32_t h = 0;
+#pragma unroll
+      for (int m = 0; m < NW; m++)
+        h = __dp4a(lwd[m], o ? __funnelshift_r(rwd[m], rwd[m + 1], 8 * o) : rwd[m], h);
+      vs[k] += (int)h - ring[j][k];
+      ring[j][k] = (int)h;
+    }
+    if (t >= 2 * R) {  // output row y0 + t - 2R
+      const uint2 a = *sa_p;
+      const uint2* mb = sa_p + mo;
+      uint32_t c[4];
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        const uint32_t v = ncc_cost_of(nn, vs[k], (int)a.x, __uint_as_float(a.y), mb[-k]);
+        c[k] = inside[k] ? v : (uint32_t)kCostOutside;
+      }
+      *out = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
+      sa_p += W;
+      out += out_row;
+    }
+  };
+  int t0 = 0;
+  for (; t0 + N_ <= nrows; t0 += N_) {
+#pragma unroll
+    for (int j = 0; j < N_; j++) row_step(t0 + j, j);
   }
-  // clear the aggregated sums and reset the right-disparity keys of the tile's pixels
-  const int ny = min(kNccTY, H - y0), nx = min(TX, W - x0);
-  const int per_px = D * agg_bytes_per_de / 16;  // 16-byte pieces per pixel (D % 16 == 0)
-  for (int i = threadIdx.x; i < ny * nx * per_px; i += 256) {
-    const int piece = i % per_px, pxi = i / per_px;
-    const int64_t p = (int64_t)(y0 + pxi / nx) * W + x0 + pxi % nx;
-    reinterpret_cast<uint4*>(reinterpret_cast<uint8_t*>(pb.agg) + p * D * agg_bytes_per_de)[piece] =
-        make_uint4(0, 0, 0, 0);
-  }
-  for (int i = threadIdx.x; i < ny * nx; i += 256)
-    pb.kr[(int64_t)(y0 + i / nx) * W + x0 + i % nx] = 0xFFFFFFFFu;
+#pragma unroll
+  for (int j = 0; j < N_; j++)
+    if (t0 + j < nrows) row_step(t0 + j, j);
 }
 
 template <int N_>
 cudaError_t launch_ncc_n(const Problem& pb, const Method& mt, cudaStream_t s) {
   const int64_t npx = (int64_t)pb.W * pb.H;
   const dim3 sg((pb.W + 31) / 32, (pb.H + 7) / 8);
-  ncc_stats_kernel<N_><<<sg, 256, 0, s>>>(pb.left, pb.in_pitch, pb.W, pb.H, pb.nsum, pb.ninv);
-  ncc_stats_kernel<N_><<<sg, 256, 0, s>>>(pb.right, pb.in_pitch, pb.W, pb.H, pb.nsum + npx,
-                                          pb.ninv + npx);
+  ncc_stats_kernel<N_><<<sg, 256, 0, s>>>(pb.left, pb.in_pitch, pb.W, pb.H, pb.nst, false);
+  ncc_stats_kernel<N_><<<sg, 256, 0, s>>>(pb.right, pb.in_pitch, pb.W, pb.H, pb.nst + npx, true);
   const int TX = ncc_tx(pb.D);
   const int blocks = ((pb.W + TX - 1) / TX) * ((pb.H + kNccTY - 1) / kNccTY);
-  ncc_cost_kernel<N_><<<blocks, 256, 0, s>>>(pb, mt.wide ? 4 : 2, pb.nsum, pb.ninv);
+  ncc_cost_kernel<N_><<<blocks, 256, 0, s>>>(pb, mt.wide ? 4 : 2, pb.nst);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_ncc_cost(const Problem& pb, const Method& mt, cudaStream_t s) {
-  if (!pb.nsum || !pb.ninv || pb.D % 16 != 0 || pb.D > 256) return cudaErrorInvalidValue;
+  if (!pb.nst || pb.D % 16 != 0 || pb.D > 256) return cudaErrorInvalidValue;
   if (mt.cw == 5) return launch_ncc_n<5>(pb, mt, s);
   if (mt.cw == 9) return launch_ncc_n<9>(pb, mt, s);
   return cudaErrorInvalidValue;
