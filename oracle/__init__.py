@@ -62,13 +62,14 @@ def _load():
         lib.r2o_subpixel.argtypes = [P, P, I, I, I, P]
         lib.r2o_cost_right.argtypes = [P, P, I, I, I, P]
         lib.r2o_ncc_cost.argtypes = [P, P, I64, I, I, I, I, P]
+        lib.r2o_rectify.argtypes = [P, I64, I, I, P, P, I64, I, I, P, I64]
         lib.r2o_ncc_cost_right.argtypes = [P, P, I64, I, I, I, I, P]
         lib.r2o_median3x3_f64.argtypes = [P, I, I, P]
         lib.r2o_sgm_subpixel.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, P, P]
         for f in (lib.r2o_census, lib.r2o_cost, lib.r2o_path, lib.r2o_aggregate, lib.r2o_wta,
                   lib.r2o_right_disparity, lib.r2o_lr_check, lib.r2o_median3x3, lib.r2o_sgm,
                   lib.r2o_subpixel, lib.r2o_median3x3_f64, lib.r2o_sgm_subpixel,
-                  lib.r2o_cost_right, lib.r2o_ncc_cost, lib.r2o_ncc_cost_right):
+                  lib.r2o_cost_right, lib.r2o_ncc_cost, lib.r2o_ncc_cost_right, lib.r2o_rectify):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -231,3 +232,16 @@ def sgm_subpixel(left: np.ndarray, right: np.ndarray, D: int, census_w: int, cen
                                   P2, num_paths, flags, lr_threshold, _ptr(disp), _ptr(ref))
     _check(rc, "sgm_subpixel")
     return disp, ref
+
+
+def rectify(raw: np.ndarray, mapx: np.ndarray, mapy: np.ndarray) -> np.ndarray:
+    """Rectified image [H, W] from a raw image and float32 maps [H, W] of source coordinates."""
+    raw = np.ascontiguousarray(raw, dtype=np.uint8)
+    mapx = np.ascontiguousarray(mapx, dtype=np.float32)
+    mapy = np.ascontiguousarray(mapy, dtype=np.float32)
+    rh, rw = raw.shape
+    H, W = mapx.shape
+    out = np.empty((H, W), np.uint8)
+    _check(_load().r2o_rectify(_ptr(raw), rw, rw, rh, _ptr(mapx), _ptr(mapy), 4 * W, W, H,
+                               _ptr(out), W), "rectify")
+    return out

@@ -32,6 +32,10 @@
  *                       s = 1 - max(0, Phi) with Phi the zero-mean NCC of the n x n patches
  *                       around (x, y) in the reference and (x -/+ d, y) in the matching image
  *                       (zero margin as for the census), scaled to 0..255 (see the function).
+ *   r2o_rectify         rectification (Sec. 2.1.1: the pair is resampled through two maps so
+ *                       that epipolar lines lie on image rows): bilinear interpolation of the raw
+ *                       image at the map's source coordinate, on a 1/32-pixel grid with integer
+ *                       weights (see the function); samples outside the raw image read 0.
  *   r2o_sgm             the whole chain above, in the order of Sec. 2.1. With flag 4 (exact
  *                       check) D^R is the WTA of the right-reference volume aggregated from C^R
  *                       over the same paths, instead of Eq. (right_disparity). The paper gets it
@@ -583,4 +587,39 @@ int r2o_sgm_subpixel(const uint8_t* left, const uint8_t* right, int64_t pitch, i
   free(ref);
   free(chk);
   return rc;
+}
+
+/* Rectification of one image through its map (Sec. 2.1.1). For every output pixel (x, y) the
+ * map gives the source coordinate (mx, my) in the raw image (float32, mapx / mapy rows of
+ * map_pitch bytes). The coordinate is put on a 1/32-pixel grid, X = rint(32 mx), Y = rint(32 my)
+ * (the product by 32 is exact in float; rint rounds ties to even); a coordinate that is not
+ * finite or has |32 m| >= 2^24 yields 0. With x0 = floor(X / 32), fx = X - 32 x0 (y likewise) the
+ * output is the bilinear interpolation with integer weights summing to 1024, rounded:
+ *   (I(x0,y0)(32-fx)(32-fy) + I(x0+1,y0) fx (32-fy) + I(x0,y0+1)(32-fx) fy
+ *    + I(x0+1,y0+1) fx fy + 512) >> 10,
+ * where samples outside the raw image (rw x rh) read 0. */
+int r2o_rectify(const uint8_t* raw, int64_t raw_pitch, int rw, int rh, const float* mapx,
+                const float* mapy, int64_t map_pitch, int W, int H, uint8_t* out,
+                int64_t out_pitch) {
+  if (!raw || !mapx || !mapy || !out || rw < 1 || rh < 1 || W < 1 || H < 1) return -1;
+  for (int y = 0; y < H; y++)
+    for (int x = 0; x < W; x++) {
+      const float* mxr = (const float*)((const uint8_t*)mapx + (int64_t)y * map_pitch);
+      const float* myr = (const float*)((const uint8_t*)mapy + (int64_t)y * map_pitch);
+      float sx = mxr[x] * 32.0f, sy = myr[x] * 32.0f;
+      int v = 0;
+      if (isfinite(sx) && isfinite(sy) && fabsf(sx) < 16777216.0f && fabsf(sy) < 16777216.0f) {
+        int X = (int)rintf(sx), Y = (int)rintf(sy);
+        int x0 = (int)floor(X / 32.0), y0 = (int)floor(Y / 32.0);
+        int fx = X - 32 * x0, fy = Y - 32 * y0;
+        int p00 = px_or_zero(raw, raw_pitch, rw, rh, x0, y0);
+        int p10 = px_or_zero(raw, raw_pitch, rw, rh, x0 + 1, y0);
+        int p01 = px_or_zero(raw, raw_pitch, rw, rh, x0, y0 + 1);
+        int p11 = px_or_zero(raw, raw_pitch, rw, rh, x0 + 1, y0 + 1);
+        v = (p00 * (32 - fx) * (32 - fy) + p10 * fx * (32 - fy) + p01 * (32 - fx) * fy +
+             p11 * fx * fy + 512) >> 10;
+      }
+      out[(int64_t)y * out_pitch + x] = (uint8_t)v;
+    }
+  return 0;
 }

@@ -263,3 +263,27 @@ def batch_pairs(seed: int = 0, n: int = 64, big_fraction: float = 0.0):
         left, right, gt = make_scene(s["kind"], s["seed"], p["width"], p["height"], p["max_disp"])
         out.append((left, right, gt, dict(p)))
     return out
+
+
+def rectification_maps(seed: int, W: int, H: int, raw_w: int | None = None,
+                       raw_h: int | None = None, strength: float = 1.0):
+    """Seeded float32 maps (mapx, mapy) [H, W] of a calibration-like rectification: for each
+    rectified pixel the source coordinate in a raw_w x raw_h image under a small in-plane rotation
+    (up to 1 degree), a sub-pixel shift and radial lens distortion (|k1| <= 0.08 at the image
+    corners). These are inputs, as a calibration routine would deliver them; no matching here."""
+    raw_w = raw_w or W
+    raw_h = raw_h or H
+    rng = np.random.default_rng(seed)
+    f = 0.9 * max(W, H)
+    theta = np.deg2rad(rng.uniform(-1.0, 1.0)) * strength
+    k1 = rng.uniform(-0.08, 0.08) * strength
+    tx, ty = rng.uniform(-1.5, 1.5, size=2) * strength
+    v, u = np.mgrid[0:H, 0:W].astype(np.float64)
+    xn, yn = (u - (W - 1) / 2) / f, (v - (H - 1) / 2) / f
+    c, s = np.cos(theta), np.sin(theta)
+    xr, yr = c * xn - s * yn, s * xn + c * yn
+    r2 = (xr * xr + yr * yr) / (((W - 1) / 2 / f) ** 2 + ((H - 1) / 2 / f) ** 2)
+    xd, yd = xr * (1 + k1 * r2), yr * (1 + k1 * r2)
+    mapx = f * xd + (raw_w - 1) / 2 + tx
+    mapy = f * yd + (raw_h - 1) / 2 + ty
+    return mapx.astype(np.float32), mapy.astype(np.float32)

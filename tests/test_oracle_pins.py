@@ -539,3 +539,39 @@ def test_ncc_pipeline_recovers_constant_shift():
     R_img[:, :W - s] = L[:, s:]
     _, dbg = oracle.sgm(L, R_img, D, 5, 5, 90, 880, 8, oracle.FLAG_NCC, debug=True)
     assert np.all(dbg["dl"][:, s + 2:W - D] == s)
+
+
+# ------------------------------------------------------- rectification (Sec. 2.1.1, resampling)
+def test_rectify_identity_shift_and_half_pixel():
+    rng = np.random.default_rng(21)
+    raw = rng.integers(0, 256, (13, 17)).astype(np.uint8)
+    y, x = np.mgrid[0:13, 0:17].astype(np.float32)
+    assert np.array_equal(oracle.rectify(raw, x, y), raw)
+    out = oracle.rectify(raw, x + 3, y - 2)  # integer shift, zeros from outside
+    want = np.zeros_like(raw)
+    want[2:, :14] = raw[:11, 3:]
+    assert np.array_equal(out, want)
+    out = oracle.rectify(raw, x + 0.5, y)  # half-pixel: (a + b + 1) >> 1
+    nxt = np.concatenate([raw[:, 1:], np.zeros((13, 1), np.uint8)], axis=1).astype(int)
+    assert np.array_equal(out, (raw.astype(int) + nxt + 1) >> 1)
+    # non-finite or huge coordinates read 0
+    x2 = x.copy()
+    x2[0, 0], x2[0, 1], x2[0, 2] = np.nan, np.inf, 1e9
+    assert list(oracle.rectify(raw, x2, y)[0, :3]) == [0, 0, 0]
+
+
+def test_rectify_matches_scipy_bilinear_on_the_grid():
+    ndimage = pytest.importorskip("scipy.ndimage")
+    from paper_2106_07927_gb300 import scenes
+    rng = np.random.default_rng(22)
+    H, W = 40, 64
+    raw = rng.integers(0, 256, (H + 6, W + 4)).astype(np.uint8)
+    mapx, mapy = scenes.rectification_maps(3, W, H, W + 4, H + 6, strength=3.0)
+    mapx[5, 5], mapy[7, 9] = -0.7, H + 5.6  # samples straddling the border
+    out = oracle.rectify(raw, mapx, mapy)
+    # the 1/32 grid the definition puts coordinates on, then scipy's exact bilinear value
+    gx = np.rint(mapx.astype(np.float32) * np.float32(32)).astype(np.float64) / 32
+    gy = np.rint(mapy.astype(np.float32) * np.float32(32)).astype(np.float64) / 32
+    ref = ndimage.map_coordinates(raw.astype(np.float64), [gy, gx], order=1,
+                                  mode="grid-constant", cval=0.0)
+    assert np.array_equal(out, np.floor(ref + 0.5).astype(np.uint8))
