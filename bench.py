@@ -323,6 +323,29 @@ def main():
         exact_cc = variant(binding.RES2TAC_EXACT_CC)
         exact_cc["valid_fraction_approximate_check"] = round(
             float((binding.u16(out) != binding.RES2TAC_INVALID).mean()), 4)
+        # rectification of the raw pair (Sec. 2.1.1) in front of the same step, through seeded
+        # calibration-like maps kept in the context
+        rmaps = [torch.from_numpy(m).cuda() for sd in (10, 11)
+                 for m in scenes.rectification_maps(sd, W, H)]
+        binding.res2tac_set_rectification(ctx.handle, *[m.data_ptr() for m in rmaps], 4 * W, W, H,
+                                          sh)
+        raw_ms, raw_st = time_variant(ctx.handle, lambda: binding.res2tac_compute_raw(
+            ctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, out.data_ptr(), 2 * W, sh))
+        rect_only = torch.empty((2, H, W), dtype=torch.uint8, device="cuda")
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record(stream)
+        for _ in range(args.steps):
+            for i, (img, mx, my) in enumerate(((Ld, rmaps[0], rmaps[1]), (Rd, rmaps[2], rmaps[3]))):
+                binding.res2tac_rectify(img.data_ptr(), W, W, H, mx.data_ptr(), my.data_ptr(),
+                                        4 * W, rect_only[i].data_ptr(), W, W, H, sh)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        launches += 2 * args.steps
+        rectify = {"value": round(ws * de / (raw_ms / 1e3) / 1e6, 1), "unit": "MDE/s",
+                   "ms_per_step": round(raw_ms, 4), "stage_ms": raw_st,
+                   "rectify_ms_per_pair": round(r0.elapsed_time(r1) / args.steps, 4),
+                   "maps": "seeded rotation <= 1 deg, shift <= 1.5 px, radial |k1| <= 0.08"}
+
         # NCC matching cost (Sec. 2.2.1), 5 x 5 and 9 x 9 patches, the paper's NCC penalties
         ncc = {f"{n}x{n}": variant(binding.RES2TAC_NCC, census_w=n, census_h=n, p1=90, p2=880)
                for n in (5, 9)}
@@ -436,6 +459,7 @@ def main():
     exact_cc["throughput_vs_integer_step"] = round(mean_ms / exact_cc["ms_per_step"], 3)
     for v in ncc.values():
         v["throughput_vs_census_step"] = round(mean_ms / v["ms_per_step"], 3)
+    rectify["throughput_vs_rectified_input"] = round(mean_ms / rectify["ms_per_step"], 3)
     agg_ms = stage["aggregate"] / args.steps
     # algorithmic operations and bytes of the aggregation per launch (16-bit lane operations):
     # 9 per DE and path (8 of the recurrence, 1 accumulation) + 2 per DE (cost xor/popcount read)
@@ -459,6 +483,7 @@ def main():
         "subpixel": subpixel,
         "exact_cc": exact_cc,
         "ncc": ncc,
+        "rectify": rectify,
         "roofline": {"kernel": "aggregate (SGM paths)", "bound": "alu",
                      "achieved": round(achieved / 1e12, 3),
                      "peak": round(int_peak / 1e12, 3), "unit": "T lane-ops/s",

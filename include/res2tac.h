@@ -157,6 +157,37 @@ int res2tac_compute_subpixel(res2tac_t h, const uint8_t* left, const uint8_t* ri
  * and aggregated volume that call left in the context. Asynchronous on s. */
 int res2tac_debug_subpixel(res2tac_t h, float* dl_sub, res2tac_stream_t s);
 
+/* Rectification (Sec. 2.1.1: the pair is resampled through two maps from the camera calibration
+ * so that epipolar lines lie on image rows; the paper computes the maps with OpenCV). Writes the
+ * width x height image out (device, out_pitch bytes per row) from the raw image raw (device,
+ * raw_w x raw_h, raw_pitch bytes per row) through the float maps mapx / mapy (device, width x
+ * height, map_pitch bytes per row, a multiple of 4; 4-byte aligned), which give for each output
+ * pixel its source coordinate (x right, y down, pixel centres at integers) in the raw image.
+ * Each coordinate is put on a 1/32-pixel grid, X = rint(32 mapx) (ties to even; exact in
+ * float), and the output is the bilinear interpolation with integer weights summing to 1024:
+ *   (I(x0,y0)(32-fx)(32-fy) + I(x0+1,y0) fx(32-fy) + I(x0,y0+1)(32-fx) fy + I(x0+1,y0+1) fx fy
+ *    + 512) >> 10,  x0 = floor(X / 32), fx = X - 32 x0 (y likewise),
+ * where raw pixels outside the image read 0, and a coordinate that is not finite or has
+ * |32 m| >= 2^24 gives 0. Sizes 1 .. 65536. Needs no context. Asynchronous on s. */
+int res2tac_rectify(const uint8_t* raw, int64_t raw_pitch, int32_t raw_w, int32_t raw_h,
+                    const float* mapx, const float* mapy, int64_t map_pitch, uint8_t* out,
+                    int64_t out_pitch, int32_t width, int32_t height, res2tac_stream_t s);
+
+/* Keeps the rectification maps of both cameras in the context (device copies of the W x H maps
+ * mapx_l, mapy_l, mapx_r, mapy_r, map_pitch bytes per row, for raw images of raw_w x raw_h) for
+ * res2tac_compute_raw. The first call allocates 16 B per pixel (not during stream capture); later
+ * calls overwrite. The copies run on s: the caller's maps must stay valid until s has done them. */
+int res2tac_set_rectification(res2tac_t h, const float* mapx_l, const float* mapy_l,
+                              const float* mapx_r, const float* mapy_r, int64_t map_pitch,
+                              int32_t raw_w, int32_t raw_h, res2tac_stream_t s);
+
+/* res2tac_compute on a raw pair (device, raw_w x raw_h as set by res2tac_set_rectification,
+ * raw_pitch bytes per row): rectifies both images into the context's staging (one launch) and
+ * runs the pipeline on them. RES2TAC_EINVAL without maps. Asynchronous on s. */
+int res2tac_compute_raw(res2tac_t h, const uint8_t* raw_left, const uint8_t* raw_right,
+                        int64_t raw_pitch, uint16_t* disp, int64_t out_pitch,
+                        res2tac_stream_t s);
+
 /* Runs n independent pairs of uneven sizes as one batch on stream s (the paper processes one
  * pair at a time, Sec. 2.2; batching is this library's addition). The batch runs as persistent
  * kernels fed by a device work queue over all pairs, recorded once into a CUDA graph and

@@ -33,6 +33,7 @@ EXPORTS = (
     "res2tac_batch_reserve",
     "res2tac_compute_static",
     "res2tac_compute_subpixel", "res2tac_debug_subpixel",
+    "res2tac_rectify", "res2tac_set_rectification", "res2tac_compute_raw",
 )
 RES2TAC_STATIC_SCRATCH_BYTES = 80 << 20
 STAGES = ("census_cost", "aggregate", "wta_dr", "lr_median")
@@ -106,6 +107,9 @@ def load():
         "res2tac_compute_static": (ctypes.c_int, [PP, P, P, I64, P, I64, P]),
         "res2tac_compute_subpixel": (ctypes.c_int, [P, P, P, I64, P, I64, P]),
         "res2tac_debug_subpixel": (ctypes.c_int, [P, P, P]),
+        "res2tac_rectify": (ctypes.c_int, [P, I64, I32, I32, P, P, I64, P, I64, I32, I32, P]),
+        "res2tac_set_rectification": (ctypes.c_int, [P, P, P, P, P, I64, I32, I32, P]),
+        "res2tac_compute_raw": (ctypes.c_int, [P, P, P, I64, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -153,6 +157,24 @@ def res2tac_compute_subpixel(h: int, left: int, right: int, in_pitch: int, disp:
                              out_pitch: int, stream: int = 0) -> None:
     """Pipeline with sub-pixel refinement; disp is a device float map (+inf = invalid)."""
     _check(load().res2tac_compute_subpixel(h, left, right, in_pitch, disp, out_pitch, stream))
+
+
+def res2tac_rectify(raw: int, raw_pitch: int, raw_w: int, raw_h: int, mapx: int, mapy: int,
+                    map_pitch: int, out: int, out_pitch: int, width: int, height: int,
+                    stream: int = 0) -> None:
+    _check(load().res2tac_rectify(raw, raw_pitch, raw_w, raw_h, mapx, mapy, map_pitch, out,
+                                  out_pitch, width, height, stream))
+
+
+def res2tac_set_rectification(h: int, mapx_l: int, mapy_l: int, mapx_r: int, mapy_r: int,
+                              map_pitch: int, raw_w: int, raw_h: int, stream: int = 0) -> None:
+    _check(load().res2tac_set_rectification(h, mapx_l, mapy_l, mapx_r, mapy_r, map_pitch, raw_w,
+                                            raw_h, stream))
+
+
+def res2tac_compute_raw(h: int, raw_left: int, raw_right: int, raw_pitch: int, disp: int,
+                        out_pitch: int, stream: int = 0) -> None:
+    _check(load().res2tac_compute_raw(h, raw_left, raw_right, raw_pitch, disp, out_pitch, stream))
 
 
 def res2tac_debug_subpixel(h: int, dl_sub: int, stream: int = 0) -> None:

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libres2tac.so")
 UNITS = ("abi.cu", "kernels_plain.cu", "kernels_batch.cu", "noalloc.cu", "agg_rows_narrow.cu",
-         "agg_rows_wide.cu", "agg_shear_narrow.cu", "agg_shear_wide.cu", "ncc.cu")
+         "agg_rows_wide.cu", "agg_shear_narrow.cu", "agg_shear_wide.cu", "ncc.cu", "rectify.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

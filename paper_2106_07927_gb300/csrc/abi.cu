@@ -88,6 +88,8 @@ struct res2tac_ctx {
   char* scratch;       // per-pair scratch of the context's own shape
   uint8_t* stage_in;   // device staging of res2tac_compute_host: left, right (pitch W)
   uint16_t* stage_out; // device staging of the output map (pitch 2W bytes)
+  float* maps;         // rectification maps mapx_l, mapy_l, mapx_r, mapy_r (W x H each), or NULL
+  int raw_w, raw_h;    // raw image size the maps sample
   int last_launches;
   r2t::BatchEngine* batch;
   int profiling;
@@ -161,6 +163,7 @@ void res2tac_destroy(res2tac_t h) {
   cudaFree(h->scratch);
   cudaFree(h->stage_in);
   cudaFree(h->stage_out);
+  cudaFree(h->maps);
   if (cur >= 0 && cur != h->device) cudaSetDevice(cur);
   delete h;
 }
@@ -215,6 +218,76 @@ int res2tac_compute_host(res2tac_t h, const uint8_t* left, const uint8_t* right,
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail_cuda(e, "res2tac_compute_host download");
   return RES2TAC_OK;
+}
+
+int res2tac_rectify(const uint8_t* raw, int64_t raw_pitch, int32_t raw_w, int32_t raw_h,
+                    const float* mapx, const float* mapy, int64_t map_pitch, uint8_t* out,
+                    int64_t out_pitch, int32_t width, int32_t height, res2tac_stream_t s) {
+  if (!raw || !mapx || !mapy || !out) return fail(RES2TAC_EINVAL, "NULL pointer");
+  if (raw_w < 1 || raw_h < 1 || width < 1 || height < 1 || raw_w > 65536 || raw_h > 65536 ||
+      width > 65536 || height > 65536)
+    return fail(RES2TAC_EINVAL, "image sizes must be 1 .. 65536");
+  if (raw_pitch < raw_w || out_pitch < width || map_pitch < 4 * (int64_t)width || (map_pitch & 3) ||
+      (reinterpret_cast<uintptr_t>(mapx) & 3) || (reinterpret_cast<uintptr_t>(mapy) & 3))
+    return fail(RES2TAC_EINVAL, "bad pitch or map alignment");
+  r2t::RectifyJob j{raw, raw_pitch, raw_w, raw_h, mapx, mapy, map_pitch, out, out_pitch, width,
+                    height};
+  cudaError_t e = r2t::launch_rectify(&j, 1, (cudaStream_t)s);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_rectify launch");
+  return RES2TAC_OK;
+}
+
+int res2tac_set_rectification(res2tac_t h, const float* mapx_l, const float* mapy_l,
+                              const float* mapx_r, const float* mapy_r, int64_t map_pitch,
+                              int32_t raw_w, int32_t raw_h, res2tac_stream_t s) {
+  if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
+  if (!mapx_l || !mapy_l || !mapx_r || !mapy_r) return fail(RES2TAC_EINVAL, "NULL map");
+  const int W = h->p.width, H = h->p.height;
+  if (raw_w < 1 || raw_h < 1 || raw_w > 65536 || raw_h > 65536)
+    return fail(RES2TAC_EINVAL, "raw size must be 1 .. 65536");
+  if (map_pitch < 4 * (int64_t)W || (map_pitch & 3)) return fail(RES2TAC_EINVAL, "bad map pitch");
+  const size_t plane = (size_t)W * H * 4;
+  if (!h->maps) {
+    cudaError_t e = cudaMalloc(&h->maps, 4 * plane);
+    if (e != cudaSuccess) {
+      h->maps = nullptr;
+      cudaGetLastError();
+      return fail(RES2TAC_ENOMEM, "rectification maps of %zu bytes could not be allocated",
+                  4 * plane);
+    }
+  }
+  const float* src[4] = {mapx_l, mapy_l, mapx_r, mapy_r};
+  for (int i = 0; i < 4; i++) {
+    cudaError_t e = cudaMemcpy2DAsync(reinterpret_cast<uint8_t*>(h->maps) + i * plane, 4 * (size_t)W,
+                                      src[i], (size_t)map_pitch, 4 * (size_t)W, H,
+                                      cudaMemcpyDeviceToDevice, (cudaStream_t)s);
+    if (e != cudaSuccess) return fail_cuda(e, "res2tac_set_rectification copy");
+  }
+  h->raw_w = raw_w;
+  h->raw_h = raw_h;
+  return RES2TAC_OK;
+}
+
+int res2tac_compute_raw(res2tac_t h, const uint8_t* raw_left, const uint8_t* raw_right,
+                        int64_t raw_pitch, uint16_t* disp, int64_t out_pitch,
+                        res2tac_stream_t s) {
+  if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
+  if (!h->maps) return fail(RES2TAC_EINVAL, "no rectification maps: call res2tac_set_rectification");
+  if (!raw_left || !raw_right) return fail(RES2TAC_EINVAL, "NULL raw image");
+  if (raw_pitch < h->raw_w) return fail(RES2TAC_EINVAL, "raw_pitch < raw width");
+  const int W = h->p.width, H = h->p.height;
+  const size_t plane = (size_t)W * H;
+  const float* m = h->maps;
+  r2t::RectifyJob j[2] = {
+      {raw_left, raw_pitch, h->raw_w, h->raw_h, m, m + plane, 4 * (int64_t)W, h->stage_in, W, W,
+       H},
+      {raw_right, raw_pitch, h->raw_w, h->raw_h, m + 2 * plane, m + 3 * plane, 4 * (int64_t)W,
+       h->stage_in + plane, W, W, H}};
+  cudaError_t e = r2t::launch_rectify(j, 2, (cudaStream_t)s);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_compute_raw rectification");
+  int rc = res2tac_compute(h, h->stage_in, h->stage_in + plane, W, disp, out_pitch, s);
+  if (rc == RES2TAC_OK) h->last_launches += 1;
+  return rc;
 }
 
 int res2tac_compute_subpixel(res2tac_t h, const uint8_t* left, const uint8_t* right,

@@ -62,6 +62,22 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
 // of both images, then the cost volume with the clearing of the aggregated sums; 3 launches.
 cudaError_t launch_ncc_cost(const Problem& pb, const Method& mt, cudaStream_t s);
 
+// One image to rectify: raw rw x rh (raw_pitch bytes per row) through float maps of W x H
+// (map_pitch bytes per row) into out (out_pitch bytes per row).
+struct RectifyJob {
+  const uint8_t* raw;
+  int64_t raw_pitch;
+  int rw, rh;
+  const float* mapx;
+  const float* mapy;
+  int64_t map_pitch;
+  uint8_t* out;
+  int64_t out_pitch;
+  int W, H;
+};
+// Rectifies n (1 or 2) images in one launch.
+cudaError_t launch_rectify(const RectifyJob* jobs, int n, cudaStream_t s);
+
 // Sets the calling thread's res2tac_last_error message; returns code.
 int report_error(int code, const char* msg);
 
