@@ -282,7 +282,8 @@ def rectification_maps(seed: int, W: int, H: int, raw_w: int | None = None,
     xn, yn = (u - (W - 1) / 2) / f, (v - (H - 1) / 2) / f
     c, s = np.cos(theta), np.sin(theta)
     xr, yr = c * xn - s * yn, s * xn + c * yn
-    r2 = (xr * xr + yr * yr) / (((W - 1) / 2 / f) ** 2 + ((H - 1) / 2 / f) ** 2)
+    corner2 = max(((W - 1) / 2 / f) ** 2 + ((H - 1) / 2 / f) ** 2, 1e-12)
+    r2 = (xr * xr + yr * yr) / corner2
     xd, yd = xr * (1 + k1 * r2), yr * (1 + k1 * r2)
     mapx = f * xd + (raw_w - 1) / 2 + tx
     mapy = f * yd + (raw_h - 1) / 2 + ty
