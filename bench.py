@@ -329,8 +329,9 @@ def main():
                  for m in scenes.rectification_maps(sd, W, H)]
         binding.res2tac_set_rectification(ctx.handle, *[m.data_ptr() for m in rmaps], 4 * W, W, H,
                                           sh)
+        outr = torch.empty((H, W), dtype=torch.int16, device="cuda")  # keeps `out` for e2e
         raw_ms, raw_st = time_variant(ctx.handle, lambda: binding.res2tac_compute_raw(
-            ctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, out.data_ptr(), 2 * W, sh))
+            ctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, outr.data_ptr(), 2 * W, sh))
         rect_only = torch.empty((2, H, W), dtype=torch.uint8, device="cuda")
         r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         r0.record(stream)

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, c
     if (item >= total) break;
     const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
-    wta_dr_tile<WIDE>(pb, item - prefix[p], wkeys, 256);
+    wta_dr_tile<WIDE, 1>(pb, item - prefix[p], wkeys, 256);
   }
 }
 

@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(256) cost_kernel(Problem pb, Method mt) {
 template <bool WIDE>
 __global__ void __launch_bounds__(256) wta_dr_kernel(Problem pb, int T) {
   extern __shared__ __align__(16) uint32_t wkeys[];
-  wta_dr_tile<WIDE>(pb, blockIdx.x, wkeys, T);
+  wta_dr_tile<WIDE, 4>(pb, blockIdx.x, wkeys, T);
 }
 
 template <bool SUB, bool WIDE>

@@ -111,7 +111,7 @@ __device__ __forceinline__ float refine_subpixel(const Problem& pb, int64_t p, i
 // One tile of T pixels of a row, 256 threads: warp w takes pixels w, w + 8, ..., PF at a time so
 // that their loads are in flight together. Targets whose sources all lie in the tile are then
 // stored, the others (at most D - 1 per tile side) merged with a global atomicMin.
-template <bool WIDE, int NDL, bool EXACT>
+template <bool WIDE, int NDL, bool EXACT, int PFMAX>
 __device__ __forceinline__ void wta_dr_tile_t(const Problem& pb, int item, uint32_t* keys, int T) {
   const int W = pb.W, D = pb.D;
   const int ntx = (W + T - 1) / T;
@@ -122,7 +122,8 @@ __device__ __forceinline__ void wta_dr_tile_t(const Problem& pb, int item, uint3
   for (int i = threadIdx.x; i < ntar; i += blockDim.x) keys[i] = 0xFFFFFFFFu;
   __syncthreads();
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  constexpr int PF = NDL <= 4 ? 4 : 2;  // pixels whose loads are in flight together
+  // pixels whose loads are in flight together (at most PFMAX)
+  constexpr int PF = (NDL <= 4 ? 4 : 2) < PFMAX ? (NDL <= 4 ? 4 : 2) : PFMAX;
   for (int px = threadIdx.x >> 5; px < n; px += PF * nw) {
     uint32_t sv[PF][NDL];
 #pragma unroll
@@ -150,26 +151,28 @@ __device__ __forceinline__ void wta_dr_tile_t(const Problem& pb, int item, uint3
   __syncthreads();
 }
 
-template <bool WIDE, int NDL>
+template <bool WIDE, int NDL, int PFMAX>
 __device__ __forceinline__ void wta_dr_tile_n(const Problem& pb, int item, uint32_t* keys, int T) {
   if (pb.D == 32 * NDL)
-    wta_dr_tile_t<WIDE, NDL, true>(pb, item, keys, T);
+    wta_dr_tile_t<WIDE, NDL, true, PFMAX>(pb, item, keys, T);
   else
-    wta_dr_tile_t<WIDE, NDL, false>(pb, item, keys, T);
+    wta_dr_tile_t<WIDE, NDL, false, PFMAX>(pb, item, keys, T);
 }
 
-// T pixels of a row (T = 64, 128 or 256), 256 threads, T + D - 1 keys of shared memory.
-template <bool WIDE>
+// T pixels of a row (T = 64, 128 or 256), 256 threads, T + D - 1 keys of shared memory. PFMAX
+// caps the pixels a warp loads at once (4 for the single-pair kernel; the persistent batch kernel,
+// measured, prefers 1).
+template <bool WIDE, int PFMAX>
 __device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint32_t* keys, int T) {
   switch ((pb.D + 31) / 32) {
-    case 1: wta_dr_tile_n<WIDE, 1>(pb, item, keys, T); break;
-    case 2: wta_dr_tile_n<WIDE, 2>(pb, item, keys, T); break;
-    case 3: wta_dr_tile_n<WIDE, 3>(pb, item, keys, T); break;
-    case 4: wta_dr_tile_n<WIDE, 4>(pb, item, keys, T); break;
-    case 5: wta_dr_tile_n<WIDE, 5>(pb, item, keys, T); break;
-    case 6: wta_dr_tile_n<WIDE, 6>(pb, item, keys, T); break;
-    case 7: wta_dr_tile_n<WIDE, 7>(pb, item, keys, T); break;
-    default: wta_dr_tile_n<WIDE, 8>(pb, item, keys, T); break;
+    case 1: wta_dr_tile_n<WIDE, 1, PFMAX>(pb, item, keys, T); break;
+    case 2: wta_dr_tile_n<WIDE, 2, PFMAX>(pb, item, keys, T); break;
+    case 3: wta_dr_tile_n<WIDE, 3, PFMAX>(pb, item, keys, T); break;
+    case 4: wta_dr_tile_n<WIDE, 4, PFMAX>(pb, item, keys, T); break;
+    case 5: wta_dr_tile_n<WIDE, 5, PFMAX>(pb, item, keys, T); break;
+    case 6: wta_dr_tile_n<WIDE, 6, PFMAX>(pb, item, keys, T); break;
+    case 7: wta_dr_tile_n<WIDE, 7, PFMAX>(pb, item, keys, T); break;
+    default: wta_dr_tile_n<WIDE, 8, PFMAX>(pb, item, keys, T); break;
   }
 }
 
