@@ -61,10 +61,8 @@ def _traffic():
 
 
 def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2106_07927_gb300 import replicas
+    return replicas.env()
 
 
 def _cpu_info():
@@ -203,17 +201,12 @@ def main():
     __graft_entry__.build()
     from paper_2106_07927_gb300 import binding, scenes
 
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
+    from paper_2106_07927_gb300 import replicas
+    max_over_ranks = replicas.max_over_ranks
 
-    def max_over_ranks(v):
-        if ws == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    def barrier():
+        replicas.barrier()
+        torch.cuda.synchronize()
 
     left, right, _, prm = scenes.single_pair(WORKLOAD, 0)
     W, H, D = prm["width"], prm["height"], prm["max_disp"]
