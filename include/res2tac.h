@@ -129,9 +129,11 @@ int res2tac_compute(res2tac_t h, const uint8_t* left, const uint8_t* right, int6
                     uint16_t* disp, int64_t out_pitch, res2tac_stream_t s);
 
 /* Same pipeline on HOST buffers, end to end as the paper times it (upload, compute, download;
- * Sec. 3.3): copies left/right (host, in_pitch bytes per row) into the context's device
- * staging, runs res2tac_compute on s, copies the map back into disp (host, out_pitch bytes per
- * row) and synchronises s before returning. Pinned host memory makes the copies faster. */
+ * Sec. 3.3): left/right (host, in_pitch bytes per row) in, the map into disp (host, out_pitch
+ * bytes per row), s synchronised before returning. When all three buffers are pinned host memory
+ * the GPU can address (cudaHostAlloc / cudaHostRegister; on a Grace system they are reached over
+ * NVLink-C2C), the kernels read the images and write the map in place; otherwise the images are
+ * copied into the context's device staging and the map copied back. */
 int res2tac_compute_host(res2tac_t h, const uint8_t* left, const uint8_t* right,
                          int64_t in_pitch, uint16_t* disp, int64_t out_pitch,
                          res2tac_stream_t s);

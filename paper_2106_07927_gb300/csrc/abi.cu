@@ -198,6 +198,17 @@ int res2tac_compute(res2tac_t h, const uint8_t* left, const uint8_t* right, int6
   return RES2TAC_OK;
 }
 
+// Device address of a host buffer the GPU can read and write in place (pinned, mapped host
+// memory: over NVLink-C2C on a Grace system), or NULL for memory that needs a copy.
+static void* device_alias(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 int res2tac_compute_host(res2tac_t h, const uint8_t* left, const uint8_t* right,
                          int64_t in_pitch, uint16_t* disp, int64_t out_pitch,
                          res2tac_stream_t s) {
@@ -205,6 +216,21 @@ int res2tac_compute_host(res2tac_t h, const uint8_t* left, const uint8_t* right,
   if (rc) return rc;
   const int W = h->p.width, H = h->p.height;
   cudaStream_t st = (cudaStream_t)s;
+  {
+    // pinned host buffers: the kernels read the images and write the map in place, so the
+    // transfers overlap the computation instead of running as separate copies
+    const void* al = device_alias(left);
+    const void* ar = device_alias(right);
+    void* ad = device_alias(disp);
+    if (al && ar && ad) {
+      rc = res2tac_compute(h, static_cast<const uint8_t*>(al), static_cast<const uint8_t*>(ar),
+                           in_pitch, static_cast<uint16_t*>(ad), out_pitch, s);
+      if (rc) return rc;
+      cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return fail_cuda(e, "res2tac_compute_host");
+      return RES2TAC_OK;
+    }
+  }
   uint8_t* dl = h->stage_in;
   uint8_t* dr = h->stage_in + (size_t)W * H;
   cudaError_t e = cudaMemcpy2DAsync(dl, W, left, in_pitch, W, H, cudaMemcpyHostToDevice, st);

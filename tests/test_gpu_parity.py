@@ -154,6 +154,14 @@ def test_repeatable_and_host_path():
                                  host_out.ctypes.data, 2 * prm["width"], 0)
     assert np.array_equal(host_out, binding.u16(a))
     assert binding.res2tac_last_launch_count(st.handle) == 5
+    # pinned host buffers: read and written in place by the kernels
+    hl = torch.from_numpy(left).pin_memory()
+    hr = torch.from_numpy(right).pin_memory()
+    ho = torch.full((prm["height"], prm["width"]), 0x4321, dtype=torch.int16).pin_memory()
+    binding.res2tac_compute_host(st.handle, hl.data_ptr(), hr.data_ptr(), prm["width"],
+                                 ho.data_ptr(), 2 * prm["width"], 0)
+    assert np.array_equal(ho.numpy().view(np.uint16), binding.u16(a))
+    assert binding.res2tac_last_launch_count(st.handle) == 5
     st.close()
 
 
