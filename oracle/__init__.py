@@ -63,13 +63,15 @@ def _load():
         lib.r2o_cost_right.argtypes = [P, P, I, I, I, P]
         lib.r2o_ncc_cost.argtypes = [P, P, I64, I, I, I, I, P]
         lib.r2o_rectify.argtypes = [P, I64, I, I, P, P, I64, I, I, P, I64]
+        lib.r2o_s_at.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, I, P]
         lib.r2o_ncc_cost_right.argtypes = [P, P, I64, I, I, I, I, P]
         lib.r2o_median3x3_f64.argtypes = [P, I, I, P]
         lib.r2o_sgm_subpixel.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, P, P]
         for f in (lib.r2o_census, lib.r2o_cost, lib.r2o_path, lib.r2o_aggregate, lib.r2o_wta,
                   lib.r2o_right_disparity, lib.r2o_lr_check, lib.r2o_median3x3, lib.r2o_sgm,
                   lib.r2o_subpixel, lib.r2o_median3x3_f64, lib.r2o_sgm_subpixel,
-                  lib.r2o_cost_right, lib.r2o_ncc_cost, lib.r2o_ncc_cost_right, lib.r2o_rectify):
+                  lib.r2o_cost_right, lib.r2o_ncc_cost, lib.r2o_ncc_cost_right, lib.r2o_rectify,
+                  lib.r2o_s_at):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -244,4 +246,16 @@ def rectify(raw: np.ndarray, mapx: np.ndarray, mapy: np.ndarray) -> np.ndarray:
     out = np.empty((H, W), np.uint8)
     _check(_load().r2o_rectify(_ptr(raw), rw, rw, rh, _ptr(mapx), _ptr(mapy), 4 * W, W, H,
                                _ptr(out), W), "rectify")
+    return out
+
+
+def s_at(left: np.ndarray, right: np.ndarray, D: int, census_w: int, census_h: int, P1: int,
+         P2: int, num_paths: int, flags: int, x: int, y: int) -> np.ndarray:
+    """S(x, y, .) (uint16, saturated) from the path lines through one pixel."""
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    right = np.ascontiguousarray(right, dtype=np.uint8)
+    H, W = left.shape
+    out = np.empty(D, np.uint16)
+    _check(_load().r2o_s_at(_ptr(left), _ptr(right), W, W, H, D, census_w, census_h, P1, P2,
+                            num_paths, flags, x, y, _ptr(out)), "s_at")
     return out

@@ -32,6 +32,9 @@
  *                       s = 1 - max(0, Phi) with Phi the zero-mean NCC of the n x n patches
  *                       around (x, y) in the reference and (x -/+ d, y) in the matching image
  *                       (zero margin as for the census), scaled to 0..255 (see the function).
+ *   r2o_s_at            S(p, .) at one pixel from the R path lines through it (each walked from
+ *                       the pixel where it enters the image, costs computed on the way): the same
+ *                       sums as r2o_aggregate, for sampled checks of images too large for it.
  *   r2o_rectify         rectification (Sec. 2.1.1: the pair is resampled through two maps so
  *                       that epipolar lines lie on image rows): bilinear interpolation of the raw
  *                       image at the map's source coordinate, on a 1/32-pixel grid with integer
@@ -621,5 +624,70 @@ int r2o_rectify(const uint8_t* raw, int64_t raw_pitch, int rw, int rh, const flo
       }
       out[(int64_t)y * out_pitch + x] = (uint8_t)v;
     }
+  return 0;
+}
+
+/* Census descriptor of one pixel (the definition of r2o_census). */
+static uint64_t census_px(const uint8_t* img, int64_t pitch, int W, int H, int cw, int ch, int x,
+                          int y) {
+  int rx = cw / 2, ry = ch / 2, centre = img[(int64_t)y * pitch + x], k = 0;
+  uint64_t bits = 0;
+  for (int j = -ry; j <= ry; j++)
+    for (int i = -rx; i <= rx; i++) {
+      if (i == 0 && j == 0) continue;
+      if (px_or_zero(img, pitch, W, H, x + i, y + j) < centre) bits |= (uint64_t)1 << k;
+      k++;
+    }
+  return bits;
+}
+
+/* Aggregated sums at the single pixel (x, y): for each of the first R directions r, the line of
+ * pixels p_0, p_1, .., p_k = (x, y) with p_{i+1} = p_i + r and p_0 where the line enters the image;
+ * L(p_0, .) = C(p_0, .), then the recurrence of r2o_path along the line. out[d] = min(65535,
+ * sum_r L_r(x, y, d)). flags bit 3 selects the NCC cost over a cw x cw patch, as in r2o_sgm. */
+int r2o_s_at(const uint8_t* left, const uint8_t* right, int64_t pitch, int W, int H, int D,
+             int cw, int ch, int P1, int P2, int R, int flags, int x, int y, uint16_t* out) {
+  if (!left || !right || !out || x < 0 || x >= W || y < 0 || y >= H || D < 1 || D > 256) return -1;
+  if ((R != 4 && R != 8) || P1 < 0 || P2 < P1 || P2 > 16384) return -1;
+  static const int dirs[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1},
+                                 {1, 1}, {-1, 1}, {1, -1}, {-1, -1}};
+  int32_t sum[256] = {0};
+  int Lq[256], Lp[256], C[256];
+  for (int r = 0; r < R; r++) {
+    int dx = dirs[r][0], dy = dirs[r][1];
+    int k = 0;  /* steps back to the entry pixel */
+    while (x - (k + 1) * dx >= 0 && x - (k + 1) * dx < W && y - (k + 1) * dy >= 0 &&
+           y - (k + 1) * dy < H)
+      k++;
+    for (int i = 0; i <= k; i++) {
+      int px = x - (k - i) * dx, py = y - (k - i) * dy;
+      if (flags & 8) {
+        for (int d = 0; d < D; d++)
+          C[d] = px - d < 0 ? 255 : ncc_pair_cost(left, right, pitch, W, H, px, px - d, py, cw);
+      } else {
+        uint64_t cl = census_px(left, pitch, W, H, cw, ch, px, py);
+        for (int d = 0; d < D; d++)
+          C[d] = px - d < 0 ? 255
+                            : popcount64(cl ^ census_px(right, pitch, W, H, cw, ch, px - d, py));
+      }
+      if (i == 0) {
+        for (int d = 0; d < D; d++) Lp[d] = C[d];
+      } else {
+        int m = Lq[0];
+        for (int d = 1; d < D; d++)
+          if (Lq[d] < m) m = Lq[d];
+        for (int d = 0; d < D; d++) {
+          int best = Lq[d];
+          if (d > 0 && Lq[d - 1] + P1 < best) best = Lq[d - 1] + P1;
+          if (d < D - 1 && Lq[d + 1] + P1 < best) best = Lq[d + 1] + P1;
+          if (m + P2 < best) best = m + P2;
+          Lp[d] = C[d] + best - m;
+        }
+      }
+      memcpy(Lq, Lp, sizeof(int) * D);
+    }
+    for (int d = 0; d < D; d++) sum[d] += Lq[d];
+  }
+  for (int d = 0; d < D; d++) out[d] = (uint16_t)(sum[d] > 65535 ? 65535 : sum[d]);
   return 0;
 }

@@ -575,3 +575,18 @@ def test_rectify_matches_scipy_bilinear_on_the_grid():
     ref = ndimage.map_coordinates(raw.astype(np.float64), [gy, gx], order=1,
                                   mode="grid-constant", cval=0.0)
     assert np.array_equal(out, np.floor(ref + 0.5).astype(np.uint8))
+
+
+# ------------------------------------------------- sums at single pixels (sampled full-size checks)
+@pytest.mark.parametrize("cw,ch,R,flags,P2", [(5, 5, 4, 0, 120), (9, 7, 8, 0, 120),
+                                              (5, 5, 8, 8, 880), (9, 7, 8, 0, 16384)])
+def test_s_at_equals_full_aggregation(cw, ch, R, flags, P2):
+    rng = np.random.default_rng(33)
+    H, W, D = 13, 29, 32
+    L = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    Rm = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    _, dbg = oracle.sgm(L, Rm, D, cw, ch, 10, P2, R, flags, debug=True)
+    for y in range(H):
+        for x in range(W):
+            assert np.array_equal(oracle.s_at(L, Rm, D, cw, ch, 10, P2, R, flags, x, y),
+                                  dbg["agg"][y, x]), (x, y)
