@@ -295,3 +295,38 @@ def test_ncc_launches_and_rejections():
     st.close()
     with pytest.raises(binding.Res2tacError):  # 9 x 7 is a census window, not an NCC patch
         binding.Stereo(dict(prm, census_w=9, census_h=7, flags=NCC))
+
+
+# ----------------------------------------------------------------------------- maximum sizes
+@pytest.mark.parametrize("W,H", [(16384, 12), (12, 16384)])
+def test_maximum_width_and_height(W, H):
+    rng = np.random.default_rng(W + H)
+    left = rng.integers(0, 256, (H, W)).astype(np.uint8)
+    right = np.roll(left, 9, axis=1)
+    right[:, :9] = rng.integers(0, 256, (H, 9))
+    _assert_same(left, right, scenes.params(W, H, 64, 5, 5, 10, 120, 8, 3))
+
+
+def test_3840x2160_d256_sampled_sums():
+    # the largest pair of the serving workload: the aggregated sums at sampled pixels (corners,
+    # borders, interior) from the oracle's walk along the 8 path lines through each of them
+    import torch
+    W, H, D = 3840, 2160, 256
+    left, right, _ = scenes.make_scene("road", 5, W, H, D)
+    prm = scenes.params(W, H, D, 9, 7, 10, 120, 8, 3)
+    st = binding.Stereo(prm)
+    st.compute(torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda())
+    dbg = st.debug_outputs()
+    rng = np.random.default_rng(6)
+    pts = [(0, 0), (W - 1, 0), (0, H - 1), (W - 1, H - 1), (W // 2, H // 2), (D - 1, 7)]
+    pts += [(int(rng.integers(0, W)), int(rng.integers(0, H))) for _ in range(10)]
+    xs = torch.tensor([p[0] for p in pts], device="cuda")
+    ys = torch.tensor([p[1] for p in pts], device="cuda")
+    agg = binding.u16(dbg["agg"][ys, xs])
+    dl = binding.u16(dbg["dl"][ys, xs])
+    del dbg
+    st.close()
+    for i, (x, y) in enumerate(pts):
+        want = oracle.s_at(left, right, D, 9, 7, 10, 120, 8, 0, x, y)
+        assert np.array_equal(agg[i], want), (x, y)
+        assert dl[i] == int(np.argmin(want)), (x, y)
