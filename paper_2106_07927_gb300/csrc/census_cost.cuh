@@ -45,12 +45,12 @@ __device__ __forceinline__ uint64_t census_at(const uint8_t (*rows)[kImgW], int 
       constexpr int centre = RY * CW + RX;
       const int n = j * CW + ii;  // window position, compile time after unrolling
       if (n == centre) continue;
-      const int k = n < centre ? n : n - 1;                        // bit of this neighbour
-      const uint32_t b = (uint32_t)((int)rows[j][i + ii] - c) >> 31;  // 1 iff darker
+      const int k = n < centre ? n : n - 1;          // bit of this neighbour
+      const uint32_t dlt = (uint32_t)((int)rows[j][i + ii] - c);  // sign bit: 1 iff darker
       if (k >= 32)
-        hi = (hi << 1) | b;
+        hi = __funnelshift_l(dlt, hi, 1);  // (hi << 1) | (dlt >> 31)
       else
-        lo = (lo << 1) | b;
+        lo = __funnelshift_l(dlt, lo, 1);
     }
   }
   return (uint64_t)lo | ((uint64_t)hi << 32);
@@ -63,6 +63,47 @@ __device__ __forceinline__ uint32_t pack_bytes(uint32_t a, uint32_t b, uint32_t 
 template <bool CT64>
 __device__ __forceinline__ uint32_t hamming(uint64_t a, uint64_t b) {
   return CT64 ? (uint32_t)__popcll(a ^ b) : (uint32_t)__popc((uint32_t)a ^ (uint32_t)b);
+}
+
+// The cost words of a tile for D = 4 NQ (NQ dividing 256): thread t computes word q = t % NQ of
+// pixels t / NQ + k 256 / NQ, k = 0 .. kCostTX NQ / 256 - 1, unrolled, so every shared-memory
+// and global offset is a constant from the thread's base. d = 4 q + j reads the right descriptor
+// r index px + D - 1 - 4 q - j (the phase split puts lanes 4 disparities apart on consecutive
+// words). Tiles whose pixels all have x >= D - 1 skip the test for x - d < 0.
+template <bool CT64, int NQ>
+__device__ __forceinline__ void cost_words(const CostSmem& sm, uint32_t* out, int x0, int npx) {
+  constexpr int D = 4 * NQ, STEP = 256 / NQ, ITER = kCostTX / STEP;
+  const int q = threadIdx.x % NQ, px0 = threadIdx.x / NQ;
+  const uint64_t* lp = &sm.l[px0];
+  const uint64_t* rp[4];
+#pragma unroll
+  for (int j = 0; j < 4; j++) {
+    const int i = px0 + D - 1 - 4 * q - j;
+    rp[j] = &sm.r[i & 3][i >> 2];
+  }
+  uint32_t* o = out + px0 * NQ + q;
+  const bool interior = x0 >= D - 1;  // block-uniform
+#pragma unroll
+  for (int it = 0; it < ITER; it++) {
+    const int px = px0 + it * STEP;
+    if (px < npx) {
+      const uint64_t cl = lp[it * STEP];
+      uint32_t v0 = hamming<CT64>(cl, rp[0][it * STEP / 4]);
+      uint32_t v1 = hamming<CT64>(cl, rp[1][it * STEP / 4]);
+      uint32_t v2 = hamming<CT64>(cl, rp[2][it * STEP / 4]);
+      uint32_t v3 = hamming<CT64>(cl, rp[3][it * STEP / 4]);
+      if (!interior) {
+        const int x = x0 + px, dmax = 4 * q + 3;
+        if (x < dmax) {  // x - d < 0: outside the right image
+          v0 = x < dmax - 3 ? kCostOutside : v0;
+          v1 = x < dmax - 2 ? kCostOutside : v1;
+          v2 = x < dmax - 1 ? kCostOutside : v2;
+          v3 = kCostOutside;
+        }
+      }
+      o[it * STEP * NQ] = pack_bytes(v0, v1, v2, v3);
+    }
+  }
 }
 
 // One row segment of kCostTX pixels, all disparities, written as 4-byte words of 4 consecutive
@@ -134,7 +175,15 @@ __device__ __forceinline__ void cost_tile(const Problem& pb, int item, CostSmem&
   __syncthreads();
   const int nq = D / 4;  // 4-disparity words per pixel
   uint32_t* out = reinterpret_cast<uint32_t*>(pb.cost + ((int64_t)y * pb.W + x0) * D);
-  if (256 % nq == 0 && blockDim.x == 256) {
+  if (blockDim.x == 256 && (nq == 4 || nq == 8 || nq == 16 || nq == 32 || nq == 64)) {
+    switch (nq) {
+      case 4: cost_words<CT64, 4>(sm, out, x0, npx); break;
+      case 8: cost_words<CT64, 8>(sm, out, x0, npx); break;
+      case 16: cost_words<CT64, 16>(sm, out, x0, npx); break;
+      case 32: cost_words<CT64, 32>(sm, out, x0, npx); break;
+      default: cost_words<CT64, 64>(sm, out, x0, npx); break;
+    }
+  } else if (256 % nq == 0 && blockDim.x == 256) {
     const int q = threadIdx.x % nq, step = 256 / nq;  // step is a multiple of 4
     int px = threadIdx.x / nq;
     // d = 4 q + j reads r index px + D - 1 - 4 q - j: phase and row offset per j
