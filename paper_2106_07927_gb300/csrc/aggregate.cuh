@@ -441,7 +441,6 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   const int sh = SH0 ? 0 : (kind < 4 ? 1 : -1);
   const bool back = (kind & 1) != 0;
   const int dy = back ? -1 : 1, dx = back ? -sh : sh;
-  const int edge = dx > 0 ? 0 : W - 1;  // (shear != 0) a chain arriving at x == edge restarts
   const int ystart = back ? H - 1 : 0;
   int xs = (j0 + sh * ystart) % W;  // pixel of chain 0 in the current row
   if (xs < 0) xs += W;
@@ -525,13 +524,19 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   };
 
   uint32_t L[CPL][NP], mm[CPL];
-  int x[CPL];  // the lane's chain pixels (meaningful for chains that exist)
+  // steps until the lane's chain g arrives at the edge column again and restarts (a chain at
+  // column x reaches the edge after (W - x) mod W steps going right, (x + 1) mod W going left;
+  // 0 means it starts there, which step 0 does anyway, so the next restart is W steps later)
+  int rs[CPL];
 #pragma unroll
   for (int g = 0; g < CPL; g++) {
 #pragma unroll
     for (int k = 0; k < NP; k++) L[g][k] = owns ? 0u : kSent * 0x10001u;
     mm[g] = 0;
-    x[g] = (xs + c + CPW * g) % W;
+    const int x0 = (xs + c + CPW * g) % W;
+    int r = dx > 0 ? W - x0 : x0 + 1;
+    r = r >= W ? r - W : r;
+    rs[g] = r == 0 ? W : r;
   }
   uint8_t* arun = reinterpret_cast<uint8_t*>(pb.agg) + ((int64_t)ystart * W + xs) * D * BPE;
   uint32_t rslot = ring_s;  // ring slot of the current step
@@ -573,17 +578,21 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
             const unsigned long long r8 = owns ? lds64(cur + rd_s[g][v]) : 0ull;
             raw[g][v] = make_uint4((uint32_t)r8, (uint32_t)(r8 >> 32), 0u, 0u);
           }
-      if (!SH0) {
+      if (!SH0 && t > 0) {
         bool hit = false;
 #pragma unroll
-        for (int g = 0; g < CPL; g++) hit |= x[g] == edge;
+        for (int g = 0; g < CPL; g++) {
+          rs[g]--;
+          hit |= rs[g] == 0;
+        }
         if (__any_sync(0xffffffffu, hit)) {  // a new line of the path enters: L = C
 #pragma unroll
           for (int g = 0; g < CPL; g++) {
-            if (x[g] == edge) {
+            if (rs[g] == 0) {
 #pragma unroll
               for (int k = 0; k < NP; k++) L[g][k] = owns ? 0u : kSent * 0x10001u;
               mm[g] = 0;
+              rs[g] = W;
             }
           }
         }
@@ -681,11 +690,6 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
         } else if (xs < 0) {
           xs += W;
           arun += awrap;
-        }
-#pragma unroll
-        for (int g = 0; g < CPL; g++) {
-          x[g] += dx;
-          x[g] = x[g] >= W ? x[g] - W : (x[g] < 0 ? x[g] + W : x[g]);
         }
       }
     }
