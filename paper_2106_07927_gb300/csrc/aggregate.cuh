@@ -539,6 +539,8 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
     rs[g] = r == 0 ? W : r;
   }
   uint8_t* arun = reinterpret_cast<uint8_t*>(pb.agg) + ((int64_t)ystart * W + xs) * D * BPE;
+  // steps until xs steps out of 0 .. W - 1 (going right: after W - xs steps; left: xs + 1)
+  int xw = dx > 0 ? W - xs : xs + 1;
   uint32_t rslot = ring_s;  // ring slot of the current step
   uint32_t sbuf = stage_s;  // staging buffer of the current step
 
@@ -555,7 +557,8 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
       const int t = t0 + u;
       if (t >= H) break;
       // the bulk add issued two steps ago has read the staging buffer this step refills
-      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+      // (bulk groups are per thread: lanes other than lane 0 have none and pass at once)
+      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
       __syncwarp();  // every lane is done with the ring slot refilled below and with the staging
       if (u == 0) {  // issue steps t + 6, t + 7, then wait for steps t, t + 1
         copy_step(t + KS - 2);
@@ -684,12 +687,10 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
       arun += astride;
       if (!SH0) {
         xs += dx;
-        if (xs >= W) {
-          xs -= W;
-          arun -= awrap;
-        } else if (xs < 0) {
-          xs += W;
-          arun += awrap;
+        if (--xw == 0) {  // chain 0 left the row at one side: back in at the other
+          xs -= dx * W;
+          arun -= dx * awrap;
+          xw = W;
         }
       }
     }
