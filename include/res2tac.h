@@ -32,7 +32,7 @@ extern "C" {
 #define RES2TAC_EINVAL (-1)   /* bad parameter, shape, pitch or NULL pointer */
 #define RES2TAC_ENOMEM (-2)   /* device memory for the scratch could not be allocated */
 #define RES2TAC_ECUDA (-3)    /* a CUDA runtime call or launch failed (message kept) */
-#define RES2TAC_ETIMEOUT (-4) /* a bounded device-side wait of the batch engine gave up */
+#define RES2TAC_ETIMEOUT (-4) /* reserved: a bounded device-side wait gave up (none exists today) */
 
 /* flags */
 #define RES2TAC_LR_CHECK 1 /* approximate left-right consistency check, Eq. (LR_check) */
@@ -196,8 +196,10 @@ int res2tac_compute_raw(res2tac_t h, const uint8_t* raw_left, const uint8_t* raw
  * replayed while the batch layout (n and every pair's W, H, D) stays the same. The context
  * grows its batch scratch when a larger batch arrives: that call allocates and must not be made
  * during stream capture. pairs: host array of n descriptors with device pointers. Results are
- * bit-identical to res2tac_compute on each pair alone. Returns RES2TAC_ETIMEOUT if a bounded
- * device wait of the queue gave up (the outputs are then unspecified). */
+ * bit-identical to res2tac_compute on each pair alone. No block of the engine ever waits for
+ * another (work is claimed with one atomic increment), so there is no device-side wait that
+ * could time out: RES2TAC_ETIMEOUT is reserved and not returned. RES2TAC_EINVAL for an invalid
+ * pair, or for RES2TAC_EXACT_CC / RES2TAC_NCC contexts (single pairs only). */
 int res2tac_compute_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res2tac_stream_t s);
 
 /* Copies the intermediates of the last res2tac_compute on this context into caller buffers

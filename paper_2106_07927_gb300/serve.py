@@ -22,8 +22,11 @@ from . import binding, scenes
 
 
 class Request:
+    """One stereo pair to serve. status: "waiting", then "ok", "cancelled" (cancel() called before
+    the request was admitted; it never reaches the GPU) or "failed: <message>" (its batch was
+    refused by the library; the server carries on with the next batches)."""
     __slots__ = ("idx", "arrival", "W", "H", "D", "left", "right", "out", "done", "stream",
-                 "batch_size", "need")
+                 "batch_size", "need", "status")
 
     def __init__(self, idx, arrival, left, right, W, H, D):
         self.idx, self.arrival = idx, arrival
@@ -34,6 +37,11 @@ class Request:
         self.stream = None
         self.batch_size = 0
         self.need = 0
+        self.status = "waiting"
+
+    def cancel(self):
+        if self.status == "waiting":
+            self.status = "cancelled"
 
 
 def poisson_arrivals(n: int, rate: float, seed: int = 0) -> np.ndarray:
@@ -83,7 +91,13 @@ class Server:
                                                   r.W, r.H, r.D, 0))
                 r.stream = slot
                 r.batch_size = len(batch)
-        binding.res2tac_compute_batch(self.ctx[slot].handle, pairs, st.cuda_stream)
+        try:
+            binding.res2tac_compute_batch(self.ctx[slot].handle, pairs, st.cuda_stream)
+        except binding.Res2tacError as e:  # refused on the host: nothing was launched
+            for r in batch:
+                r.status = f"failed: {e}"
+                r.out = None
+            return None
         self.launches += binding.res2tac_last_launch_count(self.ctx[slot].handle)
         ev = torch.cuda.Event()
         ev.record(st)
@@ -113,33 +127,56 @@ class Server:
                     tdone = time.perf_counter() - t0
                     for r in batch:
                         r.done = tdone
+                        r.status = "ok"
                     done += len(batch)
                     del inflight[slot]
                     free_slots.append(slot)
+            while pending and pending[0].status == "cancelled":  # dropped before admission
+                pending.popleft().done = time.perf_counter() - t0
+                done += 1
             while free_slots and pending:
                 batch, mem = [], 0
                 while pending and len(batch) < self.max_batch and \
                         mem + pending[0].need <= self.per_stream:
                     r = pending.popleft()
+                    if r.status == "cancelled":
+                        r.done = time.perf_counter() - t0
+                        done += 1
+                        continue
                     batch.append(r)
                     mem += r.need
+                if not batch:
+                    continue
                 slot = free_slots.pop()
-                inflight[slot] = (self._launch(slot, batch), batch)
+                ev = self._launch(slot, batch)
+                if ev is None:  # the batch failed: its requests are done, the stream is free
+                    tdone = time.perf_counter() - t0
+                    for r in batch:
+                        r.done = tdone
+                    done += len(batch)
+                    free_slots.append(slot)
+                else:
+                    inflight[slot] = (ev, batch)
         self.torch.cuda.synchronize()
         return summarize(requests)
 
 
 def summarize(requests):
-    lat = np.array([r.done - r.arrival for r in requests]) * 1e3
-    de = sum(r.W * r.H * r.D for r in requests)
-    span = max(r.done for r in requests) - min(r.arrival for r in requests)
+    """Throughput and latency over the requests served ("ok"); counts of the others."""
+    ok = [r for r in requests if r.status == "ok"] or requests[:1]
+    lat = np.array([r.done - r.arrival for r in ok]) * 1e3
+    de = sum(r.W * r.H * r.D for r in ok)
+    span = max(r.done for r in ok) - min(r.arrival for r in ok)
     return {
         "requests": len(requests),
-        "mde_per_s": round(de / span / 1e6, 1),
+        "served": sum(r.status == "ok" for r in requests),
+        "cancelled": sum(r.status == "cancelled" for r in requests),
+        "failed": sum(r.status.startswith("failed") for r in requests),
+        "mde_per_s": round(de / max(span, 1e-9) / 1e6, 1),
         "p50_ms": round(float(np.percentile(lat, 50)), 3),
         "p99_ms": round(float(np.percentile(lat, 99)), 3),
         "p999_ms": round(float(np.percentile(lat, 99.9)), 3),
-        "mean_batch": round(float(np.mean([r.batch_size for r in requests])), 2),
+        "mean_batch": round(float(np.mean([r.batch_size for r in ok])), 2),
         "span_s": round(span, 3),
     }
 

@@ -48,3 +48,38 @@ def test_admission_rejects_request_larger_than_stream_budget():
     with pytest.raises(ValueError):
         srv.run([serve.Request(0, 0.0, L, L, 400, 400, 256)])
     srv.close()
+
+
+@pytest.mark.gpu
+def test_cancelled_and_failed_requests_leave_the_rest_served():
+    # host-side faults: two requests cancelled before admission, one the library refuses (D = 8
+    # is not a valid disparity count); the others are served bit-exactly and the server goes on
+    import torch
+    srv = serve.Server(n_streams=2, max_batch=1, budget_bytes=2 * 200_000_000)
+    L, R, _ = scenes.make_scene("road", 3, 120, 60, 64)
+    Ld, Rd = torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()
+    reqs = [serve.Request(i, 0.001 * i, Ld, Rd, 120, 60, 64) for i in range(8)]
+    reqs[2].cancel()
+    reqs[5].cancel()
+    reqs[4].D = 8
+    stats = srv.run(reqs)
+    assert [r.status for r in reqs][:4] == ["ok", "ok", "cancelled", "ok"]
+    assert reqs[4].status.startswith("failed") and reqs[5].status == "cancelled"
+    assert stats["served"] == 5 and stats["cancelled"] == 2 and stats["failed"] == 1
+    ref = oracle.sgm(L, R, 64, 9, 7, 10, 120, 8, 3)
+    for r in reqs:
+        if r.status == "ok":
+            assert np.array_equal(r.out.cpu().numpy().view(np.uint16), ref)
+        else:
+            assert r.out is None
+    srv.close()
+
+
+def test_request_cancel_only_while_waiting():
+    r = serve.Request(0, 0.0, None, None, 8, 8, 16)
+    r.status = "ok"
+    r.cancel()
+    assert r.status == "ok"
+    r = serve.Request(1, 0.0, None, None, 8, 8, 16)
+    r.cancel()
+    assert r.status == "cancelled"
