@@ -14,9 +14,9 @@ __global__ void __launch_bounds__(256) cost_kernel(Problem pb, Method mt) {
 }
 
 template <bool WIDE>
-__global__ void __launch_bounds__(256) wta_dr_kernel(Problem pb, int T) {
-  extern __shared__ __align__(16) uint32_t wkeys[];
-  wta_dr_tile<WIDE, 4>(pb, blockIdx.x, wkeys, T);
+__global__ void __launch_bounds__(256) wta_dr_staged_kernel(Problem pb, int T) {
+  extern __shared__ __align__(16) uint8_t wsm[];
+  wta_dr_staged<WIDE>(pb, blockIdx.x, wsm, T);
 }
 
 template <bool SUB, bool WIDE>
@@ -133,13 +133,19 @@ static cudaError_t run_pass(const Problem& pb, const Method& mt, const Tuning& t
   if (ev) cudaEventRecord(ev[0], s);
   if ((e = launch_aggregate(pb, mt, tn, s, fork)) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
-  const int T = tn.wta_chunk;  // pixels per block of 256 threads
-  const size_t smem = wta_smem_bytes(pb.D, T);
+  // pixels per block of 256 threads, capped so that the staged sums take at most 64 KB
+  const int T = wta_staged_px(pb.D, mt.wide != 0, tn.wta_chunk);
+  const size_t smem = wta_staged_smem_bytes(pb.D, mt.wide != 0, T);
   const int nw = wta_items(pb.W, pb.H, T);
-  if (mt.wide)
-    wta_dr_kernel<true><<<nw, 256, smem, s>>>(pb, T);
-  else
-    wta_dr_kernel<false><<<nw, 256, smem, s>>>(pb, T);
+  if (mt.wide) {
+    cudaFuncSetAttribute(wta_dr_staged_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    wta_dr_staged_kernel<true><<<nw, 256, smem, s>>>(pb, T);
+  } else {
+    cudaFuncSetAttribute(wta_dr_staged_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    wta_dr_staged_kernel<false><<<nw, 256, smem, s>>>(pb, T);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
   *n += 3;

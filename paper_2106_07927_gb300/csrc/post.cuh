@@ -176,6 +176,94 @@ __device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint32_
   }
 }
 
+// The same tile with its sums staged in shared memory first: all 256 threads copy the tile's
+// contiguous run of S (n pixels x D sums) with 16-byte cp.async copies, so the whole tile is in
+// flight at once, then the warps read their pixel vectors from shared memory. T pixels with
+// T * D * bytes-per-sum <= 64 KB (wta_staged_px). Shared memory: the run, then T + D - 1 keys.
+__host__ __device__ inline int wta_staged_px(int D, bool wide, int T) {
+  const int cap = 65536 / (D * (wide ? 4 : 2));
+  return T < cap ? T : cap;
+}
+__host__ __device__ inline size_t wta_staged_smem_bytes(int D, bool wide, int T) {
+  return (size_t)T * D * (wide ? 4 : 2) + (size_t)(T + D - 1) * 4;
+}
+
+template <bool WIDE, int NDL, bool EXACT>
+__device__ __forceinline__ void wta_dr_staged_t(const Problem& pb, int item, uint8_t* smem,
+                                                int T) {
+  constexpr int BPE = WIDE ? 4 : 2;
+  const int W = pb.W, D = EXACT ? 32 * NDL : pb.D;
+  const int ntx = (W + T - 1) / T;
+  const int y = item / ntx, x0 = (item - y * ntx) * T;
+  const int n = min(T, W - x0);
+  const int64_t rowbase = (int64_t)y * W;
+  uint32_t* keys = reinterpret_cast<uint32_t*>(smem + (size_t)T * D * BPE);
+  {
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(pb.agg) + (rowbase + x0) * D * BPE;
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem);
+    const int pieces = n * D * BPE / 16;  // D % 16 == 0
+    for (int i = threadIdx.x; i < pieces; i += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * i),
+                   "l"(src + 16 * (int64_t)i));
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  const int ntar = T + D - 1;  // targets x0 - D + 1 .. x0 + T - 1
+  for (int i = threadIdx.x; i < ntar; i += blockDim.x) keys[i] = 0xFFFFFFFFu;
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int px = threadIdx.x >> 5; px < n; px += nw) {
+    uint32_t sv[NDL];
+#pragma unroll
+    for (int i = 0; i < NDL; i++) {
+      const int d = lane + 32 * i;
+      sv[i] = 0xFFFFu;
+      if (EXACT || d < D) {
+        if (WIDE)
+          sv[i] = min(reinterpret_cast<const uint32_t*>(smem)[px * D + d], 65535u);
+        else
+          sv[i] = reinterpret_cast<const uint16_t*>(smem)[px * D + d];
+      }
+    }
+    wta_keys<NDL, EXACT>(pb, rowbase, x0 + px, px, keys, lane, sv);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < ntar; i += blockDim.x) {
+    const int x = x0 - D + 1 + i;
+    if (x < 0 || x >= x0 + n) continue;
+    const uint32_t k = keys[i];
+    if (k == 0xFFFFFFFFu) continue;
+    const bool whole = x >= x0 && min(x + D - 1, W - 1) < x0 + n;
+    if (whole)
+      pb.kr[rowbase + x] = k;
+    else
+      atomicMin(&pb.kr[rowbase + x], k);
+  }
+}
+
+template <bool WIDE>
+__device__ __forceinline__ void wta_dr_staged(const Problem& pb, int item, uint8_t* smem, int T) {
+#define R2T_WTA_STAGED(N)                                 \
+  case N:                                                 \
+    if (pb.D == 32 * N)                                   \
+      wta_dr_staged_t<WIDE, N, true>(pb, item, smem, T);  \
+    else                                                  \
+      wta_dr_staged_t<WIDE, N, false>(pb, item, smem, T); \
+    break;
+  switch ((pb.D + 31) / 32) {
+    R2T_WTA_STAGED(1)
+    R2T_WTA_STAGED(2)
+    R2T_WTA_STAGED(3)
+    R2T_WTA_STAGED(4)
+    R2T_WTA_STAGED(5)
+    R2T_WTA_STAGED(6)
+    R2T_WTA_STAGED(7)
+    default:
+      R2T_WTA_STAGED(8)
+  }
+#undef R2T_WTA_STAGED
+}
+
 constexpr int kMedTW = 64;  // median tile: 64 x 4 pixels, one per thread
 constexpr int kMedTH = 4;
 __host__ __device__ inline int median_items(int W, int H) {
