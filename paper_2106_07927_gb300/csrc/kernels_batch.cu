@@ -44,18 +44,21 @@ __global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
 }
 
 
+constexpr int kBatchWtaPx = 128;  // pixels per WTA item (staged tiles, at most 64 KB of sums)
+
 template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, const Problem* probs,
                                                         const int* prefix, unsigned* counters) {
-  extern __shared__ __align__(16) uint32_t wkeys[];
+  extern __shared__ __align__(16) uint8_t wsm[];
   __shared__ int s_item;
   const int total = hd->total[kStWta], n = hd->n;
   for (;;) {
+    // (the barrier inside claim_block also ends the previous item's use of the shared memory)
     const int item = claim_block(&counters[kStWta], &s_item);
     if (item >= total) break;
     const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
-    wta_dr_tile<WIDE, 1>(pb, item - prefix[p], wkeys, 256);
+    wta_dr_staged<WIDE>(pb, item - prefix[p], wsm, wta_staged_px(pb.D, WIDE, kBatchWtaPx));
   }
 }
 
@@ -329,9 +332,10 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
     prefix[1 * stride + p] = tot[1];
     prefix[2 * stride + p] = tot[2];
     tot[0] += cost_items(pb.W, pb.H);
-    tot[1] += wta_items(pb.W, pb.H, wta_tile_px(pb.D));
+    const int wt = wta_staged_px(pb.D, mt.wide != 0, kBatchWtaPx);
+    tot[1] += wta_items(pb.W, pb.H, wt);
     tot[2] += median_items(pb.W, pb.H);
-    wta_smem = std::max(wta_smem, (int)wta_smem_bytes(pb.D, wta_tile_px(pb.D)));
+    wta_smem = std::max(wta_smem, (int)wta_staged_smem_bytes(pb.D, mt.wide != 0, wt));
     const int dpl = e->dpl_by_d16[pb.D / 16];
     lk.push_back(Keyed{AggSeg{p, 0, row_units(pb.H, false), 32 / long_lanes(pb.D, dpl)}, pb.W});
     bk.push_back(Keyed{AggSeg{p, 0, shear_items(pb.W, pb.D, 16, mt.num_paths, 1), 1}, pb.H});

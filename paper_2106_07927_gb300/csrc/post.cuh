@@ -1,7 +1,8 @@
 // Disparity selection and post-processing, Sec. 2.1.2 - 2.1.3, as block-level routines.
 //
-// wta_dr_tile: for T consecutive pixels of a row, each pixel's aggregated vector S(x, .) is read
-// once, by one warp with its lanes on consecutive disparities (coalesced loads), and gives
+// wta_dr_staged: for T consecutive pixels of a row, staged in shared memory as one contiguous
+// run, each pixel's aggregated vector S(x, .) is read once, by one warp with its lanes on
+// consecutive disparities, and gives
 //   D^L(x) = smallest d with the least S(x, d)                                  Eq. (wta)
 // as a warp minimum, and its share of
 //   D^R(x) = smallest d <= min(D-1, W-1-x) with the least S(x + d, d)          Eq. (right_disparity)
@@ -29,29 +30,7 @@
 
 namespace r2t {
 
-// Pixels per block of the WTA / right-disparity stage (the block has 256 threads).
-__host__ __device__ inline int wta_tile_px(int D) { return 256; }
-// Shared memory: one key per target pixel of the tile, T + D - 1 of them.
-__host__ __device__ inline size_t wta_smem_bytes(int D, int T) { return (size_t)(T + D - 1) * 4; }
 __host__ __device__ inline int wta_items(int W, int H, int T) { return H * ((W + T - 1) / T); }
-
-// Loads S(x, d) for the disparities d = lane + 32 i (i < NDL) of one pixel vector, saturated to
-// 16 bits (0xFFFF past D; EXACT: D == 32 NDL).
-template <bool WIDE, int NDL, bool EXACT>
-__device__ __forceinline__ void wta_load(const void* agg, int64_t vec, int D, int lane,
-                                         uint32_t (&s)[NDL]) {
-#pragma unroll
-  for (int i = 0; i < NDL; i++) {
-    const int d = lane + 32 * i;
-    s[i] = 0xFFFFu;
-    if (EXACT || d < D) {
-      if (WIDE)
-        s[i] = min(__ldg(reinterpret_cast<const uint32_t*>(agg) + vec + d), 65535u);
-      else
-        s[i] = __ldg(reinterpret_cast<const unsigned short*>(agg) + vec + d);
-    }
-  }
-}
 
 // The keys of one pixel x (tile position px): each lane offers its keys to targets x - d with a
 // shared-memory atomicMin (consecutive lanes hit consecutive targets, so no bank conflict) and the
@@ -108,78 +87,12 @@ __device__ __forceinline__ float refine_subpixel(const Problem& pb, int64_t p, i
   return v;
 }
 
-// One tile of T pixels of a row, 256 threads: warp w takes pixels w, w + 8, ..., PF at a time so
-// that their loads are in flight together. Targets whose sources all lie in the tile are then
-// stored, the others (at most D - 1 per tile side) merged with a global atomicMin.
-template <bool WIDE, int NDL, bool EXACT, int PFMAX>
-__device__ __forceinline__ void wta_dr_tile_t(const Problem& pb, int item, uint32_t* keys, int T) {
-  const int W = pb.W, D = pb.D;
-  const int ntx = (W + T - 1) / T;
-  const int y = item / ntx, x0 = (item - y * ntx) * T;
-  const int n = min(T, W - x0);
-  const int64_t rowbase = (int64_t)y * W;
-  const int ntar = T + D - 1;  // targets x0 - D + 1 .. x0 + T - 1
-  for (int i = threadIdx.x; i < ntar; i += blockDim.x) keys[i] = 0xFFFFFFFFu;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // pixels whose loads are in flight together (at most PFMAX)
-  constexpr int PF = (NDL <= 4 ? 4 : 2) < PFMAX ? (NDL <= 4 ? 4 : 2) : PFMAX;
-  for (int px = threadIdx.x >> 5; px < n; px += PF * nw) {
-    uint32_t sv[PF][NDL];
-#pragma unroll
-    for (int u = 0; u < PF; u++)
-      if (px + u * nw < n)
-        wta_load<WIDE, NDL, EXACT>(pb.agg, (rowbase + x0 + px + u * nw) * D, D, lane, sv[u]);
-#pragma unroll
-    for (int u = 0; u < PF; u++)
-      if (px + u * nw < n)
-        wta_keys<NDL, EXACT>(pb, rowbase, x0 + px + u * nw, px + u * nw, keys, lane, sv[u]);
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < ntar; i += blockDim.x) {
-    const int x = x0 - D + 1 + i;
-    if (x < 0 || x >= x0 + n) continue;
-    const uint32_t k = keys[i];
-    if (k == 0xFFFFFFFFu) continue;
-    // all sources x .. min(x + D - 1, W - 1) of this target lie in the tile
-    const bool whole = x >= x0 && min(x + D - 1, W - 1) < x0 + n;
-    if (whole)
-      pb.kr[rowbase + x] = k;
-    else
-      atomicMin(&pb.kr[rowbase + x], k);
-  }
-  __syncthreads();
-}
-
-template <bool WIDE, int NDL, int PFMAX>
-__device__ __forceinline__ void wta_dr_tile_n(const Problem& pb, int item, uint32_t* keys, int T) {
-  if (pb.D == 32 * NDL)
-    wta_dr_tile_t<WIDE, NDL, true, PFMAX>(pb, item, keys, T);
-  else
-    wta_dr_tile_t<WIDE, NDL, false, PFMAX>(pb, item, keys, T);
-}
-
-// T pixels of a row (T = 64, 128 or 256), 256 threads, T + D - 1 keys of shared memory. PFMAX
-// caps the pixels a warp loads at once (4 for the single-pair kernel; the persistent batch kernel,
-// measured, prefers 1).
-template <bool WIDE, int PFMAX>
-__device__ __forceinline__ void wta_dr_tile(const Problem& pb, int item, uint32_t* keys, int T) {
-  switch ((pb.D + 31) / 32) {
-    case 1: wta_dr_tile_n<WIDE, 1, PFMAX>(pb, item, keys, T); break;
-    case 2: wta_dr_tile_n<WIDE, 2, PFMAX>(pb, item, keys, T); break;
-    case 3: wta_dr_tile_n<WIDE, 3, PFMAX>(pb, item, keys, T); break;
-    case 4: wta_dr_tile_n<WIDE, 4, PFMAX>(pb, item, keys, T); break;
-    case 5: wta_dr_tile_n<WIDE, 5, PFMAX>(pb, item, keys, T); break;
-    case 6: wta_dr_tile_n<WIDE, 6, PFMAX>(pb, item, keys, T); break;
-    case 7: wta_dr_tile_n<WIDE, 7, PFMAX>(pb, item, keys, T); break;
-    default: wta_dr_tile_n<WIDE, 8, PFMAX>(pb, item, keys, T); break;
-  }
-}
-
-// The same tile with its sums staged in shared memory first: all 256 threads copy the tile's
-// contiguous run of S (n pixels x D sums) with 16-byte cp.async copies, so the whole tile is in
-// flight at once, then the warps read their pixel vectors from shared memory. T pixels with
-// T * D * bytes-per-sum <= 64 KB (wta_staged_px). Shared memory: the run, then T + D - 1 keys.
+// One tile of T pixels of a row (256 threads): its sums are staged in shared memory first, all
+// threads copying the tile's contiguous run of S (n pixels x D sums) with 16-byte cp.async
+// copies, so the whole tile is in flight at once; then warp w takes pixels w, w + 8, ... from
+// shared memory. Targets whose sources all lie in the tile are stored, the others (at most
+// D - 1 per tile side) merged with a global atomicMin. T pixels with T * D * bytes-per-sum
+// <= 64 KB (wta_staged_px). Shared memory: the run, then T + D - 1 keys.
 __host__ __device__ inline int wta_staged_px(int D, bool wide, int T) {
   const int cap = 65536 / (D * (wide ? 4 : 2));
   return T < cap ? T : cap;
