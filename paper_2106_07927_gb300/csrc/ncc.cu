@@ -75,12 +75,13 @@ __device__ __forceinline__ uint32_t ncc_cost_of(int nn, int sab, int sa, float i
 }
 
 template <int N_>
-__global__ void __launch_bounds__(256, N_ == 5 ? 4 : 2)
+__global__ void __launch_bounds__(256, N_ == 5 ? 4 : 3)
     ncc_cost_kernel(Problem pb, int agg_bytes_per_de, const uint2* st) {
   constexpr int R = N_ / 2;
   constexpr int NW = (N_ + 3) / 4;  // dot-product words of a patch row
   __shared__ __align__(16) uint8_t sl[kNccMaxRows][kNccLStride];
   __shared__ __align__(16) uint8_t sr[kNccMaxRows][kNccRStride];
+  extern __shared__ __align__(16) uint8_t sst_ring[];  // 9 x 9: N_ x 256 x 16 bytes of ring
   const int W = pb.W, H = pb.H, D = pb.D;
   const int TX = ncc_tx(D), G = D / 4;
   const int ntx = (W + TX - 1) / TX;
@@ -156,12 +157,21 @@ __global__ void __launch_bounds__(256, N_ == 5 ? 4 : 2)
   bool inside[4];                 // x - d >= 0 for d = 4g + k
 #pragma unroll
   for (int k = 0; k < 4; k++) inside[k] = x - 4 * g - k >= 0;
-  int ring[N_][4];
+  // The last N_ rows' dot products: in registers for 5 x 5; in shared memory for 9 x 9 (slot j of
+  // this thread at sring[j * 256 + thread], 16 bytes), which keeps the 9 x 9 kernel's registers
+  // low enough for more resident blocks.
+  constexpr bool RSM = N_ > 5;
+  int ring[RSM ? 1 : N_][4];
+  int4* sring = reinterpret_cast<int4*>(sst_ring);
   int vs[4] = {0, 0, 0, 0};
 #pragma unroll
-  for (int j = 0; j < N_; j++)
+  for (int j = 0; j < (RSM ? 1 : N_); j++)
 #pragma unroll
     for (int k = 0; k < 4; k++) ring[j][k] = 0;
+  if (RSM) {
+#pragma unroll
+    for (int j = 0; j < N_; j++) sring[j * 256 + threadIdx.x] = make_int4(0, 0, 0, 0);
+  }
 
   // one staged row t: its four row dot products enter the ring (slot j = t mod N_); from
   // t = 2R on, the patch of output row t - 2R is complete and its costs are written
@@ -182,15 +192,30 @@ __global__ void __launch_bounds__(256, N_ == 5 ? 4 : 2)
 #pragma unroll
       for (int m = 0; m <= NW; m++) rwd[m] = __funnelshift_r(raw[m], raw[m + 1], rsh);
     }
+    int h[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
       const int o = 3 - k;  // byte offset of the window of d = 4g + k
-      uint32_t h = 0;
+      uint32_t a = 0;
 #pragma unroll
       for (int m = 0; m < NW; m++)
-        h = __dp4a(lwd[m], o ? __funnelshift_r(rwd[m], rwd[m + 1], 8 * o) : rwd[m], h);
-      vs[k] += (int)h - ring[j][k];
-      ring[j][k] = (int)h;
+        a = __dp4a(lwd[m], o ? __funnelshift_r(rwd[m], rwd[m + 1], 8 * o) : rwd[m], a);
+      h[k] = (int)a;
+    }
+    if (RSM) {
+      int4* slot = &sring[j * 256 + threadIdx.x];
+      const int4 old = *slot;
+      *slot = make_int4(h[0], h[1], h[2], h[3]);
+      vs[0] += h[0] - old.x;
+      vs[1] += h[1] - old.y;
+      vs[2] += h[2] - old.z;
+      vs[3] += h[3] - old.w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        vs[k] += h[k] - ring[RSM ? 0 : j][k];
+        ring[RSM ? 0 : j][k] = h[k];
+      }
     }
     if (t >= 2 * R) {  // output row y0 + t - 2R
       const uint2 a = *sa_p;
@@ -224,7 +249,11 @@ cudaError_t launch_ncc_n(const Problem& pb, const Method& mt, cudaStream_t s) {
   ncc_stats_kernel<N_><<<sg, 256, 0, s>>>(pb.right, pb.in_pitch, pb.W, pb.H, pb.nst + npx, true);
   const int TX = ncc_tx(pb.D);
   const int blocks = ((pb.W + TX - 1) / TX) * ((pb.H + kNccTY - 1) / kNccTY);
-  ncc_cost_kernel<N_><<<blocks, 256, 0, s>>>(pb, mt.wide ? 4 : 2, pb.nst);
+  const int ring_smem = N_ > 5 ? N_ * 256 * 16 : 0;
+  if (ring_smem)
+    cudaFuncSetAttribute(ncc_cost_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         ring_smem);
+  ncc_cost_kernel<N_><<<blocks, 256, ring_smem, s>>>(pb, mt.wide ? 4 : 2, pb.nst);
   return cudaGetLastError();
 }
 
