@@ -54,7 +54,7 @@
  *                       compares the integer D^L with D^R, keeps the refined value, and the
  *                       median runs on the refined values.
  *
- * Conventions where the paper is silent (each is a reading, listed in the design doc):
+ * Conventions where the paper is silent (each is a reading of the paper, not a statement of it):
  *   - census bit = [neighbour < centre], row-major over the window (rows outer), LSB first;
  *   - disparities d = 0 .. D-1;
  *   - all volumes are [y][x][d] with the disparities of one pixel contiguous (Sec. 2.2.1).
