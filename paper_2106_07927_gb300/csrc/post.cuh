@@ -33,11 +33,11 @@ namespace r2t {
 __host__ __device__ inline int wta_items(int W, int H, int T) { return H * ((W + T - 1) / T); }
 
 // The keys of one pixel x (tile position px): each lane offers its keys to targets x - d with a
-// shared-memory atomicMin (consecutive lanes hit consecutive targets, so no bank conflict) and the
-// warp minimum gives D^L(x).
+// shared-memory atomicMin (consecutive lanes hit consecutive targets, so no bank conflict); returns
+// the warp minimum, whose low byte is D^L(x).
 template <int NDL, bool EXACT>
-__device__ __forceinline__ void wta_keys(const Problem& pb, int64_t rowbase, int x, int px,
-                                         uint32_t* keys, int lane, const uint32_t (&s)[NDL]) {
+__device__ __forceinline__ uint32_t wta_keys(const Problem& pb, int x, int px, uint32_t* keys,
+                                             int lane, const uint32_t (&s)[NDL]) {
   const int D = EXACT ? 32 * NDL : pb.D;
   uint32_t* kt = keys + (px + D - 1 - lane);  // kt[-32 i] is the key of target x - d
   uint32_t key[NDL];
@@ -58,8 +58,7 @@ __device__ __forceinline__ void wta_keys(const Problem& pb, int64_t rowbase, int
       if ((EXACT || d < D) && d <= x) atomicMin(kt - 32 * i, key[i]);
     }
   }
-  kl = __reduce_min_sync(0xffffffffu, kl);
-  if (lane == 0) pb.dl[rowbase + x] = (uint16_t)(kl & 0xFFu);
+  return __reduce_min_sync(0xffffffffu, kl);
 }
 
 // Sub-pixel D^L of pixel p (Sec. 2.1.3) from its integer D^L d and the aggregated costs at d - 1,
@@ -124,8 +123,10 @@ __device__ __forceinline__ void wta_dr_staged_t(const Problem& pb, int item, uin
   for (int i = threadIdx.x; i < ntar; i += blockDim.x) keys[i] = 0xFFFFFFFFu;
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
-  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int px = threadIdx.x >> 5; px < n; px += nw) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  uint32_t mine = 0;  // lane k keeps the key of the warp's k-th pixel (T / nw <= 32 pixels)
+  int it = 0;
+  for (int px = warp; px < n; px += nw, it++) {
     uint32_t sv[NDL];
 #pragma unroll
     for (int i = 0; i < NDL; i++) {
@@ -138,8 +139,10 @@ __device__ __forceinline__ void wta_dr_staged_t(const Problem& pb, int item, uin
           sv[i] = reinterpret_cast<const uint16_t*>(smem)[px * D + d];
       }
     }
-    wta_keys<NDL, EXACT>(pb, rowbase, x0 + px, px, keys, lane, sv);
+    const uint32_t kl = wta_keys<NDL, EXACT>(pb, x0 + px, px, keys, lane, sv);
+    mine = lane == it ? kl : mine;
   }
+  if (lane < it) pb.dl[rowbase + x0 + warp + nw * lane] = (uint16_t)(mine & 0xFFu);  // D^L
   __syncthreads();
   for (int i = threadIdx.x; i < ntar; i += blockDim.x) {
     const int x = x0 - D + 1 + i;
@@ -208,10 +211,10 @@ __device__ __forceinline__ uint32_t med3(uint32_t a, uint32_t b, uint32_t c) {
 // Disparity of pixel (x, y) after the left-right check (or D^L when the check is off). The check
 // always compares the integer D^L with D^R; SUB returns the bits of the sub-pixel D^L it kept.
 template <bool SUB, bool WIDE>
-__device__ __forceinline__ uint32_t checked_disp(const Problem& pb, const Method& mt, int x, int y) {
+__device__ __forceinline__ uint32_t checked_from(const Problem& pb, const Method& mt, int x, int y,
+                                                 int dl) {
   constexpr uint32_t inv = SUB ? kInvalidF : kInvalid;
   const int64_t row = (int64_t)y * pb.W;
-  const int dl = pb.dl[row + x];
   if (mt.flags & 1) {
     if (x - dl < 0) return inv;
     // exact check: D^R(x') = D^L of the swapped, flipped pair at W - 1 - x'
@@ -221,6 +224,10 @@ __device__ __forceinline__ uint32_t checked_disp(const Problem& pb, const Method
     if ((diff < 0 ? -diff : diff) > mt.lr_threshold) return inv;
   }
   return SUB ? __float_as_uint(refine_subpixel<WIDE>(pb, row + x, dl)) : (uint32_t)dl;
+}
+template <bool SUB, bool WIDE>
+__device__ __forceinline__ uint32_t checked_disp(const Problem& pb, const Method& mt, int x, int y) {
+  return checked_from<SUB, WIDE>(pb, mt, x, y, pb.dl[(int64_t)y * pb.W + x]);
 }
 
 // Final map of one 64 x 4 tile: LR check (+ median when flags & 2), plus the debug maps D^R and
@@ -235,11 +242,27 @@ __device__ __forceinline__ void lr_median_tile(const Problem& pb, const Method& 
   const int x0 = (item % ntx) * kMedTW, y0 = (item / ntx) * kMedTH;
   const bool median = (mt.flags & 2) != 0;
   if (median) {
-    for (int i = threadIdx.x; i < (kMedTH + 2) * (kMedTW + 2); i += blockDim.x) {
+    // the frame and tile (396 values, two per thread of 256): both D^L loads first, then the
+    // checks (whose D^R key loads depend on them), so the two load chains overlap
+    constexpr int NS = (kMedTH + 2) * (kMedTW + 2);
+    static_assert(NS <= 2 * 256, "two staged values per thread");
+    int gxs[2], gys[2], dls[2];
+    bool ins[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int i = threadIdx.x + 256 * u;
       const int ty = i / (kMedTW + 2), tx = i % (kMedTW + 2);
-      const int gx = x0 + tx - 1, gy = y0 + ty - 1;
-      sm.t[ty][tx] =
-          (gx >= 0 && gx < W && gy >= 0 && gy < H) ? checked_disp<SUB, WIDE>(pb, mt, gx, gy) : inv;
+      gxs[u] = x0 + tx - 1;
+      gys[u] = y0 + ty - 1;
+      ins[u] = i < NS && gxs[u] >= 0 && gxs[u] < W && gys[u] >= 0 && gys[u] < H;
+      dls[u] = ins[u] ? pb.dl[(int64_t)gys[u] * W + gxs[u]] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int i = threadIdx.x + 256 * u;
+      if (i < NS)
+        sm.t[i / (kMedTW + 2)][i % (kMedTW + 2)] =
+            ins[u] ? checked_from<SUB, WIDE>(pb, mt, gxs[u], gys[u], dls[u]) : inv;
     }
     __syncthreads();
   }
