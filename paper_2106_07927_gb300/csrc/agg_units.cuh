@@ -112,10 +112,11 @@ cudaError_t launch_shear(const Problem& pb, const Method& mt, const Tuning& tn, 
 template <int DPL, int LPL, bool WIDE>
 __device__ __forceinline__ void rows_full(const Problem& pb, const Method& mt, int unit0,
                                           int unit_end) {
+  // one row direction per lane group (units 0 .. 2H - 1), as the single-pair default
   if (pb.D == DPL * LPL)
-    agg_rows<DPL, LPL, WIDE, true, false>(pb, mt, unit0, unit_end);
+    agg_rows<DPL, LPL, WIDE, true, true>(pb, mt, unit0, unit_end);
   else
-    agg_rows<DPL, LPL, WIDE, false, false>(pb, mt, unit0, unit_end);
+    agg_rows<DPL, LPL, WIDE, false, true>(pb, mt, unit0, unit_end);
 }
 
 template <bool WIDE>

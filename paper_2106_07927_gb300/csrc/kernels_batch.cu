@@ -337,7 +337,7 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
     tot[2] += median_items(pb.W, pb.H);
     wta_smem = std::max(wta_smem, (int)wta_staged_smem_bytes(pb.D, mt.wide != 0, wt));
     const int dpl = e->dpl_by_d16[pb.D / 16];
-    lk.push_back(Keyed{AggSeg{p, 0, row_units(pb.H, false), 32 / long_lanes(pb.D, dpl)}, pb.W});
+    lk.push_back(Keyed{AggSeg{p, 0, row_units(pb.H, true), 32 / long_lanes(pb.D, dpl)}, pb.W});
     bk.push_back(Keyed{AggSeg{p, 0, shear_items(pb.W, pb.D, 16, mt.num_paths, 1), 1}, pb.H});
   }
   for (int k = 0; k < 3; k++) prefix[k * stride + n] = tot[k];
