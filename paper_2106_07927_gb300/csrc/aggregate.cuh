@@ -417,6 +417,12 @@ __device__ __forceinline__ unsigned long long lds64(uint32_t a) {
 // (and, FULL, every lane) compute unconditionally; only their copies and adds are skipped. With
 // CPL = 2 the step's bookkeeping (syncs, ring slots, run pointers) serves twice the chains and the
 // two chains' arithmetic interleaves.
+//
+// Events - a run that wraps around the image edge (copy or add in two parts), a chain that
+// restarts because a new line of the path enters, a cursor that wraps, the last rows - happen only
+// in a window of about CH + 8 steps each time the run passes the edge column, and near the end.
+// Between them the walk takes pairs of steps on a fast path that tests for none of them (ring slot
+// and staging buffer follow from the step index); each event step takes the general path.
 template <int DPL, int WD, int CPL, bool WIDE, bool FULL, bool SH0>
 __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt, int kind, int j0,
                                             uint8_t* ring, uint8_t* stage) {
@@ -430,6 +436,7 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   constexpr int NCP = CPL * DPL >= 16 ? CPL * DPL / 16 : 1;  // 16-byte pieces a lane copies per step
   constexpr int NVS = DPL * BPE / 16;         // sum pieces a lane stages per chain and step
   constexpr int NA = NP < 4 ? NP : 4;         // independent accumulators of a lane's minimum
+  static_assert(KS == 8, "two copied steps per group, three groups ahead");
   const int lane = threadIdx.x & 31;
   const int lig = lane % WD, c = lane / WD;
   const int W = pb.W, H = pb.H;
@@ -437,7 +444,6 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   const int PP = D / 16;        // cost pieces per pixel
   const int PS = D * BPE / 16;  // sum pieces per pixel
   const int n = min(CH, W - j0);  // chains of this warp item
-  const bool nfull = n == CH;
   const int sh = SH0 ? 0 : (kind < 4 ? 1 : -1);
   const bool back = (kind & 1) != 0;
   const int dy = back ? -1 : 1, dx = back ? -sh : sh;
@@ -447,7 +453,6 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   const bool owns = FULL || lig * DPL < D;  // the lane holds disparities of its chains
   const int slot_bytes = CH * D;
   const uint32_t ring_s = (uint32_t)__cvta_generic_to_shared(ring);
-  const uint32_t ring_end = ring_s + KS * slot_bytes;
   const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
   const int stage_bytes = CH * D * BPE;  // one step's run of sums (two such buffers)
   const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
@@ -481,18 +486,21 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
 #pragma unroll
     for (int v = 0; v < NVS; v++) st_s[g][v] = (cg * PS + lig * NVS + v) * 16;
   }
+  auto slot_of = [&](int t) { return ring_s + (uint32_t)((t & (KS - 1)) * slot_bytes); };
 
-  // copy cursor: global start of the next step's run, its column, and its ring slot
+  // copy cursor: global start of the next copied step's run and its column
   const uint8_t* crun = pb.cost + ((int64_t)ystart * W + xs) * D;
   int xc = xs;
-  uint32_t cslot = ring_s;
-  auto copy_step = [&](int t) {
-    if (t < H) {
-      if (nfull && (SH0 || xc + CH <= W)) {  // every piece, contiguous run
+  // General copy of step tc (past the last row: nothing), its run possibly wrapping around the
+  // image edge.
+  auto copy_step = [&](int tc) {
+    if (tc < H) {
+      const uint32_t cslot = slot_of(tc);
+      if (SH0 || xc + n <= W) {  // contiguous run
         const uint8_t* src = crun + 16 * lane;
 #pragma unroll
         for (int v = 0; v < NCP; v++)
-          if ((FULL && CPL * DPL >= 16) || cp_c[v] >= 0)  // (a step has 32 NCP pieces then)
+          if (cp_c[v] >= 0)
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(cslot + cp_s[v]),
                          "l"(src + 512 * v));
       } else {
@@ -501,15 +509,13 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
           if (cp_c[v] >= 0) {
             const int p = lane + 32 * v;
             const int pc = cp_c[v], pi = p - pc * PP;
-            const int back_w = (!SH0 && xc + pc >= W) ? W : 0;  // wrapped to the row's start
+            const int back_w = xc + pc >= W ? W : 0;  // wrapped to the row's start
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(cslot + cp_s[v]),
                          "l"(crun + ((int64_t)pc - back_w) * D + pi * 16));
           }
         }
       }
       crun += cstride;
-      cslot += slot_bytes;
-      if (cslot == ring_end) cslot = ring_s;
       if (!SH0) {
         xc += dx;
         if (xc >= W) {
@@ -522,27 +528,179 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
       }
     }
   };
+  // Fast copy of steps tc and tc + 1: both before the last row, both runs contiguous, and the
+  // cursor does not wrap after them.
+  auto copy_two = [&](int tc) {
+    const uint32_t s0 = slot_of(tc), s1 = slot_of(tc + 1);
+    const uint8_t* src = crun + 16 * lane;
+#pragma unroll
+    for (int v = 0; v < NCP; v++)
+      if (cp_c[v] >= 0)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + cp_s[v]),
+                     "l"(src + 512 * v));
+#pragma unroll
+    for (int v = 0; v < NCP; v++)
+      if (cp_c[v] >= 0)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s1 + cp_s[v]),
+                     "l"(src + cstride + 512 * v));
+    crun += 2 * cstride;
+    if (!SH0) xc += 2 * dx;
+  };
 
   uint32_t L[CPL][NP], mm[CPL];
-  // steps until the lane's chain g arrives at the edge column again and restarts (a chain at
-  // column x reaches the edge after (W - x) mod W steps going right, (x + 1) mod W going left;
-  // 0 means it starts there, which step 0 does anyway, so the next restart is W steps later)
-  int rs[CPL];
 #pragma unroll
   for (int g = 0; g < CPL; g++) {
 #pragma unroll
     for (int k = 0; k < NP; k++) L[g][k] = owns ? 0u : kSent * 0x10001u;
     mm[g] = 0;
-    const int x0 = (xs + c + CPW * g) % W;
-    int r = dx > 0 ? W - x0 : x0 + 1;
-    r = r >= W ? r - W : r;
-    rs[g] = r == 0 ? W : r;
   }
   uint8_t* arun = reinterpret_cast<uint8_t*>(pb.agg) + ((int64_t)ystart * W + xs) * D * BPE;
-  // steps until xs steps out of 0 .. W - 1 (going right: after W - xs steps; left: xs + 1)
-  int xw = dx > 0 ? W - xs : xs + 1;
-  uint32_t rslot = ring_s;  // ring slot of the current step
-  uint32_t sbuf = stage_s;  // staging buffer of the current step
+
+  // The step's cost pieces, all loaded before any is used.
+  auto load_costs = [&](int t, uint4 (&raw)[CPL][NVC]) {
+    const uint32_t cur = slot_of(t);
+#pragma unroll
+    for (int g = 0; g < CPL; g++)
+#pragma unroll
+      for (int v = 0; v < NVC; v++)
+        if (CW == 16) {
+          raw[g][v] = owns ? lds128(cur + rd_s[g][v]) : make_uint4(0, 0, 0, 0);
+        } else {
+          const unsigned long long r8 = owns ? lds64(cur + rd_s[g][v]) : 0ull;
+          raw[g][v] = make_uint4((uint32_t)r8, (uint32_t)(r8 >> 32), 0u, 0u);
+        }
+  };
+  // One step of the recurrence on every chain of the lane, L and mm in place, and its sums into
+  // staging buffer par (the step's parity).
+  auto update = [&](int par, const uint4 (&raw)[CPL][NVC]) {
+    // Neighbour pairs are formed on the fly from the old L: xp = (L(d0 - 1), L(d0)) of pair k,
+    // xn the same for pair k + 1; L[k] is overwritten only after both were formed.
+    uint32_t xp[CPL], dn[CPL], mP2[CPL], lm[CPL][NA];
+#pragma unroll
+    for (int g = 0; g < CPL; g++) {
+      uint32_t up = kSent << 16;
+      dn[g] = kSent;
+      if (WD > 1) {
+        const uint32_t a = __shfl_up_sync(0xffffffffu, L[g][NP - 1], 1, WD);
+        const uint32_t b = __shfl_down_sync(0xffffffffu, L[g][0], 1, WD);
+        up = lig == 0 ? up : a;
+        dn[g] = lig == WD - 1 ? dn[g] : b;
+      }
+      xp[g] = __byte_perm(up, L[g][0], 0x5432);
+      mP2[g] = mm[g] + P2P2;
+#pragma unroll
+      for (int a = 0; a < NA; a++) lm[g][a] = 0xFFFFFFFFu;
+    }
+#pragma unroll
+    for (int v = 0; v < NVC; v++) {  // CW disparities (CW / 2 pairs) per cost read
+      uint32_t cst[CPL][8];
+#pragma unroll
+      for (int g = 0; g < CPL; g++) {
+        unpack4(raw[g][v].x, cst[g][0], cst[g][1]);
+        unpack4(raw[g][v].y, cst[g][2], cst[g][3]);
+        unpack4(raw[g][v].z, cst[g][4], cst[g][5]);
+        unpack4(raw[g][v].w, cst[g][6], cst[g][7]);
+      }
+#pragma unroll
+      for (int j = 0; j < CW / 2; j++) {
+        const int k = (CW / 2) * v + j;
+#pragma unroll
+        for (int g = 0; g < CPL; g++) {
+          const uint32_t xn =
+              __byte_perm(L[g][k], k + 1 < NP ? L[g][(k + 1) % NP] : dn[g], 0x5432);
+          const uint32_t tt = vmin2(xp[g], xn) + P1P1;
+          const uint32_t uu = vmin2(vmin2(L[g][k], tt), mP2[g]);  // >= m(q) in both halves
+          const uint32_t ln = uu + cst[g][j] - mm[g];             // each half in [0, 255 + P2]
+          L[g][k] = owns ? ln : kSent * 0x10001u;
+          lm[g][k % NA] = vmin2(lm[g][k % NA], L[g][k]);
+          xp[g] = xn;
+        }
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < CPL; g++) {
+#pragma unroll
+      for (int w = 1; w < NA; w *= 2)
+#pragma unroll
+        for (int a = 0; a + w < NA; a += 2 * w) lm[g][a] = vmin2(lm[g][a], lm[g][a + w]);
+      mm[g] = group_min<WD>(halves_min(lm[g][0]));
+    }
+    const uint32_t sbuf = stage_s + (uint32_t)(par * stage_bytes);
+#pragma unroll
+    for (int g = 0; g < CPL; g++) {
+      if (FULL || act[g]) {
+#pragma unroll
+        for (int v = 0; v < NVS; v++) {
+          const uint32_t a = sbuf + (uint32_t)st_s[g][v];
+          if (!WIDE)
+            sts128(a, L[g][4 * v], L[g][4 * v + 1], L[g][4 * v + 2], L[g][4 * v + 3]);
+          else
+            sts128(a, L[g][2 * v] & 0xFFFFu, L[g][2 * v] >> 16, L[g][2 * v + 1] & 0xFFFFu,
+                   L[g][2 * v + 1] >> 16);
+        }
+      }
+    }
+    // The run's sums go to S with bulk reductions issued by lane 0 (below): the tensor memory
+    // accelerator adds the staged 32-bit words (two packed u16 sums each, which cannot carry into
+    // each other, or one u32 sum when wide) into S atomically, element by element. The staging
+    // writes are made visible to that async proxy first.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+  };
+  // The bulk add of the step's run from staging buffer par (n1 pixels from arun, the rest from
+  // the row's start).
+  auto add_run = [&](int par, int n1) {
+    if (lane == 0) {
+      const uint32_t sbuf = stage_s + (uint32_t)(par * stage_bytes);
+      asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;"
+                   ::"l"(arun), "r"(sbuf), "r"(n1 * D * BPE) : "memory");
+      if (!SH0 && n1 < n)
+        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;"
+                     ::"l"(arun - (int64_t)xs * D * BPE), "r"(sbuf + n1 * D * BPE),
+                     "r"((n - n1) * D * BPE)
+                     : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  };
+  // Start of every step: the bulk add issued two steps ago has read the staging buffer this step
+  // refills (bulk groups are per thread: lanes other than lane 0 have none and pass at once); on
+  // even steps, issue the copies of steps t + 6, t + 7 (fast or general) and wait for steps t,
+  // t + 1.
+  auto begin_step = [&](int t, bool even, bool fast) {
+    asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+    __syncwarp();  // every lane is done with the ring slot refilled below and with the staging
+    if (even) {
+      if (fast) {
+        copy_two(t + KS - 2);
+      } else {
+        copy_step(t + KS - 2);
+        copy_step(t + KS - 1);
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 3;" ::: "memory");
+      __syncwarp();
+    }
+  };
+  // Pairs of fast steps from even step t: for steps t .. t + 7 (the pair and its copies) the runs
+  // neither wrap nor restart a chain and the cursors do not wrap. Going right that holds while
+  // 1 <= xs and xs + 7 <= min(W - n, W - 2); going left while 8 <= xs <= W - n - 1 (a chain
+  // restarts at column 0 going right, W - 1 going left).
+  auto fast_pairs = [&](int t) -> int {
+    const int qh = H - KS - t;  // the pair's copies must be of rows before H
+    if (qh < 0) return 0;
+    int q = qh >> 1;
+    if (!SH0) {
+      if (dx > 0) {
+        const int lim = min(W - n, W - 2) - (KS - 1);
+        if (xs < 1 || xs > lim) return 0;
+        q = min(q, (lim - xs) >> 1);
+      } else {
+        if (xs < KS || xs > W - n - 1) return 0;
+        q = min(q, (xs - KS) >> 1);
+      }
+    }
+    return q + 1;
+  };
 
   // prologue: steps 0 .. 5 in flight as three groups of two
 #pragma unroll
@@ -551,149 +709,59 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
     copy_step(s + 1);
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  for (int t0 = 0; t0 < H; t0 += 2) {
+  int t = 0;
+  while (t < H) {
+    for (int np = (t & 1) ? 0 : fast_pairs(t); np > 0; np--, t += 2) {
 #pragma unroll
-    for (int u = 0; u < 2; u++) {
-      const int t = t0 + u;
-      if (t >= H) break;
-      // the bulk add issued two steps ago has read the staging buffer this step refills
-      // (bulk groups are per thread: lanes other than lane 0 have none and pass at once)
-      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-      __syncwarp();  // every lane is done with the ring slot refilled below and with the staging
-      if (u == 0) {  // issue steps t + 6, t + 7, then wait for steps t, t + 1
-        copy_step(t + KS - 2);
-        copy_step(t + KS - 1);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group 3;" ::: "memory");
-        __syncwarp();
+      for (int u = 0; u < 2; u++) {
+        uint4 raw[CPL][NVC];
+        begin_step(t + u, u == 0, true);
+        load_costs(t + u, raw);
+        update(u, raw);
+        add_run(u, n);
+        arun += astride;
+        if (!SH0) xs += dx;
       }
-      const uint32_t cur = rslot;  // ring slot of this step
-      rslot += slot_bytes;
-      if (rslot == ring_end) rslot = ring_s;
-      uint4 raw[CPL][NVC];  // the step's cost pieces, all loaded before any is used
+    }
+    if (t >= H) break;
+    // general step
+    uint4 raw[CPL][NVC];
+    const int par = t & 1;
+    begin_step(t, par == 0, false);
+    load_costs(t, raw);
+    if (!SH0 && t > 0) {  // a new line of the path enters where a chain reaches the edge: L = C
+      const int edge = dx > 0 ? 0 : W - 1;
+      bool hit[CPL], any = false;
 #pragma unroll
-      for (int g = 0; g < CPL; g++)
-#pragma unroll
-        for (int v = 0; v < NVC; v++)
-          if (CW == 16) {
-            raw[g][v] = owns ? lds128(cur + rd_s[g][v]) : make_uint4(0, 0, 0, 0);
-          } else {
-            const unsigned long long r8 = owns ? lds64(cur + rd_s[g][v]) : 0ull;
-            raw[g][v] = make_uint4((uint32_t)r8, (uint32_t)(r8 >> 32), 0u, 0u);
-          }
-      if (!SH0 && t > 0) {
-        bool hit = false;
+      for (int g = 0; g < CPL; g++) {
+        hit[g] = (xs + c + CPW * g) % W == edge;
+        any |= hit[g];
+      }
+      if (__any_sync(0xffffffffu, any)) {
 #pragma unroll
         for (int g = 0; g < CPL; g++) {
-          rs[g]--;
-          hit |= rs[g] == 0;
-        }
-        if (__any_sync(0xffffffffu, hit)) {  // a new line of the path enters: L = C
+          if (hit[g]) {
 #pragma unroll
-          for (int g = 0; g < CPL; g++) {
-            if (rs[g] == 0) {
-#pragma unroll
-              for (int k = 0; k < NP; k++) L[g][k] = owns ? 0u : kSent * 0x10001u;
-              mm[g] = 0;
-              rs[g] = W;
-            }
+            for (int k = 0; k < NP; k++) L[g][k] = owns ? 0u : kSent * 0x10001u;
+            mm[g] = 0;
           }
-        }
-      }
-      // Neighbour pairs are formed on the fly from the old L: xp = (L(d0 - 1), L(d0)) of pair k,
-      // xn the same for pair k + 1; L[k] is overwritten only after both were formed.
-      uint32_t xp[CPL], dn[CPL], mP2[CPL], lm[CPL][NA];
-#pragma unroll
-      for (int g = 0; g < CPL; g++) {
-        uint32_t up = kSent << 16;
-        dn[g] = kSent;
-        if (WD > 1) {
-          const uint32_t a = __shfl_up_sync(0xffffffffu, L[g][NP - 1], 1, WD);
-          const uint32_t b = __shfl_down_sync(0xffffffffu, L[g][0], 1, WD);
-          up = lig == 0 ? up : a;
-          dn[g] = lig == WD - 1 ? dn[g] : b;
-        }
-        xp[g] = __byte_perm(up, L[g][0], 0x5432);
-        mP2[g] = mm[g] + P2P2;
-#pragma unroll
-        for (int a = 0; a < NA; a++) lm[g][a] = 0xFFFFFFFFu;
-      }
-#pragma unroll
-      for (int v = 0; v < NVC; v++) {  // CW disparities (CW / 2 pairs) per cost read
-        uint32_t cst[CPL][8];
-#pragma unroll
-        for (int g = 0; g < CPL; g++) {
-          unpack4(raw[g][v].x, cst[g][0], cst[g][1]);
-          unpack4(raw[g][v].y, cst[g][2], cst[g][3]);
-          unpack4(raw[g][v].z, cst[g][4], cst[g][5]);
-          unpack4(raw[g][v].w, cst[g][6], cst[g][7]);
-        }
-#pragma unroll
-        for (int j = 0; j < CW / 2; j++) {
-          const int k = (CW / 2) * v + j;
-#pragma unroll
-          for (int g = 0; g < CPL; g++) {
-            const uint32_t xn =
-                __byte_perm(L[g][k], k + 1 < NP ? L[g][(k + 1) % NP] : dn[g], 0x5432);
-            const uint32_t tt = vmin2(xp[g], xn) + P1P1;
-            const uint32_t uu = vmin2(vmin2(L[g][k], tt), mP2[g]);  // >= m(q) in both halves
-            const uint32_t ln = uu + cst[g][j] - mm[g];             // each half in [0, 255 + P2]
-            L[g][k] = owns ? ln : kSent * 0x10001u;
-            lm[g][k % NA] = vmin2(lm[g][k % NA], L[g][k]);
-            xp[g] = xn;
-          }
-        }
-      }
-#pragma unroll
-      for (int g = 0; g < CPL; g++) {
-#pragma unroll
-        for (int w = 1; w < NA; w *= 2)
-#pragma unroll
-          for (int a = 0; a + w < NA; a += 2 * w) lm[g][a] = vmin2(lm[g][a], lm[g][a + w]);
-        mm[g] = group_min<WD>(halves_min(lm[g][0]));
-      }
-#pragma unroll
-      for (int g = 0; g < CPL; g++) {
-        if (FULL || act[g]) {
-#pragma unroll
-          for (int v = 0; v < NVS; v++) {
-            const uint32_t a = sbuf + (uint32_t)st_s[g][v];
-            if (!WIDE)
-              sts128(a, L[g][4 * v], L[g][4 * v + 1], L[g][4 * v + 2], L[g][4 * v + 3]);
-            else
-              sts128(a, L[g][2 * v] & 0xFFFFu, L[g][2 * v] >> 16, L[g][2 * v + 1] & 0xFFFFu,
-                     L[g][2 * v + 1] >> 16);
-          }
-        }
-      }
-      // The run's sums go to S with one bulk reduction (two at a wrap) issued by lane 0: the
-      // tensor memory accelerator adds the staged 32-bit words (two packed u16 sums each, which
-      // cannot carry into each other, or one u32 sum when wide) into S atomically, element by
-      // element. The staging writes are made visible to that async proxy first.
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        const int n1 = (!SH0 && xs + n > W) ? W - xs : n;  // pixels before the wrap
-        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;"
-                     ::"l"(arun), "r"(sbuf), "r"(n1 * D * BPE) : "memory");
-        if (!SH0 && n1 < n)
-          asm volatile(
-              "cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;"
-              ::"l"(arun - (int64_t)xs * D * BPE), "r"(sbuf + n1 * D * BPE), "r"((n - n1) * D * BPE)
-              : "memory");
-        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      }
-      sbuf = sbuf == stage_s ? stage_s + stage_bytes : stage_s;
-      arun += astride;
-      if (!SH0) {
-        xs += dx;
-        if (--xw == 0) {  // chain 0 left the row at one side: back in at the other
-          xs -= dx * W;
-          arun -= dx * awrap;
-          xw = W;
         }
       }
     }
+    update(par, raw);
+    add_run(par, (!SH0 && xs + n > W) ? W - xs : n);  // pixels before the wrap
+    arun += astride;
+    if (!SH0) {
+      xs += dx;
+      if (xs >= W) {  // chain 0 left the row at one side: back in at the other
+        xs -= W;
+        arun -= awrap;
+      } else if (xs < 0) {
+        xs += W;
+        arun += awrap;
+      }
+    }
+    t++;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
   if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // adds complete
