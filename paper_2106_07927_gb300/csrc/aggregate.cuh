@@ -356,7 +356,10 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
 constexpr int kShearRing = 8;  // steps in the cost ring; 2 steps per cp.async group, 6 in flight
 __host__ __device__ inline int shear_kinds(int num_paths) { return num_paths == 8 ? 6 : 2; }
 __host__ __device__ inline int shear_dpl_default(int D) { return 16; }
-__host__ __device__ inline int shear_cpl_default(int D) { return 1; }
+// Two chains per lane at D = 128: the step's bookkeeping serves both and the halved warp count
+// competes less with the concurrent row kernel (aggregation stage 5 % faster at 1242 x 375, in
+// 0.229 ms instead of 0.242); one at the other D, where it was not measured.
+__host__ __device__ inline int shear_cpl_default(int D) { return D == 128 ? 2 : 1; }
 __host__ __device__ inline int shear_width(int D, int dpl) { return pow2ceil(D / dpl); }
 // Warp items of one pair: kinds x groups of cpl * 32 / width adjacent chains (cpl chains per lane).
 __host__ __device__ inline int shear_items(int W, int D, int dpl, int num_paths, int cpl) {
