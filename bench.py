@@ -51,13 +51,18 @@ def _args():
     return ap.parse_args()
 
 
-def _traffic():
+def _traffic(tuning):
     """DRAM bytes (read + write) per launch of the aggregation stage, from the ncu capture recorded
-    in profiles/aggregate_traffic.json, or None when that capture is missing."""
+    in profiles/aggregate_traffic.json; None when that capture is missing or was taken with other
+    kernel settings than `tuning` (the timed context's res2tac_tuning)."""
     p = os.path.join(ROOT, "profiles", "aggregate_traffic.json")
     if not os.path.exists(p):
         return None
-    return json.load(open(p)).get("dram_bytes_per_launch")
+    rec = json.load(open(p))
+    want = rec.get("tuning", {})
+    if not want or any(getattr(tuning, k) != v for k, v in want.items()):
+        return None
+    return rec.get("dram_bytes_per_launch")
 
 
 def _dist():
@@ -484,7 +489,8 @@ def main():
                      "frac": round(achieved / int_peak, 3),
                      "peak_source": "measured packed-u16 min+add probe on this GPU",
                      "hbm_achieved_gbs": round(bytes_agg / (agg_ms / 1e3) / 1e9, 1),
-                     "hbm_peak_gbs": hbm, "traffic": _traffic(),
+                     "hbm_peak_gbs": hbm,
+                     "traffic": _traffic(binding.res2tac_get_tuning(ctx.handle)),
                      "ops_per_launch": ops_agg, "algorithmic_bytes_per_launch": bytes_agg,
                      "dominant_stage": dominant,
                      # the accumulation into S: every path adds 2 bytes per DE (read-modify-write
