@@ -102,7 +102,9 @@ typedef struct res2tac_pair {
  * shear_dpl: disparities per lane of the column / diagonal path kernel: 8, 16 or 32, with
  *   D % shear_dpl == 0.
  * row_mode: 1 = both directions of a row in one lane group, 2 = one direction per group.
- * shear_cpl: chains per lane of the column / diagonal path kernel (1 or 2). */
+ * shear_cpl: chains per lane of the column / diagonal path kernel (1 or 2).
+ * Automatic values: agg_dpl 2 for D <= 64, 4 for D <= 128, else 8; agg_warps 2; wta_chunk 128;
+ * shear_dpl 16; row_mode 2; shear_cpl 2 at D = 128, else 1. */
 typedef struct res2tac_tuning {
   int32_t agg_dpl;
   int32_t agg_warps;
