@@ -1,8 +1,9 @@
 """Host model of the sheared-column aggregation kernel's walk schedule, checked against the
 definition of its chains.
 
-The kernel (`agg_shear_t`) walks the column and diagonal paths of the SGM recurrence (Sec. 2.2.2,
-the path term L_r of every direction r) as sheared chains: chain j of a kind with shear s visits
+The kernel (`agg_shear_t`) walks the column and diagonal paths of the SGM recurrence (the path
+term L_r of Eq. sgm_path, Sec. 2.1.2, computed along independent path lines as in Sec. 2.2.2) as
+sheared chains: chain j of a kind with shear s visits
 pixel x = (j + s y) mod W of every row, top-down or bottom-up, and restarts where x wraps around
 the image edge, because a new line of the path enters there. A warp owns n adjacent chains. Each
 step copies the costs of its run 6 steps ahead into an 8-slot ring and adds the step's sums into
