@@ -9,10 +9,11 @@
 //
 // GB300 mapping (not the paper's). Every path line is a sequential chain; a group of lanes walks
 // one chain with the D disparities spread over its lanes, held as packed u16x2 registers.
-// Neighbouring disparities cross lanes by one shuffle each way. S is accumulated with 64-bit
-// atomic adds of four packed u16 sums: no carry can cross a half while num_paths (255 + P2) <=
-// 65535; above that the sums are uint32 ("wide"). Integer addition is associative, so the order
-// in which directions arrive does not change S. Two kernels split the paths:
+// Neighbouring disparities cross lanes by one shuffle each way. S is accumulated with atomic adds
+// of packed u16 sums (64-bit red.add in the row kernel, TMA bulk add-reductions of 32-bit words in
+// the sheared kernel): no carry can cross a half while num_paths (255 + P2) <= 65535; above that
+// the sums are uint32 ("wide"). Integer addition is associative, so the order in which directions
+// arrive does not change S. Two kernels split the paths:
 //  - rows (LR, RL), the longest chains when W >= H. A group of 8..32 lanes walks a row with 2..8
 //    disparities per lane, either both directions interleaved (two chains for ILP) or one
 //    direction per group, and forms m with a pipelined reduction: writing
@@ -23,10 +24,12 @@
 //    step. Costs are fetched several steps ahead into a register ring.
 //  - sheared columns (TB, BT and, with 8 paths, the four diagonals). Each such path is walked row
 //    by row as W sheared chains of length H (see agg_shear), so the chains of one warp sit on
-//    adjacent pixels at every step. Lane groups hold 16 or 32 disparities per lane; the warp's
-//    cost vectors of a step (adjacent, so contiguous in memory) are copied into a shared-memory
-//    ring with cp.async several steps ahead, and its new L values are staged in shared memory and
-//    added to S by coalesced atomic adds that each cover whole pixel vectors.
+//    adjacent pixels at every step. Lane groups hold 8, 16 or 32 disparities per lane and one or
+//    two chains per lane; the warp's cost vectors of a step (adjacent, so contiguous in memory)
+//    are copied into a shared-memory ring with cp.async several steps ahead, and its new L values
+//    are staged in shared memory and added to S by one bulk reduction per step (two where the
+//    run wraps around the image edge). Pairs of steps that meet no wrap, restart or last-row
+//    event take a fast path without those tests (see agg_shear_t).
 #pragma once
 #include "common.cuh"
 
