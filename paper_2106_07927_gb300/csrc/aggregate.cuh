@@ -286,7 +286,25 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
       r[u] = (active && u < W) ? RC::load(cp) : Raw();
       if (u + 1 < W) cp += estride;
     }
-    for (int t0 = 0; t0 < W; t0 += U) {
+    int t0 = 0;
+    // Blocks whose steps and refills all lie inside the row (t0 + 2U < W) test for neither and
+    // add through a running pointer; the last blocks take the tested loop below.
+    constexpr int BPE = WIDE ? 4 : 2;
+    for (; t0 + 2 * U < W; t0 += U) {
+      uint8_t* sp = reinterpret_cast<uint8_t*>(pb.agg) + e * BPE;
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        uint32_t c[NP];
+        RC::unpack(r[u], c);
+        long_step<DPL, LPL, FULL>(L, mm, c, active, lig, P1P1, P2P2);
+        r[u] = active ? RC::load(cp) : Raw();  // step t0 + u + U
+        cp += estride;
+        if (active) add_lane<DPL, WIDE>(sp, 0, L);
+        sp += estride * BPE;
+      }
+      e += U * estride;
+    }
+    for (; t0 < W; t0 += U) {
 #pragma unroll
       for (int u = 0; u < U; u++) {
         const int t = t0 + u;
