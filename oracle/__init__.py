@@ -67,6 +67,8 @@ def _load():
         lib.r2o_ncc_cost_right.argtypes = [P, P, I64, I, I, I, I, P]
         lib.r2o_median3x3_f64.argtypes = [P, I, I, P]
         lib.r2o_sgm_subpixel.argtypes = [P, P, I64, I, I, I, I, I, I, I, I, I, I, P, P]
+        lib.r2o_ncc_round.argtypes = [I64, I64, I64]
+        lib.r2o_ncc_round.restype = ctypes.c_int
         for f in (lib.r2o_census, lib.r2o_cost, lib.r2o_path, lib.r2o_aggregate, lib.r2o_wta,
                   lib.r2o_right_disparity, lib.r2o_lr_check, lib.r2o_median3x3, lib.r2o_sgm,
                   lib.r2o_subpixel, lib.r2o_median3x3_f64, lib.r2o_sgm_subpixel,
@@ -111,6 +113,12 @@ def cost_right(ctl: np.ndarray, ctr: np.ndarray, D: int) -> np.ndarray:
     out = np.empty((H, W, D), np.uint8)
     _check(_load().r2o_cost_right(_ptr(ctl), _ptr(ctr), W, H, D, _ptr(out)), "cost_right")
     return out
+
+
+def ncc_round(cov: int, va: int, vb: int) -> int:
+    """k = round(255 max(0, cov / sqrt(va vb))), ties to even, decided on integers (the scaling
+    of the NCC cost; the cost is 255 - k)."""
+    return int(_load().r2o_ncc_round(int(cov), int(va), int(vb)))
 
 
 def ncc_cost(left: np.ndarray, right: np.ndarray, D: int, n: int,

@@ -4,7 +4,8 @@
  * TEST INFRASTRUCTURE. This file is the checker of the CUDA library, not part of it: only the
  * tests, the smoke check and the benchmark's CPU-baseline leg may load it. It shares no code,
  * header, table or helper with the CUDA path. It is deliberately slow and literal: one pixel,
- * one disparity, one direction at a time, int32 arithmetic, no SIMD, no threads, no blocking.
+ * one disparity, one direction at a time, int32 arithmetic (64- and 128-bit integers for the NCC
+ * sums), no floating point on the integer path, no SIMD, no threads, no blocking.
  *
  * What each function computes, with the passage it follows:
  *   r2o_census          census transform, Sec. 2.1.1 and Sec. 2.2.1 (zero-valued margin), the
@@ -31,7 +32,8 @@
  *                       truncated version of the normalized cross-correlation"):
  *                       s = 1 - max(0, Phi) with Phi the zero-mean NCC of the n x n patches
  *                       around (x, y) in the reference and (x -/+ d, y) in the matching image
- *                       (zero margin as for the census), scaled to 0..255 (see the function).
+ *                       (zero margin as for the census), scaled to 0..255 as 255 - k with
+ *                       k = round(255 max(0, Phi)) decided in exact integer arithmetic.
  *   r2o_s_at            S(p, .) at one pixel from the R path lines through it (each walked from
  *                       the pixel where it enters the image, costs computed on the way): the same
  *                       sums as r2o_aggregate, for sampled checks of images too large for it.
@@ -184,17 +186,43 @@ static int px_or_zero(const uint8_t* img, int64_t pitch, int W, int H, int x, in
   return img[(int64_t)y * pitch + x];
 }
 
+/* The integer k = round(255 max(0, Phi)), rounded half to even, for Phi = cov / sqrt(vA vB)
+ * (Sec. 2.1.1: the cost is the truncated 1 - max(0, Phi); the 8-bit scale 255 is this library's
+ * reading). Decided on integers alone, so no floating-point rounding order enters it:
+ *   k = 0 when cov <= 0 or a patch is constant (vA = 0 or vB = 0);
+ *   otherwise x = 255 Phi lies in (0, 255] (Cauchy-Schwarz) and, for m >= 1,
+ *     x >= m - 1/2  <=>  (510 cov)^2 >= (2m - 1)^2 vA vB      (both sides are squares of
+ *                                                               non-negative numbers),
+ *   so M = floor(x + 1/2) is the largest m in 0..255 for which that holds (m = 0 always does);
+ *   x + 1/2 = M exactly (a tie) when the two sides are equal, and a tie rounds to the even one of
+ *   M - 1 and M. Products reach 2^72 for 9 x 9 patches: 128-bit integers. */
+static int ncc_round_255phi(int64_t cov, int64_t vA, int64_t vB) {
+  if (cov <= 0 || vA <= 0 || vB <= 0) return 0;
+  const __int128 t = (__int128)(510 * cov) * (__int128)(510 * cov);
+  const __int128 v = (__int128)vA * (__int128)vB;
+  int lo = 0, hi = 255; /* the largest m with (2m - 1)^2 v <= t lies in [lo, hi] */
+  while (lo < hi) {
+    int m = (lo + hi + 1) / 2;
+    __int128 r = (__int128)(2 * m - 1) * (2 * m - 1) * v;
+    if (r <= t)
+      lo = m;
+    else
+      hi = m - 1;
+  }
+  if (lo >= 1 && (__int128)(2 * lo - 1) * (2 * lo - 1) * v == t && (lo & 1)) lo -= 1;
+  return lo;
+}
+
+/* Exported for the pins: k of ncc_round_255phi for given (cov, vA, vB). */
+int r2o_ncc_round(int64_t cov, int64_t vA, int64_t vB) { return ncc_round_255phi(cov, vA, vB); }
+
 /* Inverted, truncated NCC cost of one patch pair: reference patch centred at (xa, y) of A,
  * matching patch centred at (xb, y) of B, n x n, N = n^2 pixels, zero margin.
  *   sA = sum a, sB = sum b, sAA = sum a^2, sBB = sum b^2, sAB = sum a b   (exact integers)
  *   vA = N sAA - sA^2,  vB = N sBB - sB^2,  cov = N sAB - sA sB           (N^2 (co)variances)
  *   Phi = cov / sqrt(vA vB), taken as 0 when vA or vB is 0 (a constant patch);
- *   cost = 255 - clamp(round(255 max(0, Phi)), 0, 255), the truncated 1 - max(0, Phi) on 0..255.
- * The scaling to an 8-bit cost decides an integer in floating point, so it follows one fixed
- * sequence of correctly rounded fp32 operations (the precision of the GPU path):
- *   iA = 1 / sqrt(float(vA)) (0 when vA = 0), iB likewise, jB = 255 * iB,
- *   q = (float(cov) * iA) * jB,  cost = 255 - clamp(rint(q), 0, 255)  (rint: ties to even).
- * A cov <= 0 gives q <= 0 and so 255 (the max(0, .) truncation). */
+ *   cost = 255 - k, k = round(255 max(0, Phi)) (ties to even) from ncc_round_255phi: the
+ *   truncated 1 - max(0, Phi) on 0..255, with no floating point anywhere. */
 static uint8_t ncc_pair_cost(const uint8_t* A, const uint8_t* B, int64_t pitch, int W, int H,
                              int xa, int xb, int y, int n) {
   int r = n / 2, N = n * n;
@@ -210,15 +238,7 @@ static uint8_t ncc_pair_cost(const uint8_t* A, const uint8_t* B, int64_t pitch, 
       sAB += a * b;
     }
   int64_t vA = N * sAA - sA * sA, vB = N * sBB - sB * sB, cov = N * sAB - sA * sB;
-  volatile float iA = vA > 0 ? 1.0f / sqrtf((float)vA) : 0.0f;
-  volatile float iB = vB > 0 ? 1.0f / sqrtf((float)vB) : 0.0f;
-  volatile float jB = 255.0f * iB;
-  volatile float q = (float)cov * iA;
-  q = q * jB;
-  float k = rintf(q);
-  if (k < 0.0f) k = 0.0f;
-  if (k > 255.0f) k = 255.0f;
-  return (uint8_t)(255 - (int)k);
+  return (uint8_t)(255 - ncc_round_255phi(cov, vA, vB));
 }
 
 /* NCC cost volume with the left image as reference: C(x,y,d) = ncc_pair_cost(left patch at x,

@@ -37,6 +37,7 @@ struct Problem {
   uint8_t* flip;      // [2][H][W] right and left image, each flipped horizontally (exact check)
   uint16_t* dp;       // [H][W] D^L of that swapped, flipped pair (exact check); NULL: approximate
   uint2* nst;         // [2][H][W] patch sum and factor of the reference / matching image (NCC)
+  int32_t* nsv;       // [2][H][W] exact patch variance N sum a^2 - (sum a)^2 of both images (NCC)
 };
 
 // Method parameters shared by every pair of a call.

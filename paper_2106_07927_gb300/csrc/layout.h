@@ -8,7 +8,7 @@
 namespace r2t {
 
 struct Layout {
-  size_t cost, agg, dl, dr, kr, mask, flip, dp, nst, total;  // 0: buffer not used
+  size_t cost, agg, dl, dr, kr, mask, flip, dp, nst, nsv, total;  // 0: buffer not used
 };
 
 inline size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -16,7 +16,7 @@ inline size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 // Cost 1 B/DE, aggregated volume 2 B/DE (4 when wide), D^L and D^R 2 B/px each,
 // right-disparity keys 4 B/px, LR mask 1 B/px: 3 B per DE + 9 B per pixel. The exact
 // consistency check adds the swapped, flipped pair (2 B/px) and its D^L (2 B/px); the NCC cost
-// the patch statistics of both images (16 B/px).
+// the patch statistics of both images (16 B/px) and their exact patch variances (8 B/px).
 inline Layout layout_for(int W, int H, int D, bool wide, bool exact = false, bool ncc = false) {
   const size_t npx = (size_t)W * H, nde = npx * D;
   Layout l;
@@ -32,9 +32,10 @@ inline Layout layout_for(int W, int H, int D, bool wide, bool exact = false, boo
     l.flip = o; o = align256(o + npx * 2);
     l.dp = o; o = align256(o + npx * 2);
   }
-  l.nst = 0;
+  l.nst = l.nsv = 0;
   if (ncc) {  // 2 KB of slack in front (reads at a matching pixel x - d < 0 stay inside)
     l.nst = o + 2048; o = align256(o + 2048 + npx * 16);
+    l.nsv = o; o = align256(o + npx * 8);
   }
   l.total = o;
   return l;
@@ -56,6 +57,7 @@ inline Problem problem_at(char* base, const Layout& l, int W, int H, int D) {
   pb.flip = l.flip ? reinterpret_cast<uint8_t*>(base + l.flip) : nullptr;
   pb.dp = l.dp ? reinterpret_cast<uint16_t*>(base + l.dp) : nullptr;
   pb.nst = l.nst ? reinterpret_cast<uint2*>(base + l.nst) : nullptr;
+  pb.nsv = l.nsv ? reinterpret_cast<int32_t*>(base + l.nsv) : nullptr;
   return pb;
 }
 

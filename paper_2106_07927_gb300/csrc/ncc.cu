@@ -5,13 +5,16 @@
 // For the reference patch a (around x) and the matching patch b (around x - d), N = n^2:
 //   vA = N sum a^2 - (sum a)^2,  vB likewise,  cov = N sum a b - sum a sum b   (exact integers)
 //   Phi = cov / sqrt(vA vB)  (0 when vA or vB is 0)
-// and the 8-bit cost 255 - clamp(rint(255 max(0, Phi)), 0, 255), scaled in a fixed sequence of
-// correctly rounded fp32 operations: iA = 1 / sqrt(float(vA)) (0 when vA = 0), iB likewise,
-// jB = 255 iB, q = (float(cov) * iA) * jB, cost = 255 - clamp(rint(q), 0, 255). A cov <= 0
-// gives 255.
+// and the 8-bit cost 255 - k with k = round(255 max(0, Phi)), ties to even. k is a function of
+// the three integers alone. The kernel estimates x = 255 Phi in fp32 (iA = 1 / sqrt(vA),
+// jB = 255 / sqrt(vB) per pixel, q = (cov iA) jB, each correctly rounded): the relative error of q
+// is at most about 9 * 2^-24, under 1.4e-4 absolute for x <= 255. Where q lies farther than
+// 1/1024 from the nearest k + 1/2, rint(q) is k. Closer to a boundary the boundary f + 1/2
+// (f = floor q) is settled on integers: x > f + 1/2 <=> (510 cov)^2 > (2f + 1)^2 vA vB (128-bit
+// products), equality being a tie that goes to the even one of f and f + 1. A cov <= 0 gives 255.
 //
 // ncc_stats_kernel: per pixel, the patch sum and the factor (iA for the reference image, jB for
-// the matching one), as one 8-byte pair.
+// the matching one), as one 8-byte pair, and the exact variance v.
 // ncc_cost_kernel: a band of kNccTY rows x TX pixels x all D per block of 256 threads; thread
 // (x, g) owns disparities 4g .. 4g + 3 of pixel x. Down the band it forms, per image row, the
 // dot products of the patch rows (dp4a over byte words realigned from shared memory) and keeps
@@ -37,7 +40,8 @@ __host__ __device__ inline int ncc_tx(int D) { return 256 / (D / 4); }  // pixel
 // f = 1 / sqrt(float(vA)) (reference image) or 255 / ... as fl(255 * f) (matching image, scale255).
 template <int N_>
 __global__ void __launch_bounds__(256) ncc_stats_kernel(const uint8_t* img, int64_t pitch, int W,
-                                                        int H, uint2* st, bool scale255) {
+                                                        int H, uint2* st, int32_t* sv,
+                                                        bool scale255) {
   constexpr int R = N_ / 2, TW = 32 + 2 * R;
   __shared__ uint8_t t[8 + 2 * R][TW];
   const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8;
@@ -63,20 +67,50 @@ __global__ void __launch_bounds__(256) ncc_stats_kernel(const uint8_t* img, int6
   float f = v > 0 ? __fdiv_rn(1.0f, __fsqrt_rn(__int2float_rn(v))) : 0.0f;
   if (scale255) f = __fmul_rn(255.0f, f);
   st[(int64_t)y * W + x] = make_uint2((uint32_t)s1, __float_as_uint(f));
+  sv[(int64_t)y * W + x] = v;
 }
 
-// The 8-bit cost of one patch pair from its sums: 255 - sat_u8(rint((cov * iA) * jB)).
-__device__ __forceinline__ uint32_t ncc_cost_of(int nn, int sab, int sa, float ia, uint2 mb) {
-  const int cov = nn * sab - sa * (int)mb.x;  // |cov| < 2^29
+// Half-width of the band around k + 1/2 inside which the rounding is settled on integers; the
+// fp32 estimate is within 1.4e-4 of 255 Phi.
+constexpr float kNccTieBand = 1.0f / 1024.0f;
+
+// k = round(255 Phi) for cov > 0 when the estimate q lies within kNccTieBand of f + 1/2,
+// f = floor(q): the true value lies on one side of f + 1/2, found from
+// (510 cov)^2 vs (2f + 1)^2 vA vB (both < 2^72, compared as 128-bit unsigned); equal is a tie.
+__device__ __noinline__ uint32_t ncc_exact_k(int cov, int va, int vb, float q) {
+  const int f = (int)floorf(q);
+  const unsigned long long a = 510ull * (unsigned long long)cov;  // < 2^36
+  const unsigned long long tl = a * a, th = __umul64hi(a, a);
+  const unsigned long long r =
+      (unsigned long long)(2 * f + 1) * (unsigned long long)(2 * f + 1) * (unsigned long long)va;
+  const unsigned long long rl = r * (unsigned long long)vb;
+  const unsigned long long rh = __umul64hi(r, (unsigned long long)vb);
+  int k;
+  if (th > rh || (th == rh && tl > rl))
+    k = f + 1;  // above the boundary
+  else if (th < rh || tl < rl)
+    k = f;      // below it
+  else
+    k = (f & 1) ? f + 1 : f;  // on it: the even neighbour
+  return (uint32_t)min(k, 255);
+}
+
+// The 8-bit cost of one patch pair from its sums: 255 - k, k = rint((cov * iA) * jB) clamped to
+// 0..255, settled on integers near a rounding boundary (va_p, vb_p: the two exact variances, read
+// only then).
+__device__ __forceinline__ uint32_t ncc_cost_of(int nn, int sab, int sa, float ia, uint2 mb,
+                                                const int32_t* va_p, const int32_t* vb_p) {
+  const int cov = nn * sab - sa * (int)mb.x;  // |cov| < 2^27
   const float q = __fmul_rn(__fmul_rn(__int2float_rn(cov), ia), __uint_as_float(mb.y));
   uint32_t k;
   asm("cvt.rni.sat.u8.f32 %0, %1;" : "=r"(k) : "f"(q));  // rint, then clamp to 0 .. 255
+  if (cov > 0 && fabsf(q - floorf(q) - 0.5f) < kNccTieBand) k = ncc_exact_k(cov, *va_p, *vb_p, q);
   return 255u - k;
 }
 
 template <int N_>
 __global__ void __launch_bounds__(256, N_ == 5 ? 4 : 3)
-    ncc_cost_kernel(Problem pb, int agg_bytes_per_de, const uint2* st) {
+    ncc_cost_kernel(Problem pb, int agg_bytes_per_de, const uint2* st, const int32_t* sv) {
   constexpr int R = N_ / 2;
   constexpr int NW = (N_ + 3) / 4;  // dot-product words of a patch row
   __shared__ __align__(16) uint8_t sl[kNccMaxRows][kNccLStride];
@@ -220,11 +254,14 @@ __global__ void __launch_bounds__(256, N_ == 5 ? 4 : 3)
     if (t >= 2 * R) {  // output row y0 + t - 2R
       const uint2 a = *sa_p;
       const uint2* mb = sa_p + mo;
+      const int32_t* va = sv + (sa_p - st);  // exact variances, same indexing as the stats
       uint32_t c[4];
 #pragma unroll
       for (int k = 0; k < 4; k++) {
-        const uint32_t v = ncc_cost_of(nn, vs[k], (int)a.x, __uint_as_float(a.y), mb[-k]);
-        c[k] = inside[k] ? v : (uint32_t)kCostOutside;
+        // outside (x - d < 0) the cost is 255 and the variances are not read
+        c[k] = inside[k] ? ncc_cost_of(nn, vs[k], (int)a.x, __uint_as_float(a.y), mb[-k], va,
+                                       va + mo - k)
+                         : (uint32_t)kCostOutside;
       }
       *out = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
       sa_p += W;
@@ -245,22 +282,24 @@ template <int N_>
 cudaError_t launch_ncc_n(const Problem& pb, const Method& mt, cudaStream_t s) {
   const int64_t npx = (int64_t)pb.W * pb.H;
   const dim3 sg((pb.W + 31) / 32, (pb.H + 7) / 8);
-  ncc_stats_kernel<N_><<<sg, 256, 0, s>>>(pb.left, pb.in_pitch, pb.W, pb.H, pb.nst, false);
-  ncc_stats_kernel<N_><<<sg, 256, 0, s>>>(pb.right, pb.in_pitch, pb.W, pb.H, pb.nst + npx, true);
+  ncc_stats_kernel<N_><<<sg, 256, 0, s>>>(pb.left, pb.in_pitch, pb.W, pb.H, pb.nst, pb.nsv,
+                                          false);
+  ncc_stats_kernel<N_><<<sg, 256, 0, s>>>(pb.right, pb.in_pitch, pb.W, pb.H, pb.nst + npx,
+                                          pb.nsv + npx, true);
   const int TX = ncc_tx(pb.D);
   const int blocks = ((pb.W + TX - 1) / TX) * ((pb.H + kNccTY - 1) / kNccTY);
   const int ring_smem = N_ > 5 ? N_ * 256 * 16 : 0;
   if (ring_smem)
     cudaFuncSetAttribute(ncc_cost_kernel<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          ring_smem);
-  ncc_cost_kernel<N_><<<blocks, 256, ring_smem, s>>>(pb, mt.wide ? 4 : 2, pb.nst);
+  ncc_cost_kernel<N_><<<blocks, 256, ring_smem, s>>>(pb, mt.wide ? 4 : 2, pb.nst, pb.nsv);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_ncc_cost(const Problem& pb, const Method& mt, cudaStream_t s) {
-  if (!pb.nst || pb.D % 16 != 0 || pb.D > 256) return cudaErrorInvalidValue;
+  if (!pb.nst || !pb.nsv || pb.D % 16 != 0 || pb.D > 256) return cudaErrorInvalidValue;
   if (mt.cw == 5) return launch_ncc_n<5>(pb, mt, s);
   if (mt.cw == 9) return launch_ncc_n<9>(pb, mt, s);
   return cudaErrorInvalidValue;

@@ -82,3 +82,80 @@ def test_batch_wide_and_four_paths():
         for (L, R, (W, H, D)), got in zip(items, outs):
             assert np.array_equal(got, oracle.sgm(L, R, D, 5, 5, 10, P2, R_, 3))
         ctx.close()
+
+
+LIMIT_DE = 1242 * 375 * 128  # pairs up to this size are compared with the full oracle
+
+
+def _batch64_inputs():
+    """The 64 uneven pairs of the batch workload (sizes from scenes.batch_specs(0, 64)), each
+    cropped from one 1920 x 1080 scene per (kind, D), as the benchmark makes them."""
+    specs = scenes.batch_specs(0, 64)
+    masters, items = {}, []
+    for s in specs:
+        p = s["prm"]
+        key = (s["kind"], p["max_disp"])
+        if key not in masters:
+            masters[key] = scenes.make_scene(s["kind"], 17 + len(masters), 1920, 1080,
+                                             p["max_disp"])[:2]
+        L, R = masters[key]
+        W, H, D = p["width"], p["height"], p["max_disp"]
+        items.append((np.ascontiguousarray(L[:H, :W]), np.ascontiguousarray(R[:H, :W]), (W, H, D)))
+    return items
+
+
+def _sample_points(W, H, D, rng, n=32):
+    pts = [(0, 0), (W - 1, 0), (0, H - 1), (W - 1, H - 1), (W // 2, 0), (W // 2, H - 1),
+           (0, H // 2), (W - 1, H // 2), (min(D, W) - 1, H // 3), (W // 2, H // 2)]
+    while len(pts) < n:
+        pts.append((int(rng.integers(0, W)), int(rng.integers(0, H))))
+    return pts
+
+
+def test_batch_of_64_uneven_pairs_against_oracle():
+    """The 64-pair batch workload (W up to 1920, H up to 1080, D up to 256, D > W allowed) in one
+    batch call, LR check and median on: every pair equal to its single-pair launch, every pair
+    of at most 1242 x 375 x 128 disparity estimates equal to the full oracle. Then the same batch
+    with WTA only: D^L of every D = 256 pair and of the 1920 x 1080 pairs at 32 sampled pixels
+    (corners, borders, interior) equal to the argmin of the oracle's sums there."""
+    import concurrent.futures
+    import torch
+    items = _batch64_inputs()
+    shapes = [s for _, _, s in items]
+    tensors = [(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()) for L, R, _ in items]
+    oracle._load()
+    pool = concurrent.futures.ThreadPoolExecutor(16)  # the oracle releases the GIL in C
+    small = [i for i, (W, H, D) in enumerate(shapes) if W * H * D <= LIMIT_DE]
+    assert len(small) >= 8
+    assert any(D == 256 for i in small for (_, _, D) in [shapes[i]])
+    refs = {i: pool.submit(oracle.sgm, items[i][0], items[i][1], shapes[i][2], 9, 7, 10, 120, 8,
+                           3) for i in small}
+    ctx = binding.Stereo(scenes.params(64, 64, 64, 9, 7, 10, 120, 8, 3))
+    outs = _run_batch(ctx.handle, tensors, shapes)
+    for i, ((L, R), (W, H, D)) in enumerate(zip(tensors, shapes)):
+        single = binding.Stereo(scenes.params(W, H, D, 9, 7, 10, 120, 8, 3))
+        s_out = single.compute(L, R)
+        torch.cuda.synchronize()
+        assert np.array_equal(binding.u16(s_out), outs[i]), (i, W, H, D)
+        single.close()
+    for i in small:
+        assert np.array_equal(outs[i], refs[i].result()), (i, shapes[i])
+    ctx.close()
+
+    # WTA only: the map is D^L, checked at sampled pixels of the large pairs
+    big = [i for i, (W, H, D) in enumerate(shapes) if D == 256 or (W, H) == (1920, 1080)]
+    assert any((W, H) == (1920, 1080) for (W, H, _) in (shapes[i] for i in big))
+    assert any(W == 320 and D == 256 for (W, _, D) in (shapes[i] for i in big))
+    ctx = binding.Stereo(scenes.params(64, 64, 64, 9, 7, 10, 120, 8, 0))
+    outs = _run_batch(ctx.handle, tensors, shapes)
+    ctx.close()
+    rng = np.random.default_rng(11)
+    jobs = []
+    for i in big:
+        W, H, D = shapes[i]
+        for (x, y) in _sample_points(W, H, D, rng):
+            jobs.append((i, x, y, pool.submit(oracle.s_at, items[i][0], items[i][1], D, 9, 7, 10,
+                                              120, 8, 0, x, y)))
+    for i, x, y, f in jobs:
+        assert outs[i][y, x] == int(np.argmin(f.result())), (i, shapes[i], x, y)
+    pool.shutdown()

@@ -271,6 +271,29 @@ def test_ncc_ragged_tiles(W, H, D, n):
     _assert_same(left, right, scenes.params(W, H, D, n, n, 90, 880, 8, 3 | NCC))
 
 
+@pytest.mark.parametrize("n", [5, 9])
+def test_ncc_near_tie_patches(n):
+    """Patch pairs whose 255 Phi lies within 1e-6 of k + 1/2, side by side in one n-row image
+    (pair i in columns [i n, (i + 1) n), so the patch at its centre is exactly that pair): the
+    kernel's fp32 estimate cannot tell those roundings apart and must settle them on integers.
+    Cost volume, sums and maps bit-exact against the oracle; the centre costs against exact
+    decimal arithmetic."""
+    from test_oracle_pins import _k_decimal, _near_tie_patch_pairs
+    pairs = _near_tie_patch_pairs(n, 600 + n, want=24)
+    left = np.concatenate([a.reshape(n, n) for a, _ in pairs], axis=1).astype(np.uint8)
+    right = np.concatenate([b.reshape(n, n) for _, b in pairs], axis=1).astype(np.uint8)
+    H, W = left.shape
+    prm = scenes.params(W, H, 16, n, n, 90, 880, 8, 3 | NCC)
+    _, got = _gpu(left, right, prm)
+    r, N = n // 2, n * n
+    for i, (a, b) in enumerate(pairs):
+        sA, sB = int(a.sum()), int(b.sum())
+        k = _k_decimal(N * int((a * b).sum()) - sA * sB, N * int((a * a).sum()) - sA * sA,
+                       N * int((b * b).sum()) - sB * sB)
+        assert got["cost"][r, i * n + r, 0] == 255 - k, i
+    _assert_same(left, right, prm)
+
+
 def test_ncc_saturated_sums_exact_check_padded_pitches():
     rng = np.random.default_rng(8)
     W, H, D = 140, 70, 64

@@ -495,6 +495,111 @@ def test_ncc_cost_matches_numpy_corrcoef(n):
     assert checked > 0.95 * H * W * D / 2
 
 
+def _k_decimal(cov, va, vb):
+    """round(255 max(0, cov / sqrt(va vb))), ties to even, in 80-digit decimal arithmetic: an
+    independent statement of the NCC cost's scaling (exact where sqrt(va vb) is an integer, and
+    80 digits resolve every other case)."""
+    import decimal
+    if cov <= 0 or va <= 0 or vb <= 0:
+        return 0
+    ctx = decimal.Context(prec=80, rounding=decimal.ROUND_HALF_EVEN)
+    x = ctx.divide(ctx.multiply(decimal.Decimal(255), decimal.Decimal(cov)),
+                   ctx.sqrt(decimal.Decimal(va) * decimal.Decimal(vb)))
+    return int(x.quantize(decimal.Decimal(1), rounding=decimal.ROUND_HALF_EVEN, context=ctx))
+
+
+def test_ncc_round_exact_ties_go_to_even():
+    # Phi = (2m - 1) / 510 exactly puts 255 Phi on m - 1/2: the even one of m - 1 and m wins
+    for m in range(1, 256):
+        for s, t in ((1, 1), (7, 1), (3, 5), (101, 2)):
+            va, vb, cov = 510 * s * t * t, 510 * s, (2 * m - 1) * s * t
+            want = m - 1 if (m - 1) % 2 == 0 else m
+            assert oracle.ncc_round(cov, va, vb) == want == _k_decimal(cov, va, vb), (m, s, t)
+    # the end points and the truncation
+    assert oracle.ncc_round(1, 510 * 510, 1) == 0 and _k_decimal(1, 510 * 510, 1) == 0  # 1/2
+    assert oracle.ncc_round(3, 510 * 510, 1) == 2 and _k_decimal(3, 510 * 510, 1) == 2  # 3/2
+    assert oracle.ncc_round(0, 5, 7) == 0 and oracle.ncc_round(-9, 5, 7) == 0
+    assert oracle.ncc_round(5, 0, 7) == 0 and oracle.ncc_round(5, 7, 0) == 0
+    assert oracle.ncc_round(12345, 12345, 12345) == 255
+
+
+def test_ncc_round_near_ties_against_decimal():
+    # (cov, vA, vB) in the ranges of 9 x 9 patches (< 2^27) with 255 Phi within about 1e-9 of
+    # k + 1/2, on both sides
+    rng = np.random.default_rng(5)
+    checked = 0
+    for _ in range(3000):
+        va, vb = (int(v) for v in rng.integers(1, 1 << 27, 2))
+        k = int(rng.integers(0, 255))
+        cov = int(round((k + 0.5) * (va * vb) ** 0.5 / 255))
+        for c in (cov - 1, cov, cov + 1):
+            if 0 < c and c * c <= va * vb:
+                assert oracle.ncc_round(c, va, vb) == _k_decimal(c, va, vb), (c, va, vb)
+                checked += 1
+    assert checked > 5000
+
+
+def _near_tie_patch_pairs(n, seed, tol=1e-6, want=8):
+    """Seeded n x n patch pairs (a, b) whose 255 Phi lies within tol of some k + 1/2: random pairs,
+    with one pixel of b swept over 0..255, screened in float64 (exact enough to select)."""
+    rng = np.random.default_rng(seed)
+    N = n * n
+    v = np.arange(256)
+    found = []
+    for _ in range(200):
+        K = 4096
+        a = rng.integers(0, 256, (K, N)).astype(np.int64)
+        b = np.clip(a + rng.integers(-60, 61, (K, N)), 0, 255).astype(np.int64)
+        sA, sAA = a.sum(1), (a * a).sum(1)
+        sB = b[:, 1:].sum(1)[:, None] + v
+        sBB = (b[:, 1:] ** 2).sum(1)[:, None] + v * v
+        sAB = (a[:, 1:] * b[:, 1:]).sum(1)[:, None] + a[:, :1] * v
+        vA = (N * sAA - sA * sA)[:, None]
+        vB = N * sBB - sB * sB
+        cov = N * sAB - sA[:, None] * sB
+        ok = (cov > 0) & (vB > 0) & (vA > 0)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            x = 255.0 * cov / np.sqrt(vA.astype(np.float64) * vB)
+        dist = np.abs(x - np.floor(x) - 0.5)
+        for i, j in np.argwhere(ok & (dist < tol)):
+            bb = b[i].copy()
+            bb[0] = j
+            found.append((a[i].copy(), bb))
+        if len(found) >= want:
+            break
+    return found[:want]
+
+
+@pytest.mark.parametrize("n", [5, 9])
+def test_ncc_cost_near_tie_patches_against_exact_rationals(n):
+    """Patch pairs within 1e-6 of a rounding boundary: the oracle's cost equals 255 - k with k
+    from exact arithmetic; the two fp32 evaluation orders ((cov iA) iB) 255 and (cov iA)(255 iB)
+    disagree on some of them and each misses k on some, so this pin separates the integer
+    definition from either."""
+    pairs = _near_tie_patch_pairs(n, 600 + n, want=24)
+    assert len(pairs) >= 20
+    r, N = n // 2, n * n
+    f32 = np.float32
+    disagree = miss0 = miss1 = 0
+    for a, b in pairs:
+        sA, sB = int(a.sum()), int(b.sum())
+        va = N * int((a * a).sum()) - sA * sA
+        vb = N * int((b * b).sum()) - sB * sB
+        cov = N * int((a * b).sum()) - sA * sB
+        k = _k_decimal(cov, va, vb)
+        L = a.reshape(n, n).astype(np.uint8)
+        R = b.reshape(n, n).astype(np.uint8)
+        assert oracle.ncc_cost(L, R, 1, n)[r, r, 0] == 255 - k
+        ia = f32(1) / np.sqrt(f32(va))
+        ib = f32(1) / np.sqrt(f32(vb))
+        q0 = ((f32(cov) * ia) * ib) * f32(255)
+        q1 = (f32(cov) * ia) * (f32(255) * ib)
+        disagree += int(np.rint(q0) != np.rint(q1))
+        miss0 += int(np.rint(q0) != k)
+        miss1 += int(np.rint(q1) != k)
+    assert disagree >= 1 and miss0 >= 1 and miss1 >= 1
+
+
 @pytest.mark.parametrize("n", [5, 9])
 def test_ncc_cost_special_cases(n):
     rng = np.random.default_rng(80 + n)
