@@ -45,10 +45,11 @@ extern "C" {
 /* NCC matching cost (Sec. 2.1.1, Sec. 2.2.1 "Inverted and truncated version of the normalized
  * cross-correlation") instead of the census: s = 1 - max(0, Phi) with Phi the zero-mean NCC of
  * the census_w x census_h patches (5 x 5 or 9 x 9; zero margin outside the image), on the same
- * 8-bit cost scale: cost = 255 - clamp(rint(q), 0, 255), q = ((float(cov) * iA) * iB) * 255 in
- * correctly rounded fp32 steps, where for N = n^2 the integers cov = N sum ab - sum a sum b,
- * vA = N sum a^2 - (sum a)^2 (vB likewise) and iA = 1 / sqrt(float(vA)), 0 when vA = 0 (a constant
- * patch: cost 255). 255 where x - d < 0. Single pairs only: res2tac_compute_batch rejects it. */
+ * 8-bit cost scale: cost = 255 - k, k = round(255 max(0, Phi)) with ties to even, where for
+ * N = n^2 the integers cov = N sum ab - sum a sum b, vA = N sum a^2 - (sum a)^2 (vB likewise) give
+ * Phi = cov / sqrt(vA vB), and Phi = 0 when vA or vB is 0 (a constant patch: cost 255). k is exact
+ * (settled on integers wherever an fp32 estimate could round either way). 255 where x - d < 0.
+ * Single pairs only: res2tac_compute_batch rejects it. */
 #define RES2TAC_NCC 8
 
 #define RES2TAC_INVALID 0xFFFF /* disparity of a pixel rejected by the left-right check */
@@ -247,19 +248,6 @@ int res2tac_last_launch_count(res2tac_t h);
 int res2tac_set_profiling(res2tac_t h, int enable);
 int res2tac_stage_times(res2tac_t h, float* ms, int n);
 
-/* Integer-throughput probe (measurement aid, not part of the method): runs independent chains
- * of packed u16x2 min and add instructions on every SM for about `iters` iterations on stream s
- * and returns the sustained rate in 16-bit lane operations per second (one packed instruction
- * counts two) through *lane_ops_per_s. Synchronises s. */
-int res2tac_probe_int_peak(int iters, res2tac_stream_t s, double* lane_ops_per_s);
-
-/* Reduction-throughput probe (measurement aid, not part of the method): allocates a device buffer
- * of `bytes` bytes (>= 1024) on stream s, adds 32-bit ones into all of it `passes` times with TMA
- * bulk add-reductions of 1 KB (the way the column / diagonal aggregation adds its runs into the
- * aggregated volume), frees it, and returns the sustained rate in bytes reduced per second through
- * *bytes_per_s. Synchronises s. RES2TAC_ENOMEM if the buffer does not fit. */
-int res2tac_probe_red_peak(int64_t bytes, int32_t passes, res2tac_stream_t s, double* bytes_per_s);
-
 /* No-allocation variant of res2tac_compute. The paper has no counterpart: it is an addition for
  * callers that must not allocate device memory while they run, for example an onboard stereo loop
  * that is only allowed to allocate at start-up, a plugin whose host framework owns every byte of
@@ -273,9 +261,10 @@ int res2tac_probe_red_peak(int64_t bytes, int32_t passes, res2tac_stream_t s, do
  * that array until the process exits.
  * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 9 B per pixel,
  * 5 B per W*H*D when num_paths * (255 + p2) > 65535, 4 B more per pixel with RES2TAC_EXACT_CC,
- * 16 B more per pixel with RES2TAC_NCC)
+ * 24 B more per pixel and 2 KB with RES2TAC_NCC)
  * is rejected with RES2TAC_ENOMEM and a
- * message giving both sizes; 640 x 480 with D = 64 fits.
+ * message giving both sizes. 640 x 480 with D = 64 fits with 16-bit sums
+ * (num_paths * (255 + p2) <= 65535: about 62 MB) but not with 32-bit ones (about 101 MB).
  * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
  * Sharing: every call in the process uses the same array, which keeps the contents of the last

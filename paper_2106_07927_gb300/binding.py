@@ -29,12 +29,14 @@ EXPORTS = (
     "res2tac_debug_outputs", "res2tac_workspace_bytes", "res2tac_batch_workspace_bytes",
     "res2tac_get_tuning", "res2tac_set_tuning", "res2tac_autotune", "res2tac_last_launch_count",
     "res2tac_destroy", "res2tac_strerror", "res2tac_last_error", "res2tac_set_profiling",
-    "res2tac_stage_times", "res2tac_probe_int_peak", "res2tac_probe_red_peak",
+    "res2tac_stage_times",
     "res2tac_batch_reserve",
     "res2tac_compute_static",
     "res2tac_compute_subpixel", "res2tac_debug_subpixel",
     "res2tac_rectify", "res2tac_set_rectification", "res2tac_compute_raw",
 )
+# Every symbol include/res2tac_measure.h declares (measurement aids of the benchmark).
+MEASURE_EXPORTS = ("res2tac_probe_int_peak", "res2tac_probe_red_peak")
 RES2TAC_STATIC_SCRATCH_BYTES = 80 << 20
 STAGES = ("census_cost", "aggregate", "wta_dr", "lr_median")
 

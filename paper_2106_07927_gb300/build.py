@@ -33,7 +33,7 @@ def nvcc() -> str:
 
 def _sources():
     return (glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
-            glob.glob(os.path.join(CSRC, "*.h")) + [os.path.join(INCLUDE, "res2tac.h")])
+            glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
 def is_stale() -> bool:

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "../../include/res2tac.h"
+#include "../../include/res2tac_measure.h"
 #include "batch.h"
 #include "launch.h"
 #include "layout.h"

@@ -6,22 +6,23 @@ import pytest
 
 from paper_2106_07927_gb300 import binding
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
-                      "res2tac.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
 
 
-def _declared():
-    src = open(HEADER).read()
+def _declared(header="res2tac.h"):
+    src = open(os.path.join(INCLUDE, header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(res2tac_\w+)\s*\(", src)))
 
 
 def test_header_declarations_match_binding(cuda_lib):
     assert _declared() == sorted(binding.EXPORTS)
+    assert _declared("res2tac_measure.h") == sorted(binding.MEASURE_EXPORTS)
+    assert sorted(os.listdir(INCLUDE)) == ["res2tac.h", "res2tac_measure.h"]
 
 
 def test_library_exports_every_declared_symbol(cuda_lib):
-    for name in _declared():
+    for name in _declared() + _declared("res2tac_measure.h"):
         assert hasattr(cuda_lib, name), name
 
 

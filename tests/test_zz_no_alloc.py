@@ -68,6 +68,25 @@ def test_static_entry_exact_check_matches_context_entry():
     assert np.array_equal(binding.u16(got), expected)
 
 
+def test_static_entry_wide_sums_and_ncc_after_a_narrow_call():
+    """The two other layouts of the shared array: 32-bit sums (num_paths (255 + p2) > 65535,
+    4 B per disparity estimate) and the NCC cost (patch statistics and variances placed after the
+    maps), each called right after a call of another layout, so each starts from the previous
+    call's contents; compared with res2tac_compute."""
+    import torch
+    narrow = scenes.single_pair("320x240_d64_ct5x5_r4", 2)
+    lw, rw, _ = scenes.make_scene("road", 12, 160, 120, 64)
+    wide = (lw, rw, None, scenes.params(160, 120, 64, 9, 7, 10, 9000, 8, 3))
+    ln, rn, _ = scenes.make_scene("nadir", 13, 150, 100, 64)
+    ncc = (ln, rn, None, scenes.params(150, 100, 64, 5, 5, 90, 880, 8, 3 | binding.RES2TAC_NCC))
+    cases = (narrow, wide, ncc, wide)
+    expected = [_with_context(c[0], c[1], c[3]) for c in cases]
+    for c, want in zip(cases, expected):
+        got = _static_call(c[0], c[1], c[3])
+        torch.cuda.synchronize()
+        assert np.array_equal(binding.u16(got), want)
+
+
 def test_static_entry_rejects_a_problem_larger_than_its_array():
     import torch
     prm = scenes.params(1242, 375, 128, 9, 7, 10, 120, 8, 3)  # needs about 190 MB
