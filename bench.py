@@ -5,10 +5,14 @@ Default (N = 1): the 1242x375 pair, D = 128, census 9x7, 8 paths, P1 = 10, P2 = 
 3x3 median, one res2tac_compute per step on device-resident inputs, L2 flushed between steps
 (a 256 MB write outside the per-step events). Also measured in the same run and reported in the
 same JSON line:
-  - e2e: the same pair through res2tac_compute_host from pinned host buffers (upload, compute,
-    download, synchronise), as the paper times its pipeline;
+  - e2e: four pairs of the workload in turn through res2tac_compute_host from pinned host
+    buffers (transfers, compute, synchronise; L2 flushed before each step), as the paper times
+    its pipeline, and the same with one staged cudaMemcpyAsync per image and for the map;
   - batched: 64 pairs of uneven W, H, D in one res2tac_compute_batch call (persistent kernels
     under a CUDA graph) vs the same 64 pairs as per-pair res2tac_compute launches;
+  - serving: 10,000 Poisson arrivals (the batch sizes plus 5 % 3840x2160, D = 256) at each of
+    200, 500, 1000, 2000 and 5000 pairs/s through the continuous-batching server, p50 / p99 /
+    p99.9 latency per rate; a 1 % sample checked against the CPU oracle after the sweep;
   - roofline of the dominant kernel (path aggregation) from CUDA events recorded around it on its
     own stream, against the measured packed-u16 integer rate (and the measured HBM copy rate);
   - cpu_baseline: the single-threaded C oracle on the same pair, on the host cores.
@@ -44,8 +48,8 @@ def _args():
     ap.add_argument("--batch-pairs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-batch", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=1000)
-    ap.add_argument("--serve-rate", type=float, default=500.0)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rates", default="200,500,1000,2000,5000")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -189,6 +193,57 @@ def _batch_inputs(n, torch):
         out.append((torch.from_numpy(L[:H, :W].copy()).cuda(),
                     torch.from_numpy(R[:H, :W].copy()).cuda(), W, H, D))
     return out
+
+
+def _serving_sweep(args, torch, np):
+    """Continuous batching over 4 streams (serve.Server): the same 10,000 requests (sizes of the
+    batch workload plus 5 % 3840x2160 with D = 256, Poisson arrivals) at each arrival rate;
+    latency = completion - arrival. A 1 % sample (the same requests at every rate) must give the
+    same map at every rate and equal the CPU oracle (checked after the sweep, off the clock)."""
+    import concurrent.futures
+
+    import oracle
+    from paper_2106_07927_gb300 import binding, serve
+    srv = serve.Server(n_streams=4, max_batch=16)
+    rates = [float(r) for r in args.serve_rates.split(",")]
+    n = args.serve_requests
+    idx = sorted(np.random.default_rng(1).choice(n, max(1, n // 100), replace=False).tolist())
+    pool, per_rate, first, same, launches = None, [], None, True, 0
+    for rate in rates:
+        reqs, pool = serve.make_requests(torch, n, rate, 0, 0.05, pool)
+        warm, _ = serve.make_requests(torch, 32, rate, 1, 0.05, pool)
+        srv.run(warm)
+        l0 = srv.launches
+        st = srv.run(reqs)
+        st["rate_per_s"] = rate
+        st["gpu_launches"] = srv.launches - l0
+        launches += st["gpu_launches"]
+        served_per_s = st["served"] / max(st["span_s"], 1e-9)
+        st["served_pairs_per_s"] = round(served_per_s, 1)
+        st["keeps_up"] = bool(served_per_s >= 0.95 * rate)
+        outs = {i: binding.u16(reqs[i].out) for i in idx}
+        if first is None:
+            first = (outs, {i: (reqs[i].left.cpu().numpy(), reqs[i].right.cpu().numpy(),
+                                reqs[i].D) for i in idx})
+        else:
+            same = same and all(np.array_equal(outs[i], first[0][i]) for i in idx)
+        per_rate.append(st)
+        del reqs
+    srv.close()
+    # the sample against the oracle (single-threaded C per pair, pairs in parallel threads: the
+    # oracle's ctypes calls release the GIL)
+    oracle._load()
+    with concurrent.futures.ThreadPoolExecutor(os.cpu_count() or 4) as ex:
+        futs = {i: ex.submit(oracle.sgm, L, R, D, 9, 7, 10, 120, 8, 3)
+                for i, (L, R, D) in first[1].items()}
+        mism = sum(not np.array_equal(first[0][i], f.result()) for i, f in futs.items())
+    kept = [p["rate_per_s"] for p in per_rate if p["keeps_up"]]
+    return {"per_rate": per_rate, "streams": 4, "max_batch": 16, "requests_per_rate": n,
+            "max_sustained_rate_per_s": max(kept) if kept else None,
+            "sample_checked_vs_oracle": len(idx), "sample_mismatches_vs_oracle": int(mism),
+            "sample_same_at_every_rate": bool(same), "gpu_launches": launches,
+            "sizes": "as the batch, plus 5 % 3840x2160 with D = 256",
+            "keeps_up": "served pairs/s >= 0.95 x the arrival rate"}
 
 
 def main():
@@ -413,6 +468,8 @@ def main():
                 bpairs.append(binding.res2tac_pair(Lb.data_ptr(), Rb.data_ptr(), w, o.data_ptr(),
                                                    2 * w, w, h, d, 0))
             bde = sum(w * h * d for _, _, w, h, d in pairs_in)
+            # the batch autotuner (per bucket of D and size class) before the timed batches
+            table, ms_def, ms_tuned = binding.res2tac_autotune_batch(bctx.handle, bpairs, sh)
             for _ in range(2):
                 binding.res2tac_compute_batch(bctx.handle, bpairs, sh)
             torch.cuda.synchronize()
@@ -459,6 +516,10 @@ def main():
                                       "ms_per_batch": round(1e3 * t_single, 3)},
                 "speedup_vs_per_pair": round(t_single / t_batch, 3),
                 "bit_identical_to_per_pair": bool(same),
+                "autotune": {"table": [e.as_dict() for e in table],
+                             "mde_per_s_default": round(bde / (ms_def / 1e3) / 1e6, 1),
+                             "mde_per_s_tuned": round(bde / (ms_tuned / 1e3) / 1e6, 1),
+                             "ms_default": round(ms_def, 3), "ms_tuned": round(ms_tuned, 3)},
                 "sizes": "W in {320,640,1024,1242,1920}, H in {240,375,512,768,1080}, "
                          "D in {64,128,256}, seed 0",
             }
@@ -467,24 +528,7 @@ def main():
             bctx.close()
         serving = None
         if not args.no_serve and rank == 0:
-            # continuous batching over 4 streams: Poisson arrivals of uneven pairs (5 % 3840x2160,
-            # D = 256), admitted by device memory; latency = completion - arrival
-            from paper_2106_07927_gb300 import serve
-            srv = serve.Server(n_streams=4, max_batch=16)
-            reqs, pool = serve.make_requests(torch, args.serve_requests, args.serve_rate, 0, 0.05)
-            warm, _ = serve.make_requests(torch, 32, args.serve_rate, 1, 0.05, pool)
-            srv.run(warm)
-            l0 = srv.launches
-            serving = srv.run(reqs)
-            rng = np.random.default_rng(1)
-            idx = sorted(rng.choice(len(reqs), max(1, len(reqs) // 100), replace=False))
-            serving.update({
-                "rate_per_s": args.serve_rate, "streams": 4, "max_batch": 16,
-                "gpu_launches": srv.launches - l0,
-                "sample_checked_vs_single_pair": len(idx),
-                "sample_mismatches": len(serve.check_alone(srv, reqs, idx)),
-                "sizes": "as the batch, plus 5 % 3840x2160 with D = 256"})
-            srv.close()
+            serving = _serving_sweep(args, torch, np)
     mean_ms = max_over_ranks(sum(step_ms) / len(step_ms))
     value = ws * de / (mean_ms / 1e3) / 1e6
     subpixel["throughput_vs_integer_step"] = round(mean_ms / subpixel["ms_per_step"], 3)

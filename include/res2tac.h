@@ -237,6 +237,42 @@ int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int
                      uint16_t* disp, int64_t out_pitch, res2tac_stream_t s,
                      res2tac_tuning* best);
 
+/* Kernel settings of the batch engine for one bucket of pairs (not in the paper: batching is
+ * this library's addition). A pair's bucket is its D together with its size class (large = 1
+ * when width * height >= 2^18 pixels, else 0); every pair of a bucket runs with the bucket's
+ * settings, which change the schedule only, never the results (bit-identical maps).
+ *   row_dpl    disparities per lane of the row paths (LR, RL): 2, 4 or 8, D / row_dpl <= 32
+ *   shear_dpl, shear_cpl  disparities and chains per lane of the column and diagonal paths:
+ *              (16, 1) or (16, 2)
+ *   wta_px     pixels per WTA / right-disparity tile: 64, 128 or 256 (fewer when the tile's sums
+ *              would exceed 64 KB)
+ * Defaults: row_dpl 2 / 4 / 8 for D <= 64 / <= 128 / larger, (16, 1), 128. */
+typedef struct res2tac_batch_tuning {
+  int32_t max_disp, large;
+  int32_t row_dpl, shear_dpl, shear_cpl, wta_px;
+} res2tac_batch_tuning;
+
+/* Sets the batch settings of n buckets (each entry names its bucket by max_disp and large).
+ * RES2TAC_EINVAL (nothing changed) if an entry is invalid for its D. Applies from the next
+ * res2tac_compute_batch; the first change that needs more shared memory than the captured graph
+ * recaptures it there. */
+int res2tac_set_batch_tuning(res2tac_t h, const res2tac_batch_tuning* t, int32_t n);
+
+/* Reads the batch settings of the bucket named by t->max_disp and t->large into *t. */
+int res2tac_get_batch_tuning(res2tac_t h, res2tac_batch_tuning* t);
+
+/* Autotuner of the batch engine: for the buckets the n pairs fall into (largest total work
+ * first; each starts from the defaults) it times the whole batch (res2tac_compute_batch on stream s, median of 3 runs after one
+ * warm-up) for each candidate of one setting at a time - row_dpl, then (shear_dpl, shear_cpl),
+ * then wta_px - keeping the fastest, and leaves the chosen table in the context. It writes up to
+ * cap entries of the buckets it tuned into table (count into *count) and the batch times before
+ * and after into *ms_default and *ms_tuned (any of these may be NULL). The pairs' maps are
+ * written as by res2tac_compute_batch. Synchronises s; allocates the batch scratch as
+ * res2tac_compute_batch does. */
+int res2tac_autotune_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res2tac_stream_t s,
+                           res2tac_batch_tuning* table, int32_t cap, int32_t* count,
+                           float* ms_default, float* ms_tuned);
+
 /* Number of kernel launches the last res2tac_compute / res2tac_compute_batch issued. */
 int res2tac_last_launch_count(res2tac_t h);
 
@@ -259,12 +295,12 @@ int res2tac_stage_times(res2tac_t h, float* ms, int n);
  * volume, intermediate maps) is one fixed device array of
  * RES2TAC_STATIC_SCRATCH_BYTES compiled into the library; every GPU that loads the library holds
  * that array until the process exits.
- * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 9 B per pixel,
+ * Size limit: a problem whose scratch does not fit the array (3 B per W*H*D plus 25 B per pixel,
  * 5 B per W*H*D when num_paths * (255 + p2) > 65535, 4 B more per pixel with RES2TAC_EXACT_CC,
  * 24 B more per pixel and 2 KB with RES2TAC_NCC)
  * is rejected with RES2TAC_ENOMEM and a
  * message giving both sizes. 640 x 480 with D = 64 fits with 16-bit sums
- * (num_paths * (255 + p2) <= 65535: about 62 MB) but not with 32-bit ones (about 101 MB).
+ * (num_paths * (255 + p2) <= 65535: about 67 MB) but not with 32-bit ones (about 106 MB).
  * Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress)
  * with that device current; make that first call before any stream capture.
  * Sharing: every call in the process uses the same array, which keeps the contents of the last

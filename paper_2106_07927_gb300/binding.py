@@ -34,9 +34,10 @@ EXPORTS = (
     "res2tac_compute_static",
     "res2tac_compute_subpixel", "res2tac_debug_subpixel",
     "res2tac_rectify", "res2tac_set_rectification", "res2tac_compute_raw",
+    "res2tac_set_batch_tuning", "res2tac_get_batch_tuning", "res2tac_autotune_batch",
 )
 # Every symbol include/res2tac_measure.h declares (measurement aids of the benchmark).
-MEASURE_EXPORTS = ("res2tac_probe_int_peak", "res2tac_probe_red_peak")
+MEASURE_EXPORTS = ("res2tac_probe_int_peak", "res2tac_probe_red_peak", "res2tac_bounds_status")
 RES2TAC_STATIC_SCRATCH_BYTES = 80 << 20
 STAGES = ("census_cost", "aggregate", "wta_dr", "lr_median")
 
@@ -59,6 +60,14 @@ class res2tac_tuning(ctypes.Structure):
                                                "row_mode", "shear_cpl")]
 
 
+class res2tac_batch_tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("max_disp", "large", "row_dpl", "shear_dpl",
+                                               "shear_cpl", "wta_px")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 class Res2tacError(RuntimeError):
     def __init__(self, code: int, message: str):
         super().__init__(f"res2tac error {code}: {message}")
@@ -72,16 +81,18 @@ def library_path() -> str:
     return _build.LIB
 
 
-def load():
-    """Loads libres2tac.so; raises if it has not been built (no fallback exists)."""
+def load(path: str | None = None):
+    """Loads libres2tac.so (or the library at path); raises if it has not been built (no
+    fallback exists)."""
     global _lib
-    if _lib is not None:
+    if _lib is not None and path is None:
         return _lib
-    if not os.path.exists(_build.LIB):
+    path = path or _build.LIB
+    if not os.path.exists(path):
         raise RuntimeError(
             "libres2tac.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'` "
             "(needs nvcc); the SGM path has no CPU fallback")
-    lib = ctypes.CDLL(_build.LIB)
+    lib = ctypes.CDLL(path)
     P, I32, I64, S = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
     PP = ctypes.POINTER(res2tac_params)
     sig = {
@@ -112,6 +123,15 @@ def load():
         "res2tac_rectify": (ctypes.c_int, [P, I64, I32, I32, P, P, I64, P, I64, I32, I32, P]),
         "res2tac_set_rectification": (ctypes.c_int, [P, P, P, P, P, I64, I32, I32, P]),
         "res2tac_compute_raw": (ctypes.c_int, [P, P, P, I64, P, I64, P]),
+        "res2tac_set_batch_tuning": (ctypes.c_int, [P, ctypes.POINTER(res2tac_batch_tuning), I32]),
+        "res2tac_bounds_status": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                                 ctypes.POINTER(I64)]),
+        "res2tac_get_batch_tuning": (ctypes.c_int, [P, ctypes.POINTER(res2tac_batch_tuning)]),
+        "res2tac_autotune_batch": (ctypes.c_int, [P, ctypes.POINTER(res2tac_pair), I32, P,
+                                                  ctypes.POINTER(res2tac_batch_tuning), I32,
+                                                  ctypes.POINTER(I32),
+                                                  ctypes.POINTER(ctypes.c_float),
+                                                  ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -119,6 +139,21 @@ def load():
         f.argtypes = args
     _lib = lib
     return lib
+
+
+def use_check_library(on: bool = True):
+    """Switches every function of this module to the debug build with range checks
+    (libres2tac_check.so, built on first use) or, with on=False, back to libres2tac.so."""
+    global _lib
+    _lib = None
+    return load(_build.build(check=True) if on else None)
+
+
+def res2tac_bounds_status(h: int) -> tuple:
+    """(checked, site, byte offset) of the context's range-check record."""
+    c, s, o = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(load().res2tac_bounds_status(h, ctypes.byref(c), ctypes.byref(s), ctypes.byref(o)))
+    return c.value, s.value, o.value
 
 
 def _check(rc: int):
@@ -244,6 +279,29 @@ def res2tac_stage_times(h: int) -> dict:
     ms = (ctypes.c_float * len(STAGES))()
     _check(load().res2tac_stage_times(h, ms, len(STAGES)))
     return dict(zip(STAGES, [float(v) for v in ms]))
+
+
+def res2tac_set_batch_tuning(h: int, entries) -> None:
+    arr = (res2tac_batch_tuning * len(entries))(*entries)
+    _check(load().res2tac_set_batch_tuning(h, arr, len(entries)))
+
+
+def res2tac_get_batch_tuning(h: int, max_disp: int, large: int) -> res2tac_batch_tuning:
+    t = res2tac_batch_tuning(max_disp, large, 0, 0, 0, 0)
+    _check(load().res2tac_get_batch_tuning(h, ctypes.byref(t)))
+    return t
+
+
+def res2tac_autotune_batch(h: int, pairs, stream: int = 0):
+    """Returns (table entries of the tuned buckets, batch ms with the defaults, ms tuned)."""
+    arr = (res2tac_pair * len(pairs))(*pairs)
+    cap = 34
+    table = (res2tac_batch_tuning * cap)()
+    count = ctypes.c_int32()
+    m0, m1 = ctypes.c_float(), ctypes.c_float()
+    _check(load().res2tac_autotune_batch(h, arr, len(pairs), stream, table, cap,
+                                         ctypes.byref(count), ctypes.byref(m0), ctypes.byref(m1)))
+    return [table[i] for i in range(count.value)], m0.value, m1.value
 
 
 def res2tac_probe_red_peak(nbytes: int, passes: int = 16, stream: int = 0) -> float:

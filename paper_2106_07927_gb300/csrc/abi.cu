@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/res2tac.h"
@@ -140,6 +141,7 @@ int res2tac_create(const res2tac_params* p, res2tac_t* out) {
                       (p->flags & RES2TAC_EXACT_CC) != 0, (p->flags & RES2TAC_NCC) != 0);
   const size_t npx = (size_t)p->width * p->height;
   e = cudaMalloc(&h->scratch, h->lay.total);
+  if (e == cudaSuccess) e = cudaMemset(h->scratch + h->lay.fault, 0, 16);  // range-check record
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_in, align_up(npx * 2, 256));
   if (e == cudaSuccess) e = cudaMalloc(&h->stage_out, align_up(npx * 2, 256));
   if (e == cudaSuccess) e = r2t::fork_create(&h->fork);
@@ -565,6 +567,175 @@ int res2tac_compute_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res
   h->last_launches = launches;
   if (rc == -4) return fail(RES2TAC_ETIMEOUT, "batch work queue wait timed out");
   if (rc) return fail(RES2TAC_ECUDA, "batch run failed: %s", r2t::batch_error(h->batch));
+  return RES2TAC_OK;
+}
+
+static int bucket_of(const res2tac_batch_tuning* t) {
+  if (!t || t->max_disp < 16 || t->max_disp > 256 || t->max_disp % 16 || (t->large & ~1)) return -1;
+  return 2 * (t->max_disp / 16) + t->large;
+}
+
+static int ensure_engine(res2tac_t h) {
+  if (h->batch) return RES2TAC_OK;
+  int rc = r2t::batch_reserve(&h->batch, 0, 1);
+  if (rc == -2) return fail(RES2TAC_ENOMEM, "batch engine setup: out of memory");
+  if (rc) return fail(RES2TAC_ECUDA, "batch engine setup failed: %s", r2t::batch_error(h->batch));
+  return RES2TAC_OK;
+}
+
+int res2tac_set_batch_tuning(res2tac_t h, const res2tac_batch_tuning* t, int32_t n) {
+  if (!h || !t || n < 0) return fail(RES2TAC_EINVAL, "NULL argument");
+  for (int i = 0; i < n; i++) {
+    const int b = bucket_of(&t[i]);
+    r2t::BatchTune v;
+    memset(&v, 0, sizeof(v));
+    v.row_dpl = (signed char)t[i].row_dpl;
+    v.shear_dpl = (signed char)t[i].shear_dpl;
+    v.shear_cpl = (signed char)t[i].shear_cpl;
+    v.wta_px = (short)t[i].wta_px;
+    if (b < 0 || t[i].row_dpl != v.row_dpl || t[i].shear_dpl != v.shear_dpl ||
+        t[i].shear_cpl != v.shear_cpl || t[i].wta_px != v.wta_px || !r2t::batch_tune_valid(b, v))
+      return fail(RES2TAC_EINVAL,
+                  "batch tuning %d (D %d, large %d: row dpl %d, shear %d x %d, wta %d) invalid", i,
+                  t[i].max_disp, t[i].large, t[i].row_dpl, t[i].shear_dpl, t[i].shear_cpl,
+                  t[i].wta_px);
+  }
+  int rc = ensure_engine(h);
+  if (rc) return rc;
+  for (int i = 0; i < n; i++) {
+    r2t::BatchTune v;
+    memset(&v, 0, sizeof(v));
+    v.row_dpl = (signed char)t[i].row_dpl;
+    v.shear_dpl = (signed char)t[i].shear_dpl;
+    v.shear_cpl = (signed char)t[i].shear_cpl;
+    v.wta_px = (short)t[i].wta_px;
+    r2t::batch_set_tune(h->batch, bucket_of(&t[i]), v);
+  }
+  return RES2TAC_OK;
+}
+
+int res2tac_get_batch_tuning(res2tac_t h, res2tac_batch_tuning* t) {
+  if (!h || !t) return fail(RES2TAC_EINVAL, "NULL argument");
+  const int b = bucket_of(t);
+  if (b < 0) return fail(RES2TAC_EINVAL, "bucket D %d large %d invalid", t->max_disp, t->large);
+  const r2t::BatchTune v = r2t::batch_get_tune(h->batch, b);
+  t->row_dpl = v.row_dpl;
+  t->shear_dpl = v.shear_dpl;
+  t->shear_cpl = v.shear_cpl;
+  t->wta_px = v.wta_px;
+  return RES2TAC_OK;
+}
+
+// Median time of 3 batch runs after one warm-up (ms), or a negative RES2TAC code.
+static float time_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, cudaStream_t st,
+                        cudaEvent_t e0, cudaEvent_t e1, int* rc) {
+  *rc = res2tac_compute_batch(h, pairs, n, st);
+  if (*rc) return -1.0f;
+  float ms[3];
+  for (int r = 0; r < 3; r++) {
+    cudaEventRecord(e0, st);
+    *rc = res2tac_compute_batch(h, pairs, n, st);
+    if (*rc) return -1.0f;
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      *rc = fail(RES2TAC_ECUDA, "autotune synchronisation failed");
+      return -1.0f;
+    }
+    cudaEventElapsedTime(&ms[r], e0, e1);
+  }
+  std::sort(ms, ms + 3);
+  return ms[1];
+}
+
+int res2tac_autotune_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res2tac_stream_t s,
+                           res2tac_batch_tuning* table, int32_t cap, int32_t* count,
+                           float* ms_default, float* ms_tuned) {
+  if (!h || !pairs || n < 1) return fail(RES2TAC_EINVAL, "empty batch");
+  cudaStream_t st = (cudaStream_t)s;
+  // buckets present, by their total work
+  std::vector<std::pair<double, int>> work;
+  for (int i = 0; i < n; i++) {
+    if (!shape_ok(pairs[i].width, pairs[i].height, pairs[i].max_disp))
+      return fail(RES2TAC_EINVAL, "pair %d: invalid shape", i);
+    const int b = r2t::tune_bucket(pairs[i].width, pairs[i].height, pairs[i].max_disp);
+    const double de = (double)pairs[i].width * pairs[i].height * pairs[i].max_disp;
+    bool found = false;
+    for (auto& w : work)
+      if (w.second == b) {
+        w.first += de;
+        found = true;
+      }
+    if (!found) work.push_back({de, b});
+  }
+  std::sort(work.begin(), work.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  int rc = ensure_engine(h);
+  if (rc) return rc;
+  for (const auto& w : work) r2t::batch_set_tune(h->batch, w.second, r2t::batch_default_tune(w.second));
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(RES2TAC_ECUDA, "cudaEventCreate failed");
+  float best = time_batch(h, pairs, n, st, e0, e1, &rc);
+  const float first = best;
+  const int rows[3] = {2, 4, 8}, sdpl[2] = {16, 16}, scpl[2] = {1, 2};
+  const int wpx[3] = {64, 128, 256};
+  for (size_t wi = 0; wi < work.size() && !rc; wi++) {
+    const int b = work[wi].second;
+    for (int param = 0; param < 3 && !rc; param++) {
+      const int ncand = param == 1 ? 2 : 3;
+      r2t::BatchTune keep = r2t::batch_get_tune(h->batch, b);
+      for (int c = 0; c < ncand && !rc; c++) {
+        r2t::BatchTune t = keep;
+        if (param == 0) t.row_dpl = (signed char)rows[c];
+        if (param == 1) {
+          t.shear_dpl = (signed char)sdpl[c];
+          t.shear_cpl = (signed char)scpl[c];
+        }
+        if (param == 2) t.wta_px = (short)wpx[c];
+        if (memcmp(&t, &keep, sizeof(t)) == 0 || !r2t::batch_tune_valid(b, t)) continue;
+        const r2t::BatchTune prev = r2t::batch_get_tune(h->batch, b);
+        r2t::batch_set_tune(h->batch, b, t);
+        const float ms = time_batch(h, pairs, n, st, e0, e1, &rc);
+        if (!rc && ms < best) {
+          best = ms;
+        } else {
+          r2t::batch_set_tune(h->batch, b, prev);
+        }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  int k = 0;
+  for (size_t wi = 0; wi < work.size() && table && k < cap; wi++, k++) {
+    const int b = work[wi].second;
+    const r2t::BatchTune v = r2t::batch_get_tune(h->batch, b);
+    table[k].max_disp = 16 * (b / 2);
+    table[k].large = b & 1;
+    table[k].row_dpl = v.row_dpl;
+    table[k].shear_dpl = v.shear_dpl;
+    table[k].shear_cpl = v.shear_cpl;
+    table[k].wta_px = v.wta_px;
+  }
+  if (count) *count = k;
+  if (ms_default) *ms_default = first;
+  if (ms_tuned) *ms_tuned = best;
+  return RES2TAC_OK;
+}
+
+int res2tac_bounds_status(res2tac_t h, int32_t* checked, int32_t* site, int64_t* offset) {
+  if (!h) return fail(RES2TAC_EINVAL, "handle is NULL");
+#ifdef RES2TAC_CHECK_BOUNDS
+  const int on = 1;
+#else
+  const int on = 0;
+#endif
+  long long rec[2] = {0, 0};
+  cudaError_t e = cudaMemcpy(rec, h->scratch + h->lay.fault, 16, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_bounds_status");
+  if (checked) *checked = on;
+  if (site) *site = (int32_t)(rec[0] & 0xFFFFFFFFll);
+  if (offset) *offset = rec[1];
   return RES2TAC_OK;
 }
 

@@ -136,26 +136,31 @@ __device__ __forceinline__ void rows_dispatch(const Problem& pb, const Method& m
   }
 }
 
-template <int DPL, int WD, bool WIDE>
+template <int DPL, int WD, int CPL, bool WIDE>
 __device__ __forceinline__ void shear_full(const Problem& pb, const Method& mt, int item,
                                            uint8_t* base) {
   if (pb.D == DPL * WD)
-    agg_shear<DPL, WD, 1, WIDE, true>(pb, mt, item, base, base + shear_ring_bytes(DPL, 1));
+    agg_shear<DPL, WD, CPL, WIDE, true>(pb, mt, item, base, base + shear_ring_bytes(DPL, CPL));
   else
-    agg_shear<DPL, WD, 1, WIDE, false>(pb, mt, item, base, base + shear_ring_bytes(DPL, 1));
+    agg_shear<DPL, WD, CPL, WIDE, false>(pb, mt, item, base, base + shear_ring_bytes(DPL, CPL));
 }
 
-// Batch pairs use the default 16 disparities per lane. base: this warp's
-// shear_default_smem_bytes(WIDE) bytes of shared memory.
+// The sheared-column setting (dpl, cpl) of a batch bucket (batch_shear_ok). base: this warp's
+// shear_smem_bytes of that setting.
 template <bool WIDE>
 __device__ __forceinline__ void shear_dispatch(const Problem& pb, const Method& mt, int item,
-                                               uint8_t* base) {
-  switch (shear_width(pb.D, 16)) {
-    case 1: shear_full<16, 1, WIDE>(pb, mt, item, base); break;
-    case 2: shear_full<16, 2, WIDE>(pb, mt, item, base); break;
-    case 4: shear_full<16, 4, WIDE>(pb, mt, item, base); break;
-    case 8: shear_full<16, 8, WIDE>(pb, mt, item, base); break;
-    case 16: shear_full<16, 16, WIDE>(pb, mt, item, base); break;
+                                               uint8_t* base, int dpl, int cpl) {
+  switch (dpl * 1000 + cpl * 100 + shear_width(pb.D, dpl)) {
+    case 16101: shear_full<16, 1, 1, WIDE>(pb, mt, item, base); break;
+    case 16102: shear_full<16, 2, 1, WIDE>(pb, mt, item, base); break;
+    case 16104: shear_full<16, 4, 1, WIDE>(pb, mt, item, base); break;
+    case 16108: shear_full<16, 8, 1, WIDE>(pb, mt, item, base); break;
+    case 16116: shear_full<16, 16, 1, WIDE>(pb, mt, item, base); break;
+    case 16201: shear_full<16, 1, 2, WIDE>(pb, mt, item, base); break;
+    case 16202: shear_full<16, 2, 2, WIDE>(pb, mt, item, base); break;
+    case 16204: shear_full<16, 4, 2, WIDE>(pb, mt, item, base); break;
+    case 16208: shear_full<16, 8, 2, WIDE>(pb, mt, item, base); break;
+    case 16216: shear_full<16, 16, 2, WIDE>(pb, mt, item, base); break;
     default: break;
   }
 }
@@ -163,7 +168,8 @@ __device__ __forceinline__ void shear_dispatch(const Problem& pb, const Method& 
 template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_row_kernel(const BatchHeader* hd, const Problem* probs,
                                                         const AggSeg* segs, const int* seg_prefix,
-                                                        int nseg, Method mt, unsigned* counters) {
+                                                        int nseg, Method mt, unsigned* counters,
+                                                        int warp_smem) {
   const int total = hd->total[kStRows];
   for (;;) {
     const int item = claim_warp(&counters[kStRows]);
@@ -172,17 +178,20 @@ __global__ void __launch_bounds__(256) batch_row_kernel(const BatchHeader* hd, c
     const AggSeg sg = segs[si];
     const Problem pb = probs[sg.pair];
     rows_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, sg.end,
-                        hd->dpl_by_d16[pb.D / 16]);
+                        hd->tune[tune_bucket(pb.W, pb.H, pb.D)].row_dpl);
   }
 }
 
+// warp_smem: shared memory of one warp, at least shear_smem_bytes(dpl, WIDE, cpl) of every
+// bucket setting the batch uses.
 template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_shear_kernel(const BatchHeader* hd,
                                                           const Problem* probs, const AggSeg* segs,
                                                           const int* seg_prefix, int nseg,
-                                                          Method mt, unsigned* counters) {
+                                                          Method mt, unsigned* counters,
+                                                          int warp_smem) {
   extern __shared__ __align__(16) uint8_t shm[];
-  uint8_t* base = shm + (threadIdx.x >> 5) * shear_default_smem_bytes(WIDE);
+  uint8_t* base = shm + (threadIdx.x >> 5) * warp_smem;
   const int total = hd->total[kStShear];
   for (;;) {
     const int item = claim_warp(&counters[kStShear]);
@@ -190,7 +199,9 @@ __global__ void __launch_bounds__(256) batch_shear_kernel(const BatchHeader* hd,
     const int si = find_slot(seg_prefix, nseg, item);
     const AggSeg sg = segs[si];
     const Problem pb = probs[sg.pair];
-    shear_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, base);
+    const BatchTune tn = hd->tune[tune_bucket(pb.W, pb.H, pb.D)];
+    shear_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, base,
+                         tn.shear_dpl, tn.shear_cpl);
   }
 }
 

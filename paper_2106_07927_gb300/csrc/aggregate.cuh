@@ -271,6 +271,8 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
   const int d0 = active ? lig * DPL : 0;
   const int64_t pl = (int64_t)y * W, pr = pl + W - 1;  // first and last pixel of the row
   const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
+  const int64_t nde = (int64_t)W * H * D;  // extent of the volumes (range checks)
+  (void)nde;
   if constexpr (SPLIT) {
     const bool back = (ui & 1) != 0;
     const int64_t estride = back ? -(int64_t)D : (int64_t)D;
@@ -283,7 +285,7 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
     Raw r[U];
 #pragma unroll
     for (int u = 0; u < U; u++) {
-      r[u] = (active && u < W) ? RC::load(cp) : Raw();
+      r[u] = (active && u < W && R2T_CHECKED(pb, cp, DPL, pb.cost, nde, 1)) ? RC::load(cp) : Raw();
       if (u + 1 < W) cp += estride;
     }
     int t0 = 0;
@@ -297,9 +299,11 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
         uint32_t c[NP];
         RC::unpack(r[u], c);
         long_step<DPL, LPL, FULL>(L, mm, c, active, lig, P1P1, P2P2);
-        r[u] = active ? RC::load(cp) : Raw();  // step t0 + u + U
+        r[u] = (active && R2T_CHECKED(pb, cp, DPL, pb.cost, nde, 1)) ? RC::load(cp)
+                                                                      : Raw();  // step t0 + u + U
         cp += estride;
-        if (active) add_lane<DPL, WIDE>(sp, 0, L);
+        if (active && R2T_CHECKED(pb, sp, DPL * BPE, pb.agg, nde * BPE, 2))
+          add_lane<DPL, WIDE>(sp, 0, L);
         sp += estride * BPE;
       }
       e += U * estride;
@@ -312,9 +316,13 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
         uint32_t c[NP];
         RC::unpack(r[u], c);
         long_step<DPL, LPL, FULL>(L, mm, c, active, lig, P1P1, P2P2);
-        r[u] = (active && t + U < W) ? RC::load(cp) : Raw();  // step t + U
+        r[u] = (active && t + U < W && R2T_CHECKED(pb, cp, DPL, pb.cost, nde, 1))
+                   ? RC::load(cp)
+                   : Raw();  // step t + U
         if (t + U + 1 < W) cp += estride;
-        if (active) add_lane<DPL, WIDE>(pb.agg, e, L);
+        if (active && R2T_CHECKED(pb, reinterpret_cast<uint8_t*>(pb.agg) + e * BPE, DPL * BPE,
+                                  pb.agg, nde * BPE, 2))
+          add_lane<DPL, WIDE>(pb.agg, e, L);
         e += estride;
       }
     }
@@ -331,8 +339,8 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
 #pragma unroll
     for (int u = 0; u < U; u++) {
       const bool ok = active && u < W;
-      rf[u] = ok ? RC::load(cf) : Raw();
-      rb[u] = ok ? RC::load(cb) : Raw();
+      rf[u] = (ok && R2T_CHECKED(pb, cf, DPL, pb.cost, nde, 1)) ? RC::load(cf) : Raw();
+      rb[u] = (ok && R2T_CHECKED(pb, cb, DPL, pb.cost, nde, 1)) ? RC::load(cb) : Raw();
       if (u + 1 < W) {
         cf += estride;
         cb -= estride;
@@ -349,16 +357,18 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
         long_step2<DPL, LPL, FULL>(Lf, mf, c1, Lb, mb, c2, active, lig, P1P1, P2P2);
         // refill this slot with step t + U (the pointers sit there already)
         const bool ok = active && t + U < W;
-        rf[u] = ok ? RC::load(cf) : Raw();
-        rb[u] = ok ? RC::load(cb) : Raw();
+        rf[u] = (ok && R2T_CHECKED(pb, cf, DPL, pb.cost, nde, 1)) ? RC::load(cf) : Raw();
+        rb[u] = (ok && R2T_CHECKED(pb, cb, DPL, pb.cost, nde, 1)) ? RC::load(cb) : Raw();
         if (t + U + 1 < W) {
           cf += estride;
           cb -= estride;
         }
-        if (active) {
+        if (active && R2T_CHECKED(pb, reinterpret_cast<uint8_t*>(pb.agg) + ef * (WIDE ? 4 : 2),
+                                  DPL * (WIDE ? 4 : 2), pb.agg, nde * (WIDE ? 4 : 2), 2))
           add_lane<DPL, WIDE>(pb.agg, ef, Lf);
+        if (active && R2T_CHECKED(pb, reinterpret_cast<uint8_t*>(pb.agg) + eb * (WIDE ? 4 : 2),
+                                  DPL * (WIDE ? 4 : 2), pb.agg, nde * (WIDE ? 4 : 2), 2))
           add_lane<DPL, WIDE>(pb.agg, eb, Lb);
-        }
         ef += estride;
         eb -= estride;
       }
@@ -375,6 +385,7 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
 // new line of the path enters there and the chain restarts with L = C. Every pixel lies on exactly
 // one chain of each kind, j = (x - s y) mod W, so the W chains of a kind cover its path once.
 constexpr int kShearRing = 8;  // steps in the cost ring; 2 steps per cp.async group, 6 in flight
+
 __host__ __device__ inline int shear_kinds(int num_paths) { return num_paths == 8 ? 6 : 2; }
 __host__ __device__ inline int shear_dpl_default(int D) { return 16; }
 // Two chains per lane at D = 128: the step's bookkeeping serves both and the halved warp count
@@ -396,10 +407,6 @@ __host__ __device__ inline int shear_stage_bytes(int dpl, bool wide, int cpl) {
 // Ring plus two staging buffers (steps alternate between them).
 __host__ __device__ inline int shear_smem_bytes(int dpl, bool wide, int cpl) {
   return shear_ring_bytes(dpl, cpl) + 2 * shear_stage_bytes(dpl, wide, cpl);
-}
-// Per warp for the default configuration of every D.
-__host__ __device__ inline int shear_default_smem_bytes(bool wide) {
-  return shear_smem_bytes(16, wide, 1);
 }
 
 // Position, in 16-byte pieces, of piece i of pixel slot c in a buffer of pixel vectors of pp
@@ -483,6 +490,8 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   // bytes from one step's run to the next (before any wrap correction)
   const int64_t cstride = ((int64_t)dy * W + dx) * D, astride = cstride * BPE;
   const int64_t cwrap = (int64_t)W * D, awrap = cwrap * BPE;  // one row, subtracted at a wrap
+  const int64_t nde = (int64_t)W * H * D;  // extent of the volumes (range checks)
+  (void)nde;
 
   // Per-lane pieces, fixed for the whole walk: cost piece v of the step's run (chain cp_c[v],
   // shared offset cp_s[v] inside a ring slot); the lane's own cost pieces (rd_s) and sum pieces
@@ -524,7 +533,7 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
         const uint8_t* src = crun + 16 * lane;
 #pragma unroll
         for (int v = 0; v < NCP; v++)
-          if (cp_c[v] >= 0)
+          if (cp_c[v] >= 0 && R2T_CHECKED(pb, src + 512 * v, 16, pb.cost, nde, 3))
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(cslot + cp_s[v]),
                          "l"(src + 512 * v));
       } else {
@@ -534,8 +543,10 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
             const int p = lane + 32 * v;
             const int pc = cp_c[v], pi = p - pc * PP;
             const int back_w = xc + pc >= W ? W : 0;  // wrapped to the row's start
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(cslot + cp_s[v]),
-                         "l"(crun + ((int64_t)pc - back_w) * D + pi * 16));
+            const uint8_t* a = crun + ((int64_t)pc - back_w) * D + pi * 16;
+            if (R2T_CHECKED(pb, a, 16, pb.cost, nde, 3))
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(cslot + cp_s[v]),
+                           "l"(a));
           }
         }
       }
@@ -559,12 +570,12 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
     const uint8_t* src = crun + 16 * lane;
 #pragma unroll
     for (int v = 0; v < NCP; v++)
-      if (cp_c[v] >= 0)
+      if (cp_c[v] >= 0 && R2T_CHECKED(pb, src + 512 * v, 16, pb.cost, nde, 3))
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + cp_s[v]),
                      "l"(src + 512 * v));
 #pragma unroll
     for (int v = 0; v < NCP; v++)
-      if (cp_c[v] >= 0)
+      if (cp_c[v] >= 0 && R2T_CHECKED(pb, src + cstride + 512 * v, 16, pb.cost, nde, 3))
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s1 + cp_s[v]),
                      "l"(src + cstride + 512 * v));
     crun += 2 * cstride;
@@ -676,9 +687,12 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   auto add_run = [&](int par, int n1) {
     if (lane == 0) {
       const uint32_t sbuf = stage_s + (uint32_t)(par * stage_bytes);
-      asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;"
-                   ::"l"(arun), "r"(sbuf), "r"(n1 * D * BPE) : "memory");
-      if (!SH0 && n1 < n)
+      if (R2T_CHECKED(pb, arun, (int64_t)n1 * D * BPE, pb.agg, nde * BPE, 4))
+        asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;"
+                     ::"l"(arun), "r"(sbuf), "r"(n1 * D * BPE) : "memory");
+      if (!SH0 && n1 < n &&
+          R2T_CHECKED(pb, arun - (int64_t)xs * D * BPE, (int64_t)(n - n1) * D * BPE, pb.agg,
+                      nde * BPE, 5))
         asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;"
                      ::"l"(arun - (int64_t)xs * D * BPE), "r"(sbuf + n1 * D * BPE),
                      "r"((n - n1) * D * BPE)
@@ -792,14 +806,26 @@ __device__ __forceinline__ void agg_shear_t(const Problem& pb, const Method& mt,
   __syncwarp();
 }
 
-// Warp item `item` of a pair's sheared-column work (see shear_items).
+// Warp item `item` of a pair's sheared-column work (see shear_items). Items run kind by kind in
+// the order TB, TLBR, TRBL, BT, BRTL, BLTR: the three downward kinds first, then the three upward
+// ones. Warps that start together walk the same rows at about the same time, so when the downward
+// kinds' warps are resident together they add into the same band of S while it is in L2 (one
+// DRAM round trip of that band instead of one per kind); the upward kinds share the band moving
+// up. Kind-major order with both directions of a kind together kept them apart on images whose
+// warps do not all fit on the GPU at once (1920 x 1080, D = 256: 27.6 B of DRAM traffic per
+// disparity estimate for the six kinds).
+__device__ __forceinline__ int shear_kind_of(int k, int num_kinds) {
+  return num_kinds == 6 ? (k < 3 ? 2 * k : 2 * (k - 3) + 1) : k;
+}
+
 template <int DPL, int WD, int CPL, bool WIDE, bool FULL>
 __device__ __forceinline__ void agg_shear(const Problem& pb, const Method& mt, int item,
                                           uint8_t* ring, uint8_t* stage) {
   constexpr int CH = CPL * (32 / WD);
   const int G = (pb.W + CH - 1) / CH;
-  const int kind = item / G;
-  const int j0 = (item - kind * G) * CH;
+  const int k = item / G;
+  const int kind = shear_kind_of(k, shear_kinds(mt.num_paths));
+  const int j0 = (item - k * G) * CH;
   if (kind < 2)
     agg_shear_t<DPL, WD, CPL, WIDE, FULL, true>(pb, mt, kind, j0, ring, stage);
   else

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "batch_dev.cuh"
 #include "common.cuh"
 
 namespace r2t {
@@ -24,8 +25,12 @@ char* batch_scratch(BatchEngine* e);
 int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cudaStream_t s,
               int* launches);
 
-// Sets the disparities-per-lane of the aggregation for pairs with D disparities (0 = default).
-void batch_set_dpl(BatchEngine* e, int D, int dpl);
+// Kernel settings per bucket of pairs (tune_bucket: D / 16 and the size class): the defaults,
+// their validity, and the engine's table (set returns -1 for an invalid setting).
+BatchTune batch_default_tune(int bucket);
+bool batch_tune_valid(int bucket, const BatchTune& t);
+int batch_set_tune(BatchEngine* e, int bucket, const BatchTune& t);
+BatchTune batch_get_tune(BatchEngine* e, int bucket);
 
 const char* batch_error(BatchEngine* e);
 void batch_destroy(BatchEngine* e);

@@ -6,18 +6,38 @@
 namespace r2t {
 
 enum {
-  kStCost = 0, kStRows = 1, kStShear = 2, kStWta = 3, kStMedian = 4,
-  kNumCounters = 5
+  kStCost = 0, kStRows = 1, kStShear = 2, kStWta = 3, kStMedian = 4, kStCensus = 5,
+  kNumCounters = 6
 };
 
-// Header of the device descriptor block. It is followed by Problem[cap], int prefix[3][cap + 1]
-// (census + cost, wta, median items), then for the row and the sheared-column queue each
+// Kernel settings of the batch for one bucket of pairs (see tune_bucket): disparities per lane of
+// the row kernel (2, 4 or 8), disparities and chains per lane of the sheared kernel (16 with 1
+// or 2 chains), pixels per WTA tile (64, 128 or 256, capped so the tile's sums take at most
+// 64 KB). The persistent sheared kernel holds every setting it may meet inlined, so its settings
+// are kept to the two that cost the most compile time to leave out.
+struct BatchTune {
+  signed char row_dpl, shear_dpl, shear_cpl, pad;
+  short wta_px, pad2;
+};
+constexpr int kTuneBuckets = 34;
+// Sheared-column settings a batch bucket may take: 16 disparities per lane, 1 or 2 chains.
+__host__ __device__ inline bool batch_shear_ok(int dpl, int cpl) {
+  return dpl == 16 && (cpl == 1 || cpl == 2);
+}
+// Bucket of a pair: its disparity count (D / 16) and its size class (W * H below or at least
+// 2^18 pixels, about 512 x 512).
+__host__ __device__ inline int tune_bucket(int W, int H, int D) {
+  return 2 * (D / 16) + ((long long)W * H >= (1 << 18) ? 1 : 0);
+}
+
+// Header of the device descriptor block. It is followed by Problem[cap], int prefix[4][cap + 1]
+// (cost, wta, median and census items), then for the row and the sheared-column queue each
 // AggSeg[cap] and int seg_prefix[cap + 1].
 struct BatchHeader {
   int n;
   int total[kNumCounters];
   int pad;
-  signed char dpl_by_d16[17];  // row-kernel disparities per lane, indexed by D / 16
+  BatchTune tune[kTuneBuckets];
 };
 
 struct AggSeg {

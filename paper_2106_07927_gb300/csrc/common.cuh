@@ -28,6 +28,7 @@ struct Problem {
   int64_t out_pitch;  // bytes
   int W, H, D;
   uint8_t* cost;      // [H][W][D]
+  uint64_t* ct;       // [2][H][W] census descriptors of the left, then the right image
   void* agg;          // [H][W][D], uint16 (or uint32 when wide)
   uint16_t* dl;       // [H][W] winner-takes-all map
   uint16_t* dr;       // [H][W] approximate right map
@@ -38,7 +39,30 @@ struct Problem {
   uint16_t* dp;       // [H][W] D^L of that swapped, flipped pair (exact check); NULL: approximate
   uint2* nst;         // [2][H][W] patch sum and factor of the reference / matching image (NCC)
   int32_t* nsv;       // [2][H][W] exact patch variance N sum a^2 - (sum a)^2 of both images (NCC)
+  unsigned* fault;    // range-check record {site, 0, byte offset (int64)} (RES2TAC_CHECK_BOUNDS)
 };
+
+// Debug build with range checks (compiled with -DRES2TAC_CHECK_BOUNDS): the checked global
+// accesses of the aggregation and WTA kernels first test that [p, p + bytes) lies inside their
+// buffer [lo, lo + size); a failing test records its site and byte offset in pb.fault (the first
+// failure wins) and the access is skipped. Nothing traps. In the normal build every test is the
+// constant true and compiles away.
+// Sites: 1 row-kernel cost load, 2 row-kernel add into S, 3 sheared-kernel cost copy, 4 / 5
+// sheared-kernel bulk add (run before / after a wrap), 6 WTA staging copy of S, 7 WTA store of D^L.
+#ifdef RES2TAC_CHECK_BOUNDS
+static __device__ __noinline__ bool check_range(unsigned* fault, const void* p, int64_t bytes,
+                                                const void* lo, int64_t size, int site) {
+  const int64_t off = static_cast<const char*>(p) - static_cast<const char*>(lo);
+  const bool ok = off >= 0 && bytes >= 0 && off + bytes <= size;
+  if (!ok && fault && atomicCAS(fault, 0u, (unsigned)site) == 0u)
+    reinterpret_cast<long long*>(fault)[1] = off;
+  return ok;
+}
+#define R2T_CHECKED(pb, p, bytes, lo, size, site) \
+  r2t::check_range((pb).fault, (p), (bytes), (lo), (size), (site))
+#else
+#define R2T_CHECKED(pb, p, bytes, lo, size, site) true
+#endif
 
 // Method parameters shared by every pair of a call.
 struct Method {

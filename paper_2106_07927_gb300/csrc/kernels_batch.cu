@@ -28,6 +28,22 @@
 namespace r2t {
 
 
+__global__ void __launch_bounds__(256) batch_census_kernel(const BatchHeader* hd,
+                                                           const Problem* probs,
+                                                           const int* prefix, Method mt,
+                                                           unsigned* counters) {
+  __shared__ CensusSmem sm;
+  __shared__ int s_item;
+  const int total = hd->total[kStCensus], n = hd->n;
+  for (;;) {
+    const int item = claim_block(&counters[kStCensus], &s_item);
+    if (item >= total) break;
+    const int p = find_slot(prefix, n, item);
+    const Problem pb = probs[p];
+    census_tile_dispatch(pb, mt, item - prefix[p], sm);
+  }
+}
+
 __global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
                                                          const Problem* probs, const int* prefix,
                                                          Method mt, unsigned* counters) {
@@ -44,8 +60,6 @@ __global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
 }
 
 
-constexpr int kBatchWtaPx = 128;  // pixels per WTA item (staged tiles, at most 64 KB of sums)
-
 template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, const Problem* probs,
                                                         const int* prefix, unsigned* counters) {
@@ -58,7 +72,8 @@ __global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, c
     if (item >= total) break;
     const int p = find_slot(prefix, n, item);
     const Problem pb = probs[p];
-    wta_dr_staged<WIDE>(pb, item - prefix[p], wsm, wta_staged_px(pb.D, WIDE, kBatchWtaPx));
+    const int T = wta_staged_px(pb.D, WIDE, hd->tune[tune_bucket(pb.W, pb.H, pb.D)].wta_px);
+    wta_dr_staged<WIDE>(pb, item - prefix[p], wsm, T);
   }
 }
 
@@ -92,15 +107,16 @@ struct BatchEngine {
   bool copy_pending = false;
   Method graph_method;
   int graph_wta_smem = 0;
+  int graph_shear_smem = 0;  // per warp
   int graph_launches = 0;
-  signed char dpl_by_d16[17];
+  BatchTune tune[kTuneBuckets];
   char err[256];
 };
 
 static size_t probs_offset() { return (sizeof(BatchHeader) + 255) / 256 * 256; }
 static size_t prefix_offset(int cap) { return probs_offset() + (size_t)cap * sizeof(Problem); }
 static size_t segs_offset(int cap, int q) {  // q = 0 rows, 1 sheared columns
-  const size_t base = (prefix_offset(cap) + 3 * sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
+  const size_t base = (prefix_offset(cap) + 4 * sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
   const size_t per = ((size_t)cap * sizeof(AggSeg) + sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
   return base + q * per;
 }
@@ -143,7 +159,7 @@ static int grow_desc(BatchEngine* e, int n) {
 int batch_reserve(BatchEngine** pe, size_t scratch_bytes, int n) {
   if (!*pe) {
     BatchEngine* e = new BatchEngine();
-    for (int i = 0; i < 17; i++) e->dpl_by_d16[i] = (signed char)long_dpl_default(i * 16);
+    for (int b = 0; b < kTuneBuckets; b++) e->tune[b] = batch_default_tune(b);
     e->err[0] = 0;
     memset(&e->graph_method, 0, sizeof(Method));
     *pe = e;
@@ -172,9 +188,34 @@ int batch_reserve(BatchEngine** pe, size_t scratch_bytes, int n) {
 char* batch_scratch(BatchEngine* e) { return e ? e->scratch : nullptr; }
 const char* batch_error(BatchEngine* e) { return e ? e->err : "no batch engine"; }
 
-void batch_set_dpl(BatchEngine* e, int D, int dpl) {
-  if (e && D >= 0 && D <= 256)
-    e->dpl_by_d16[D / 16] = (signed char)(dpl ? dpl : long_dpl_default(D));
+BatchTune batch_default_tune(int bucket) {
+  const int D = 16 * (bucket / 2);
+  BatchTune t;
+  memset(&t, 0, sizeof(t));
+  t.row_dpl = (signed char)long_dpl_default(D);
+  t.shear_dpl = 16;
+  t.shear_cpl = 1;
+  t.wta_px = 128;
+  return t;
+}
+
+bool batch_tune_valid(int bucket, const BatchTune& t) {
+  const int D = 16 * (bucket / 2);
+  if (bucket < 2 || bucket >= kTuneBuckets) return false;
+  if (t.row_dpl != 2 && t.row_dpl != 4 && t.row_dpl != 8) return false;
+  if (D % t.row_dpl != 0 || D / t.row_dpl > 32) return false;
+  if (!batch_shear_ok(t.shear_dpl, t.shear_cpl) || D % t.shear_dpl != 0) return false;
+  return t.wta_px == 64 || t.wta_px == 128 || t.wta_px == 256;
+}
+
+int batch_set_tune(BatchEngine* e, int bucket, const BatchTune& t) {
+  if (!e || !batch_tune_valid(bucket, t)) return -1;
+  e->tune[bucket] = t;
+  return 0;
+}
+
+BatchTune batch_get_tune(BatchEngine* e, int bucket) {
+  return (e && bucket >= 0 && bucket < kTuneBuckets) ? e->tune[bucket] : batch_default_tune(bucket);
 }
 
 void batch_destroy(BatchEngine* e) {
@@ -201,7 +242,7 @@ static int persistent_grid(K kernel, size_t smem) {
 }
 
 template <bool WIDE>
-static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
+static int capture_t(BatchEngine* e, const Method& mt, int wta_smem, int warp_smem) {
   const int cap = e->cap_pairs;
   const BatchHeader* hd = reinterpret_cast<const BatchHeader*>(e->d_desc);
   const Problem* probs = reinterpret_cast<const Problem*>(e->d_desc + probs_offset());
@@ -214,11 +255,12 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   // launch shapes and attributes are settled before the capture starts
   cudaFuncSetAttribute(batch_wta_kernel<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        wta_smem);
+  const int g_census = persistent_grid(batch_census_kernel, 0);
   const int g_cost = persistent_grid(batch_cost_kernel, 0);
   const void* k_rows = batch_row_kernel_fn<WIDE>();
   const void* k_shear = batch_shear_kernel_fn<WIDE>();
   const int g_rows = persistent_grid(k_rows, 0);
-  const int shear_smem = 8 * shear_default_smem_bytes(WIDE);  // 8 warps per block
+  const int shear_smem = 8 * warp_smem;  // 8 warps per block
   cudaFuncSetAttribute(k_shear, cudaFuncAttributeMaxDynamicSharedMemorySize, shear_smem);
   const int g_shear = persistent_grid(k_shear, shear_smem);
   const int g_wta = persistent_grid(batch_wta_kernel<WIDE>, wta_smem);
@@ -233,6 +275,7 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   // an external record node, so the host can wait for the upload of each replay
   cudaEventRecordWithFlags(e->copied, cs, cudaEventRecordExternal);
   cudaMemsetAsync(e->d_counters, 0, 64, cs);
+  batch_census_kernel<<<g_census, 256, 0, cs>>>(hd, probs, prefix + 3 * stride, mt, e->d_counters);
   batch_cost_kernel<<<g_cost, 256, 0, cs>>>(hd, probs, prefix + 0 * stride, mt, e->d_counters);
   cudaEventRecord(e->fork.fork, cs);
   cudaStreamWaitEvent(e->fork.aux, e->fork.fork, 0);
@@ -240,10 +283,11 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
     int nseg = cap;
     Method m = mt;
     unsigned* counters = e->d_counters;
+    int wsm = warp_smem;
     void* rargs[] = {(void*)&hd, (void*)&probs, (void*)&lsegs, (void*)&lpre, (void*)&nseg,
-                     (void*)&m, (void*)&counters};
+                     (void*)&m, (void*)&counters, (void*)&wsm};
     void* sargs[] = {(void*)&hd, (void*)&probs, (void*)&bsegs, (void*)&bpre, (void*)&nseg,
-                     (void*)&m, (void*)&counters};
+                     (void*)&m, (void*)&counters, (void*)&wsm};
     // the row kernel holds the batch's longest chains: its node keeps the highest priority so
     // its blocks are dispatched ahead of the sheared kernel's
     int lo = 0, hi = 0;
@@ -273,16 +317,18 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem) {
   if (c != cudaSuccess) return set_err(e, c, "graph instantiate");
   e->graph_method = mt;
   e->graph_wta_smem = wta_smem;
-  e->graph_launches = 5;
+  e->graph_shear_smem = warp_smem;
+  e->graph_launches = 6;
   return 0;
 }
 
-static int capture(BatchEngine* e, const Method& mt, int wta_smem) {
+static int capture(BatchEngine* e, const Method& mt, int wta_smem, int warp_smem) {
   if (e->exec) {
     cudaGraphExecDestroy(e->exec);
     e->exec = nullptr;
   }
-  return mt.wide ? capture_t<true>(e, mt, wta_smem) : capture_t<false>(e, mt, wta_smem);
+  return mt.wide ? capture_t<true>(e, mt, wta_smem, warp_smem)
+                 : capture_t<false>(e, mt, wta_smem, warp_smem);
 }
 
 struct Keyed {
@@ -320,27 +366,32 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
   Problem* hp = reinterpret_cast<Problem*>(e->h_desc + probs_offset());
   int* prefix = reinterpret_cast<int*>(e->h_desc + prefix_offset(cap));
   const int stride = cap + 1;
-  int tot[3] = {0, 0, 0};
-  int wta_smem = 0;
+  int tot[4] = {0, 0, 0, 0};
+  int wta_smem = 0, warp_smem = 0;
   std::vector<Keyed> lk, bk;
   lk.reserve(n);
   bk.reserve(n);
   for (int p = 0; p < n; p++) {
     const Problem& pb = probs[p];
+    const BatchTune& tn = e->tune[tune_bucket(pb.W, pb.H, pb.D)];
     hp[p] = pb;
     prefix[0 * stride + p] = tot[0];
     prefix[1 * stride + p] = tot[1];
     prefix[2 * stride + p] = tot[2];
+    prefix[3 * stride + p] = tot[3];
     tot[0] += cost_items(pb.W, pb.H);
-    const int wt = wta_staged_px(pb.D, mt.wide != 0, kBatchWtaPx);
+    tot[3] += 2 * census_items(pb.W, pb.H);
+    const int wt = wta_staged_px(pb.D, mt.wide != 0, tn.wta_px);
     tot[1] += wta_items(pb.W, pb.H, wt);
     tot[2] += median_items(pb.W, pb.H);
     wta_smem = std::max(wta_smem, (int)wta_staged_smem_bytes(pb.D, mt.wide != 0, wt));
-    const int dpl = e->dpl_by_d16[pb.D / 16];
-    lk.push_back(Keyed{AggSeg{p, 0, row_units(pb.H, true), 32 / long_lanes(pb.D, dpl)}, pb.W});
-    bk.push_back(Keyed{AggSeg{p, 0, shear_items(pb.W, pb.D, 16, mt.num_paths, 1), 1}, pb.H});
+    warp_smem = std::max(warp_smem, shear_smem_bytes(tn.shear_dpl, mt.wide != 0, tn.shear_cpl));
+    lk.push_back(Keyed{AggSeg{p, 0, row_units(pb.H, true), 32 / long_lanes(pb.D, tn.row_dpl)},
+                       pb.W});
+    bk.push_back(Keyed{AggSeg{p, 0, shear_items(pb.W, pb.D, tn.shear_dpl, mt.num_paths,
+                                                tn.shear_cpl), 1}, pb.H});
   }
-  for (int k = 0; k < 3; k++) prefix[k * stride + n] = tot[k];
+  for (int k = 0; k < 4; k++) prefix[k * stride + n] = tot[k];
   const int nrows = write_queue(lk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 0)),
                                 reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 0)), cap);
   const int nshear = write_queue(bk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 1)),
@@ -351,10 +402,12 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
   hd->total[kStShear] = nshear;
   hd->total[kStWta] = tot[1];
   hd->total[kStMedian] = tot[2];
-  memcpy(hd->dpl_by_d16, e->dpl_by_d16, sizeof(hd->dpl_by_d16));
+  hd->total[kStCensus] = tot[3];
+  memcpy(hd->tune, e->tune, sizeof(hd->tune));
   if (!e->exec || memcmp(&e->graph_method, &mt, sizeof(Method)) != 0 ||
-      wta_smem > e->graph_wta_smem) {
-    rc = capture(e, mt, std::max(wta_smem, e->graph_wta_smem));
+      wta_smem > e->graph_wta_smem || warp_smem > e->graph_shear_smem) {
+    rc = capture(e, mt, std::max(wta_smem, e->graph_wta_smem),
+                 std::max(warp_smem, e->graph_shear_smem));
     if (rc) return rc;
   }
   cudaError_t c = cudaGraphLaunch(e->exec, s);

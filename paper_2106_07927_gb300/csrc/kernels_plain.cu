@@ -8,6 +8,11 @@
 
 namespace r2t {
 
+__global__ void __launch_bounds__(256) census_kernel(Problem pb, Method mt) {
+  __shared__ CensusSmem sm;
+  census_tile_dispatch(pb, mt, blockIdx.x, sm);
+}
+
 __global__ void __launch_bounds__(256) cost_kernel(Problem pb, Method mt) {
   __shared__ CostSmem sm;
   cost_tile_dispatch(pb, mt, blockIdx.x, sm);
@@ -126,9 +131,10 @@ static cudaError_t run_pass(const Problem& pb, const Method& mt, const Tuning& t
     if ((e = launch_ncc_cost(pb, mt, s)) != cudaSuccess) return e;
     *n += 3;
   } else {
+    census_kernel<<<2 * census_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
     cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    *n += 1;
+    *n += 2;
   }
   if (ev) cudaEventRecord(ev[0], s);
   if ((e = launch_aggregate(pb, mt, tn, s, fork)) != cudaSuccess) return e;

@@ -38,18 +38,19 @@ template <bool WIDE>
 cudaError_t launch_shear(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s);
 // Persistent batch variants of the two kernels, as handles for cudaLaunchKernel. Parameters:
 // (const BatchHeader*, const Problem*, const AggSeg* segs, const int* seg_prefix, int nseg,
-// Method, unsigned* counters); 256 threads; the sheared one takes 8 shear_default_smem_bytes(WIDE)
-// bytes of dynamic shared memory.
+// Method, unsigned* counters, int warp_smem); 256 threads; the sheared one takes 8 warp_smem
+// bytes of dynamic shared memory (warp_smem: the largest shear_smem_bytes of the batch's
+// settings).
 template <bool WIDE>
 const void* batch_row_kernel_fn();
 template <bool WIDE>
 const void* batch_shear_kernel_fn();
 
-// Plain single-pair pipeline: 5 kernel launches on stream s (census + cost + clearing of the
-// aggregated volume; two aggregation kernels; WTA + right-disparity keys; LR check + median).
-// With the exact check (mt.flags & 4; pb.flip and pb.dp set) first a flip kernel and the first
-// four launches again on the swapped, flipped pair: 10 launches. The NCC cost (mt.flags & 8)
-// takes 3 launches instead of 1 per pass.
+// Plain single-pair pipeline: 6 kernel launches on stream s (census of both images; cost +
+// clearing of the aggregated volume; two aggregation kernels; WTA + right-disparity keys; LR
+// check + median). With the exact check (mt.flags & 4; pb.flip and pb.dp set) first a flip kernel
+// and the first five launches again on the swapped, flipped pair: 12 launches. The NCC cost
+// (mt.flags & 8) takes 3 launches instead of 2 per pass.
 // Returns the number of launches through *launches.
 // ev: NULL, or events recorded around the stages: 5 (before the cost stage, after each of the
 // four), with the exact check 8 (before the flip; after the cost, aggregation and WTA of each

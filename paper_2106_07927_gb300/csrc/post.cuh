@@ -114,9 +114,12 @@ __device__ __forceinline__ void wta_dr_staged_t(const Problem& pb, int item, uin
     const uint8_t* src = reinterpret_cast<const uint8_t*>(pb.agg) + (rowbase + x0) * D * BPE;
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(smem);
     const int pieces = n * D * BPE / 16;  // D % 16 == 0
+    const int64_t vbytes = (int64_t)W * pb.H * D * BPE;  // extent of S (range checks)
+    (void)vbytes;
     for (int i = threadIdx.x; i < pieces; i += blockDim.x)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * i),
-                   "l"(src + 16 * (int64_t)i));
+      if (R2T_CHECKED(pb, src + 16 * (int64_t)i, 16, pb.agg, vbytes, 6))
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * i),
+                     "l"(src + 16 * (int64_t)i));
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
   const int ntar = T + D - 1;  // targets x0 - D + 1 .. x0 + T - 1
@@ -142,7 +145,9 @@ __device__ __forceinline__ void wta_dr_staged_t(const Problem& pb, int item, uin
     const uint32_t kl = wta_keys<NDL, EXACT>(pb, x0 + px, px, keys, lane, sv);
     mine = lane == it ? kl : mine;
   }
-  if (lane < it) pb.dl[rowbase + x0 + warp + nw * lane] = (uint16_t)(mine & 0xFFu);  // D^L
+  if (lane < it && R2T_CHECKED(pb, pb.dl + rowbase + x0 + warp + nw * lane, 2, pb.dl,
+                              2 * (int64_t)W * pb.H, 7))
+    pb.dl[rowbase + x0 + warp + nw * lane] = (uint16_t)(mine & 0xFFu);  // D^L
   __syncthreads();
   for (int i = threadIdx.x; i < ntar; i += blockDim.x) {
     const int x = x0 - D + 1 + i;

@@ -1,5 +1,7 @@
 """Batch engine: uneven pairs in persistent kernels under a CUDA graph give, per pair, the same
 bits as a single-pair call and as the oracle."""
+import itertools
+
 import numpy as np
 import pytest
 
@@ -159,3 +161,54 @@ def test_batch_of_64_uneven_pairs_against_oracle():
     for i, x, y, f in jobs:
         assert outs[i][y, x] == int(np.argmin(f.result())), (i, shapes[i], x, y)
     pool.shutdown()
+
+
+def test_every_batch_tuning_candidate_matches_oracle():
+    """Every setting the batch autotuner may pick (row disparities per lane, sheared disparities
+    and chains per lane, WTA tile), applied to every bucket of a small uneven batch (D from 32 to
+    256, both size classes), gives the oracle's maps; then the autotuner itself runs on that
+    batch, reports a table of valid entries and leaves maps that still match."""
+    import torch
+    rng = np.random.default_rng(21)
+    shapes = [(96, 40, 32), (130, 33, 64), (512, 520, 64), (200, 61, 128), (77, 50, 256),
+              (160, 45, 144)]
+    items = []
+    for i, (W, H, D) in enumerate(shapes):
+        L, R, _ = scenes.make_scene(("road", "nadir")[i % 2], 40 + i, W, H, D)
+        items.append((L, R, (W, H, D)))
+    refs = [oracle.sgm(L, R, D, 9, 7, 10, 120, 8, 3) for L, R, (W, H, D) in items]
+    tensors = [(torch.from_numpy(L).cuda(), torch.from_numpy(R).cuda()) for L, R, _ in items]
+    ctx = binding.Stereo(scenes.params(64, 64, 64, 9, 7, 10, 120, 8, 3))
+    buckets = sorted({(D, int(W * H >= (1 << 18))) for W, H, D in shapes})
+    tried = 0
+    for row, (sd, sc), wpx in itertools.product((2, 4, 8), ((16, 1), (16, 2)), (64, 128, 256)):
+        entries = [binding.res2tac_batch_tuning(D, lg, row, sd, sc, wpx) for D, lg in buckets
+                   if D % row == 0 and D // row <= 32 and D % sd == 0]
+        if not entries:
+            continue
+        binding.res2tac_set_batch_tuning(ctx.handle, entries)
+        outs = _run_batch(ctx.handle, tensors, [s for _, _, s in items])
+        for got, ref, (_, _, shp) in zip(outs, refs, items):
+            assert np.array_equal(got, ref), (row, sd, sc, wpx, shp)
+        tried += 1
+    assert tried >= 18
+    pairs, outs = [], []
+    for (L, R), (W, H, D) in zip(tensors, [s for _, _, s in items]):
+        o = torch.full((H, W), -1, dtype=torch.int16, device="cuda")
+        outs.append(o)
+        pairs.append(binding.res2tac_pair(L.data_ptr(), R.data_ptr(), L.stride(0), o.data_ptr(),
+                                          2 * W, W, H, D, 0))
+    table, ms0, ms1 = binding.res2tac_autotune_batch(ctx.handle, pairs,
+                                                     torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert len(table) == len(buckets) and 0 < ms1 <= ms0
+    for e in table:
+        assert (e.max_disp, e.large) in buckets and e.max_disp % e.shear_dpl == 0
+        got = binding.res2tac_get_batch_tuning(ctx.handle, e.max_disp, e.large)
+        assert got.as_dict() == e.as_dict()
+    for o, ref in zip(outs, refs):
+        assert np.array_equal(binding.u16(o), ref)
+    with pytest.raises(binding.Res2tacError):  # 8 disparities per sheared lane: not a setting
+        binding.res2tac_set_batch_tuning(ctx.handle, [binding.res2tac_batch_tuning(64, 0, 2, 8,
+                                                                                   1, 128)])
+    ctx.close()

@@ -153,7 +153,7 @@ def test_repeatable_and_host_path():
     binding.res2tac_compute_host(st.handle, left.ctypes.data, right.ctypes.data, prm["width"],
                                  host_out.ctypes.data, 2 * prm["width"], 0)
     assert np.array_equal(host_out, binding.u16(a))
-    assert binding.res2tac_last_launch_count(st.handle) == 5
+    assert binding.res2tac_last_launch_count(st.handle) == 6
     # pinned host buffers: read and written in place by the kernels
     hl = torch.from_numpy(left).pin_memory()
     hr = torch.from_numpy(right).pin_memory()
@@ -161,7 +161,7 @@ def test_repeatable_and_host_path():
     binding.res2tac_compute_host(st.handle, hl.data_ptr(), hr.data_ptr(), prm["width"],
                                  ho.data_ptr(), 2 * prm["width"], 0)
     assert np.array_equal(ho.numpy().view(np.uint16), binding.u16(a))
-    assert binding.res2tac_last_launch_count(st.handle) == 5
+    assert binding.res2tac_last_launch_count(st.handle) == 6
     st.close()
 
 
@@ -223,7 +223,7 @@ def test_exact_check_launches_stages_and_batch_rejection():
     L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
     st.compute(L, R)
     times = binding.res2tac_stage_times(st.handle)
-    assert binding.res2tac_last_launch_count(st.handle) == 10
+    assert binding.res2tac_last_launch_count(st.handle) == 12
     assert all(v > 0 for v in times.values())
     o = torch.empty_like(L, dtype=torch.int16)
     pair = binding.res2tac_pair(L.data_ptr(), R.data_ptr(), L.shape[1], o.data_ptr(),

@@ -43,7 +43,7 @@ def _check(left, right, prm, **kw):
     want, want_ref = oracle.sgm_subpixel(left, right, prm["max_disp"], prm["census_w"],
                                          prm["census_h"], prm["p1"], prm["p2"], prm["num_paths"],
                                          prm["flags"], prm["lr_threshold"])
-    assert launches == (10 if prm["flags"] & 4 else 5)
+    assert launches == (12 if prm["flags"] & 4 else 6)
     err = np.abs(ref - want_ref)
     assert err.max() <= TOL, f"refined D^L: max error {err.max()} at {np.argmax(err)}"
     inv = np.isinf(want)
