@@ -34,9 +34,11 @@ __host__ __device__ inline int census_items(int W, int H) {
 struct CensusSmem {
   uint8_t win[kCtTY + 6][kCtTX + 8];  // rows y0 - ry .. y0 + 7 + ry, columns x0 - rx .. x0 + 31 + rx
 };
+// CT_R(x0 - D + i) sits at r[i & 3][i >> 2]: the lanes of a warp read i, i - 4, i - 8, ... (their
+// words are 4 disparities apart), which this split keeps on consecutive words (no bank conflict).
 struct CostSmem {
-  uint64_t l[kCostTX];        // CT_L(x0 .. x0 + kCostTX - 1)
-  uint64_t r[kCostTX + 256];  // CT_R(x0 - D + i), i < kCostTX + D (0 outside the image)
+  uint64_t l[kCostTX];                // CT_L(x0 .. x0 + kCostTX - 1)
+  uint64_t r[4][(kCostTX + 256) / 4]; // CT_R(x0 - D + i), i < kCostTX + D (0 outside the image)
 };
 
 // Census descriptor of the pixel whose window's top-left byte is win[0][i] (row stride kCtTX + 8).
@@ -102,16 +104,22 @@ __device__ __forceinline__ uint32_t hamming(uint64_t a, uint64_t b) {
   return CT64 ? (uint32_t)__popcll(a ^ b) : (uint32_t)__popc((uint32_t)a ^ (uint32_t)b);
 }
 
-// The cost words of a tile for D = 4 NQ (NQ dividing 256): thread t computes word q = t % NQ
-// (d = 4q .. 4q + 3) of the PPR = kCostTX NQ / 256 consecutive pixels px0 = (t / NQ) PPR ...;
-// d = 4q + j at tile pixel px reads r[px + D - 4q - j]. Tiles whose pixels all have x >= D - 1
-// skip the test for x - d < 0.
+// The cost words of a tile for D = 4 NQ (NQ = 8 .. 64 dividing 256): thread t computes word
+// q = t % NQ (d = 4q .. 4q + 3) of the PPR = kCostTX NQ / 256 consecutive pixels
+// px0 = (t / NQ) PPR ...; d = 4q + j at tile pixel px0 + k reads right descriptor
+// i = a + k - j with a = px0 + D - 4q, a multiple of 4 (PPR is), so its phase (k - j) & 3 and word
+// a / 4 + floor((k - j) / 4) are compile-time offsets. From one pixel to the next, three of the
+// four descriptors carry over in registers. Tiles whose pixels all have x >= D - 1 skip the test
+// for x - d < 0.
 template <bool CT64, int NQ>
 __device__ __forceinline__ void cost_words(const CostSmem& sm, uint32_t* out, int x0, int npx) {
   constexpr int D = 4 * NQ, PPR = kCostTX * NQ / 256;
+  static_assert(PPR % 4 == 0, "runs start on a multiple of 4");
   const int q = threadIdx.x % NQ, px0 = (threadIdx.x / NQ) * PPR;
-  const uint64_t* rp = &sm.r[px0 + D - 4 * q];  // rp[k - j]: d = 4q + j at pixel px0 + k
-  uint64_t r0 = rp[0], r1 = rp[-1], r2 = rp[-2], r3 = rp[-3];
+  const int aw = (px0 + D - 4 * q) >> 2;  // word of descriptor a (phase 0)
+  // descriptor a + o for a compile-time offset o >= -3
+#define R2T_RD(o) sm.r[(o) & 3][aw + ((o) >> 2)]
+  uint64_t r0 = R2T_RD(0), r1 = R2T_RD(-1), r2 = R2T_RD(-2), r3 = R2T_RD(-3);
   uint32_t* o = out + px0 * NQ + q;
   const bool interior = x0 >= D - 1;  // block-uniform
 #pragma unroll
@@ -135,9 +143,10 @@ __device__ __forceinline__ void cost_words(const CostSmem& sm, uint32_t* out, in
       r3 = r2;
       r2 = r1;
       r1 = r0;
-      r0 = rp[k + 1];
+      r0 = R2T_RD(k + 1);
     }
   }
+#undef R2T_RD
 }
 
 // One row segment of kCostTX pixels, all disparities, written as 4-byte words of 4 consecutive
@@ -158,14 +167,13 @@ __device__ __forceinline__ void cost_tile(const Problem& pb, int item, CostSmem&
   for (int i = threadIdx.x; i < kCostTX + D; i += blockDim.x) {
     if (i < kCostTX) sm.l[i] = i < npx ? ctl[x0 + i] : 0ull;
     const int xr = x0 - D + i;  // only x - d >= 0 within the row are read
-    sm.r[i] = (xr >= 0 && xr < W) ? ctr[xr] : 0ull;
+    sm.r[i & 3][i >> 2] = (xr >= 0 && xr < W) ? ctr[xr] : 0ull;
   }
   __syncthreads();
   const int nq = D / 4;  // 4-disparity words per pixel
   uint32_t* out = reinterpret_cast<uint32_t*>(pb.cost + ((int64_t)y * W + x0) * D);
-  if (blockDim.x == 256 && (nq == 4 || nq == 8 || nq == 16 || nq == 32 || nq == 64)) {
+  if (blockDim.x == 256 && (nq == 8 || nq == 16 || nq == 32 || nq == 64)) {
     switch (nq) {
-      case 4: cost_words<CT64, 4>(sm, out, x0, npx); break;
       case 8: cost_words<CT64, 8>(sm, out, x0, npx); break;
       case 16: cost_words<CT64, 16>(sm, out, x0, npx); break;
       case 32: cost_words<CT64, 32>(sm, out, x0, npx); break;
@@ -182,7 +190,8 @@ __device__ __forceinline__ void cost_tile(const Problem& pb, int item, CostSmem&
 #pragma unroll
       for (int j = 0; j < 4; j++) {
         const int d = 4 * q + j;
-        v[j] = x >= d ? hamming<CT64>(cl, sm.r[px + D - d]) : (uint32_t)kCostOutside;
+        const int i = px + D - d;
+        v[j] = x >= d ? hamming<CT64>(cl, sm.r[i & 3][i >> 2]) : (uint32_t)kCostOutside;
       }
       out[it] = pack_bytes(v[0], v[1], v[2], v[3]);
     }

@@ -95,17 +95,19 @@ __device__ __noinline__ uint32_t ncc_exact_k(int cov, int va, int vb, float q) {
   return (uint32_t)min(k, 255);
 }
 
-// The 8-bit cost of one patch pair from its sums: 255 - k, k = rint((cov * iA) * jB) clamped to
-// 0..255, settled on integers near a rounding boundary (va_p, vb_p: the two exact variances, read
-// only then).
-__device__ __forceinline__ uint32_t ncc_cost_of(int nn, int sab, int sa, float ia, uint2 mb,
-                                                const int32_t* va_p, const int32_t* vb_p) {
-  const int cov = nn * sab - sa * (int)mb.x;  // |cov| < 2^27
-  const float q = __fmul_rn(__fmul_rn(__int2float_rn(cov), ia), __uint_as_float(mb.y));
+// The fp32 estimate q = (cov * iA) * jB of 255 Phi for one patch pair from its sums (cov is
+// returned too).
+__device__ __forceinline__ float ncc_estimate(int nn, int sab, int sa, float ia, uint2 mb,
+                                              int& cov) {
+  cov = nn * sab - sa * (int)mb.x;  // |cov| < 2^27
+  return __fmul_rn(__fmul_rn(__int2float_rn(cov), ia), __uint_as_float(mb.y));
+}
+
+// k = rint(q) clamped to 0 .. 255.
+__device__ __forceinline__ uint32_t ncc_round(float q) {
   uint32_t k;
-  asm("cvt.rni.sat.u8.f32 %0, %1;" : "=r"(k) : "f"(q));  // rint, then clamp to 0 .. 255
-  if (cov > 0 && fabsf(q - floorf(q) - 0.5f) < kNccTieBand) k = ncc_exact_k(cov, *va_p, *vb_p, q);
-  return 255u - k;
+  asm("cvt.rni.sat.u8.f32 %0, %1;" : "=r"(k) : "f"(q));
+  return k;
 }
 
 template <int N_>
@@ -254,15 +256,25 @@ __global__ void __launch_bounds__(256, N_ == 5 ? 4 : 3)
     if (t >= 2 * R) {  // output row y0 + t - 2R
       const uint2 a = *sa_p;
       const uint2* mb = sa_p + mo;
-      const int32_t* va = sv + (sa_p - st);  // exact variances, same indexing as the stats
+      float q[4];
+      int cov[4];
       uint32_t c[4];
+      float far = 0.0f;  // the largest distance of a q from its rounded value
 #pragma unroll
       for (int k = 0; k < 4; k++) {
-        // outside (x - d < 0) the cost is 255 and the variances are not read
-        c[k] = inside[k] ? ncc_cost_of(nn, vs[k], (int)a.x, __uint_as_float(a.y), mb[-k], va,
-                                       va + mo - k)
-                         : (uint32_t)kCostOutside;
+        q[k] = ncc_estimate(nn, vs[k], (int)a.x, __uint_as_float(a.y), mb[-k], cov[k]);
+        c[k] = 255u - ncc_round(q[k]);
+        far = fmaxf(far, fabsf(q[k] - rintf(q[k])));
       }
+      if (far > 0.5f - kNccTieBand) {  // some q near a k + 1/2 boundary: settle it on integers
+        const int32_t* va = sv + (sa_p - st);  // exact variances, same indexing as the stats
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          if (inside[k] && cov[k] > 0 && fabsf(q[k] - rintf(q[k])) > 0.5f - kNccTieBand)
+            c[k] = 255u - ncc_exact_k(cov[k], *va, va[mo - k], q[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; k++) c[k] = inside[k] ? c[k] : (uint32_t)kCostOutside;
       *out = c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24);
       sa_p += W;
       out += out_row;
