@@ -457,75 +457,91 @@ def main():
 
         batched = None
         if not args.no_batch:
-            pairs_in = _batch_inputs(args.batch_pairs, torch)
-            bprm = scenes.params(64, 64, 64, 9, 7, 10, 120, 8,
-                                 scenes.FLAG_LR_CHECK | scenes.FLAG_MEDIAN)
-            bctx = binding.Stereo(bprm)
-            bouts, bpairs, singles = [], [], []
-            for Lb, Rb, w, h, d in pairs_in:
-                o = torch.empty((h, w), dtype=torch.int16, device="cuda")
-                bouts.append(o)
-                bpairs.append(binding.res2tac_pair(Lb.data_ptr(), Rb.data_ptr(), w, o.data_ptr(),
-                                                   2 * w, w, h, d, 0))
-            bde = sum(w * h * d for _, _, w, h, d in pairs_in)
-            # the batch autotuner (per bucket of D and size class) before the timed batches
-            table, ms_def, ms_tuned = binding.res2tac_autotune_batch(bctx.handle, bpairs, sh)
-            for _ in range(2):
-                binding.res2tac_compute_batch(bctx.handle, bpairs, sh)
-            torch.cuda.synchronize()
-            be0 = torch.cuda.Event(enable_timing=True)
-            be1 = torch.cuda.Event(enable_timing=True)
-            barrier()
-            be0.record(stream)
-            for _ in range(args.batch_steps):
-                binding.res2tac_compute_batch(bctx.handle, bpairs, sh)
-            be1.record(stream)
-            barrier()
-            t_batch = max_over_ranks(be0.elapsed_time(be1) / 1e3 / args.batch_steps)
-            launches += binding.res2tac_last_launch_count(bctx.handle) * args.batch_steps
-            batch_result = [o.clone() for o in bouts]
-            # the same 64 pairs as per-pair launches, one context each
-            souts = []
-            for Lb, Rb, w, h, d in pairs_in:
-                c = binding.Stereo(scenes.params(w, h, d, 9, 7, 10, 120, 8, 3))
-                singles.append((c, Lb, Rb, w, h))
-                souts.append(torch.empty((h, w), dtype=torch.int16, device="cuda"))
+            def batch_vs_per_pair(pairs_in):
+                """The pairs as one res2tac_compute_batch (autotuned first) and as per-pair
+                res2tac_compute launches: MDE/s of both, bit-identity of the maps."""
+                nonlocal launches
+                bprm = scenes.params(64, 64, 64, 9, 7, 10, 120, 8,
+                                     scenes.FLAG_LR_CHECK | scenes.FLAG_MEDIAN)
+                bctx = binding.Stereo(bprm)
+                bouts, bpairs, singles = [], [], []
+                for Lb, Rb, w, h, d in pairs_in:
+                    o = torch.empty((h, w), dtype=torch.int16, device="cuda")
+                    bouts.append(o)
+                    bpairs.append(binding.res2tac_pair(Lb.data_ptr(), Rb.data_ptr(), w,
+                                                       o.data_ptr(), 2 * w, w, h, d, 0))
+                bde = sum(w * h * d for _, _, w, h, d in pairs_in)
+                # the batch autotuner (per bucket of D and size class) before the timed batches
+                table, ms_def, ms_tuned = binding.res2tac_autotune_batch(bctx.handle, bpairs, sh)
+                for _ in range(2):
+                    binding.res2tac_compute_batch(bctx.handle, bpairs, sh)
+                torch.cuda.synchronize()
+                be0 = torch.cuda.Event(enable_timing=True)
+                be1 = torch.cuda.Event(enable_timing=True)
+                barrier()
+                be0.record(stream)
+                for _ in range(args.batch_steps):
+                    binding.res2tac_compute_batch(bctx.handle, bpairs, sh)
+                be1.record(stream)
+                barrier()
+                t_batch = max_over_ranks(be0.elapsed_time(be1) / 1e3 / args.batch_steps)
+                launches += binding.res2tac_last_launch_count(bctx.handle) * args.batch_steps
+                batch_result = [o.clone() for o in bouts]
+                # the same pairs as per-pair launches, one context each
+                souts = []
+                for Lb, Rb, w, h, d in pairs_in:
+                    c = binding.Stereo(scenes.params(w, h, d, 9, 7, 10, 120, 8, 3))
+                    singles.append((c, Lb, Rb, w, h))
+                    souts.append(torch.empty((h, w), dtype=torch.int16, device="cuda"))
 
-            def per_pair():
-                for (c, Lb, Rb, w, h), o in zip(singles, souts):
-                    binding.res2tac_compute(c.handle, Lb.data_ptr(), Rb.data_ptr(), w,
-                                            o.data_ptr(), 2 * w, sh)
+                def per_pair():
+                    for (c, Lb, Rb, w, h), o in zip(singles, souts):
+                        binding.res2tac_compute(c.handle, Lb.data_ptr(), Rb.data_ptr(), w,
+                                                o.data_ptr(), 2 * w, sh)
 
-            per_pair()
-            torch.cuda.synchronize()
-            barrier()
-            be0.record(stream)
-            for _ in range(args.batch_steps):
                 per_pair()
-            be1.record(stream)
-            barrier()
-            t_single = max_over_ranks(be0.elapsed_time(be1) / 1e3 / args.batch_steps)
-            launches += sum(binding.res2tac_last_launch_count(c.handle) for c, *_ in singles) * \
-                args.batch_steps
-            same = all(torch.equal(a, b) for a, b in zip(batch_result, souts))
-            batched = {
-                "value": round(ws * bde / t_batch / 1e6, 1), "unit": "MDE/s",
-                "pairs": args.batch_pairs, "de_per_batch": bde,
-                "ms_per_batch": round(1e3 * t_batch, 3),
-                "per_pair_launches": {"value": round(ws * bde / t_single / 1e6, 1),
-                                      "ms_per_batch": round(1e3 * t_single, 3)},
-                "speedup_vs_per_pair": round(t_single / t_batch, 3),
-                "bit_identical_to_per_pair": bool(same),
-                "autotune": {"table": [e.as_dict() for e in table],
-                             "mde_per_s_default": round(bde / (ms_def / 1e3) / 1e6, 1),
-                             "mde_per_s_tuned": round(bde / (ms_tuned / 1e3) / 1e6, 1),
-                             "ms_default": round(ms_def, 3), "ms_tuned": round(ms_tuned, 3)},
-                "sizes": "W in {320,640,1024,1242,1920}, H in {240,375,512,768,1080}, "
-                         "D in {64,128,256}, seed 0",
-            }
-            for c, *_ in singles:
-                c.close()
-            bctx.close()
+                torch.cuda.synchronize()
+                barrier()
+                be0.record(stream)
+                for _ in range(args.batch_steps):
+                    per_pair()
+                be1.record(stream)
+                barrier()
+                t_single = max_over_ranks(be0.elapsed_time(be1) / 1e3 / args.batch_steps)
+                launches += sum(binding.res2tac_last_launch_count(c.handle)
+                                for c, *_ in singles) * args.batch_steps
+                same = all(torch.equal(a, b) for a, b in zip(batch_result, souts))
+                for c, *_ in singles:
+                    c.close()
+                bctx.close()
+                return {
+                    "value": round(ws * bde / t_batch / 1e6, 1), "unit": "MDE/s",
+                    "pairs": len(pairs_in), "de_per_batch": bde,
+                    "ms_per_batch": round(1e3 * t_batch, 3),
+                    "per_pair_launches": {"value": round(ws * bde / t_single / 1e6, 1),
+                                          "ms_per_batch": round(1e3 * t_single, 3)},
+                    "speedup_vs_per_pair": round(t_single / t_batch, 3),
+                    "bit_identical_to_per_pair": bool(same),
+                    "autotune": {"table": [e.as_dict() for e in table],
+                                 "mde_per_s_default": round(bde / (ms_def / 1e3) / 1e6, 1),
+                                 "mde_per_s_tuned": round(bde / (ms_tuned / 1e3) / 1e6, 1),
+                                 "ms_default": round(ms_def, 3), "ms_tuned": round(ms_tuned, 3)}}
+
+            batched = batch_vs_per_pair(_batch_inputs(args.batch_pairs, torch))
+            batched["sizes"] = ("W in {320,640,1024,1242,1920}, H in {240,375,512,768,1080}, "
+                                "D in {64,128,256}, seed 0")
+            # batches of one size: the 1242x375 D=128 pair (16 seeded pairs) and the 320x240
+            # D=64 pair of the small workload (64 pairs), census 9x7 as in the mix
+            same_size = {}
+            for name, n, wl in (("1242x375_d128 x16", 16, WORKLOAD),
+                                ("320x240_d64 x64", 64, "320x240_d64_ct5x5_r4")):
+                items = []
+                for sd in range(n):
+                    l_, r_, _, p_ = scenes.single_pair(wl, sd)
+                    items.append((torch.from_numpy(l_).cuda(), torch.from_numpy(r_).cuda(),
+                                  p_["width"], p_["height"], p_["max_disp"]))
+                same_size[name] = batch_vs_per_pair(items)
+            batched["same_size_batches"] = same_size
         serving = None
         if not args.no_serve and rank == 0:
             serving = _serving_sweep(args, torch, np)
