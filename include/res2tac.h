@@ -194,15 +194,18 @@ int res2tac_compute_raw(res2tac_t h, const uint8_t* raw_left, const uint8_t* raw
                         res2tac_stream_t s);
 
 /* Runs n independent pairs of uneven sizes as one batch on stream s (the paper processes one
- * pair at a time, Sec. 2.2; batching is this library's addition). The batch runs as persistent
- * kernels fed by a device work queue over all pairs, recorded once into a CUDA graph and
- * replayed while the batch layout (n and every pair's W, H, D) stays the same. The context
- * grows its batch scratch when a larger batch arrives: that call allocates and must not be made
- * during stream capture. pairs: host array of n descriptors with device pointers. Results are
- * bit-identical to res2tac_compute on each pair alone. No block of the engine ever waits for
- * another (work is claimed with one atomic increment), so there is no device-side wait that
- * could time out: RES2TAC_ETIMEOUT is reserved and not returned. RES2TAC_EINVAL for an invalid
- * pair, or for RES2TAC_EXACT_CC / RES2TAC_NCC contexts (single pairs only). */
+ * pair at a time, Sec. 2.2; batching is this library's addition). The pairs are sorted by memory
+ * footprint and cut into groups of at most 96 MB of cost and aggregated volumes (a larger pair is
+ * a group of its own); each group runs the six stages as persistent kernels fed by device work
+ * queues over its pairs, and groups alternate between two stream slots so consecutive groups
+ * overlap. The whole batch is one CUDA graph, captured once per group count and replayed while
+ * the capacities last (res2tac_last_launch_count: 6 per group). The context grows its batch
+ * scratch when a larger batch arrives: that call allocates and must not be made during stream
+ * capture. pairs: host array of n descriptors with device pointers. Results are bit-identical to
+ * res2tac_compute on each pair alone. No block of the engine ever waits for another (work is
+ * claimed with one atomic increment), so there is no device-side wait that could time out:
+ * RES2TAC_ETIMEOUT is reserved and not returned. RES2TAC_EINVAL for an invalid pair, or for
+ * RES2TAC_EXACT_CC / RES2TAC_NCC contexts (single pairs only). */
 int res2tac_compute_batch(res2tac_t h, const res2tac_pair* pairs, int32_t n, res2tac_stream_t s);
 
 /* Copies the intermediates of the last res2tac_compute on this context into caller buffers

@@ -165,16 +165,18 @@ __device__ __forceinline__ void shear_dispatch(const Problem& pb, const Method& 
   }
 }
 
+// Persistent aggregation kernels of one group of a batch: warps claim row units / sheared items
+// from the group's queue; the segment of an item is found among the group's pairs.
 template <bool WIDE>
-__global__ void __launch_bounds__(256) batch_row_kernel(const BatchHeader* hd, const Problem* probs,
-                                                        const AggSeg* segs, const int* seg_prefix,
-                                                        int nseg, Method mt, unsigned* counters,
-                                                        int warp_smem) {
-  const int total = hd->total[kStRows];
+__global__ void __launch_bounds__(256) batch_row_kernel(const BatchHeader* hd, const GroupDesc* gd,
+                                                        const Problem* probs, const AggSeg* segs,
+                                                        const int* seg_prefix, Method mt,
+                                                        unsigned* counters, int warp_smem) {
+  const int p0 = gd->p0, np = gd->np, lo = gd->lo[kStRows], hi = gd->hi[kStRows];
   for (;;) {
-    const int item = claim_warp(&counters[kStRows]);
-    if (item >= total) break;
-    const int si = find_slot(seg_prefix, nseg, item);
+    const int item = lo + claim_warp(&counters[kStRows]);
+    if (item >= hi) break;
+    const int si = p0 + find_slot(seg_prefix + p0, np, item);
     const AggSeg sg = segs[si];
     const Problem pb = probs[sg.pair];
     rows_dispatch<WIDE>(pb, mt, sg.begin + (item - seg_prefix[si]) * sg.group, sg.end,
@@ -186,17 +188,17 @@ __global__ void __launch_bounds__(256) batch_row_kernel(const BatchHeader* hd, c
 // bucket setting the batch uses.
 template <bool WIDE>
 __global__ void __launch_bounds__(256) batch_shear_kernel(const BatchHeader* hd,
+                                                          const GroupDesc* gd,
                                                           const Problem* probs, const AggSeg* segs,
-                                                          const int* seg_prefix, int nseg,
-                                                          Method mt, unsigned* counters,
-                                                          int warp_smem) {
+                                                          const int* seg_prefix, Method mt,
+                                                          unsigned* counters, int warp_smem) {
   extern __shared__ __align__(16) uint8_t shm[];
   uint8_t* base = shm + (threadIdx.x >> 5) * warp_smem;
-  const int total = hd->total[kStShear];
+  const int p0 = gd->p0, np = gd->np, lo = gd->lo[kStShear], hi = gd->hi[kStShear];
   for (;;) {
-    const int item = claim_warp(&counters[kStShear]);
-    if (item >= total) break;
-    const int si = find_slot(seg_prefix, nseg, item);
+    const int item = lo + claim_warp(&counters[kStShear]);
+    if (item >= hi) break;
+    const int si = p0 + find_slot(seg_prefix + p0, np, item);
     const AggSeg sg = segs[si];
     const Problem pb = probs[sg.pair];
     const BatchTune tn = hd->tune[tune_bucket(pb.W, pb.H, pb.D)];

@@ -44,6 +44,15 @@ struct AggSeg {
   int pair, begin, end, group;  // lines / chains [begin, end) of one pair, `group` per warp item
 };
 
+// One group of the batch: pairs [p0, p0 + np) of the descriptor arrays and, per stage, its items
+// [lo, hi) in that stage's numbering (item prefixes are cumulative over the whole batch). Each
+// group has its own kNumCounters queue counters.
+struct GroupDesc {
+  int p0, np;
+  int lo[kNumCounters], hi[kNumCounters];
+};
+constexpr int kCountersPerGroup = 8;
+
 __device__ __forceinline__ int find_slot(const int* prefix, int n, int item) {
   int lo = 0, hi = n - 1;  // largest p with prefix[p] <= item
   while (lo < hi) {

@@ -1,21 +1,27 @@
-// Batch engine: every stage of the pipeline runs as a persistent kernel over all pairs of the
-// batch. A block (or, in the aggregation, a warp) claims its next work item from a device queue
-// with one atomic increment and maps it to (pair, item of that pair) through prefix tables; no
-// block ever waits for another, so the queues need no device-side spin. Stage order is kept by
-// the launch order on one stream; the two aggregation kernels (row paths and sheared-column
-// paths) run concurrently on a forked stream inside the graph. The descriptor upload, the queue
-// reset and the stage kernels are recorded once into a CUDA graph and replayed while the
-// capacities last.
+// Batch engine: many pairs of uneven W, H, D run as persistent stage kernels fed by device work
+// queues, recorded into a CUDA graph and replayed while the batch layout lasts.
 //
-// Aggregation work is described by segments, two per pair: its rows (one warp item per group of
-// rows) and its sheared columns (one warp item per group of adjacent chains of one kind). Each
-// queue is ordered by the chain length of its segments across the whole batch (longest first),
-// so the sequential chains that bound the batch's duration start earliest.
+// Groups. The pairs are sorted by their memory footprint (cost volume + aggregated volume) and
+// cut into groups whose footprint stays within kGroupBytes (a larger pair is a group of its own).
+// Each group runs the six stages - census, cost, the two aggregation kernels (concurrently, on
+// a forked stream), WTA, LR check + median - as persistent kernels over its own pairs, so a
+// group's volumes are still in L2 when its next stage reads them, as they are for a pair run
+// alone, while the pairs of a group fill the GPU together. Groups alternate between two slots
+// of streams, so one group's latency-bound aggregation overlaps the next group's other stages.
+//
+// A block (or, in the aggregation, a warp) claims its next work item from its group's queue
+// with one atomic increment and maps it to (pair, item of that pair) through prefix tables; no
+// block ever waits for another, so the queues need no device-side spin. Aggregation work is
+// described by segments, two per pair: its rows (one warp item per group of rows) and its
+// sheared columns (one warp item per group of adjacent chains of one kind); each group's queue
+// is ordered by chain length (longest first), so the sequential chains that bound the group's
+// duration start earliest.
 #include <cuda_runtime.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <numeric>
 #include <vector>
 
 #include "aggregate.cuh"
@@ -28,69 +34,57 @@
 namespace r2t {
 
 
-__global__ void __launch_bounds__(256) batch_census_kernel(const BatchHeader* hd,
+// Footprint bound of one group (bytes of cost and aggregated volumes) and its pair count.
+constexpr size_t kGroupBytes = 96u << 20;
+constexpr int kGroupMaxPairs = 32;
+constexpr int kSlots = 2;  // groups in flight
+
+// Block-claimed stage kernels of one group: item = lo + claim, pair found among the group's.
+#define R2T_GROUP_LOOP(STAGE, BODY)                                                  \
+  __shared__ int s_item;                                                             \
+  const int p0 = gd->p0, np = gd->np, lo = gd->lo[STAGE], hi = gd->hi[STAGE];       \
+  for (;;) {                                                                         \
+    const int item = lo + claim_block(&counters[STAGE], &s_item);                   \
+    if (item >= hi) break;                                                           \
+    const int p = p0 + find_slot(prefix + p0, np, item);                             \
+    const Problem pb = probs[p];                                                     \
+    BODY;                                                                            \
+  }
+
+__global__ void __launch_bounds__(256) batch_census_kernel(const GroupDesc* gd,
                                                            const Problem* probs,
                                                            const int* prefix, Method mt,
                                                            unsigned* counters) {
   __shared__ CensusSmem sm;
-  __shared__ int s_item;
-  const int total = hd->total[kStCensus], n = hd->n;
-  for (;;) {
-    const int item = claim_block(&counters[kStCensus], &s_item);
-    if (item >= total) break;
-    const int p = find_slot(prefix, n, item);
-    const Problem pb = probs[p];
-    census_tile_dispatch(pb, mt, item - prefix[p], sm);
-  }
+  R2T_GROUP_LOOP(kStCensus, census_tile_dispatch(pb, mt, item - prefix[p], sm))
 }
 
-__global__ void __launch_bounds__(256) batch_cost_kernel(const BatchHeader* hd,
+__global__ void __launch_bounds__(256) batch_cost_kernel(const GroupDesc* gd,
                                                          const Problem* probs, const int* prefix,
                                                          Method mt, unsigned* counters) {
   __shared__ CostSmem sm;
-  __shared__ int s_item;
-  const int total = hd->total[kStCost], n = hd->n;
-  for (;;) {
-    const int item = claim_block(&counters[kStCost], &s_item);
-    if (item >= total) break;
-    const int p = find_slot(prefix, n, item);
-    const Problem pb = probs[p];
-    cost_tile_dispatch(pb, mt, item - prefix[p], sm);
-  }
+  R2T_GROUP_LOOP(kStCost, cost_tile_dispatch(pb, mt, item - prefix[p], sm))
 }
 
-
+// (the barrier inside claim_block also ends the previous item's use of the shared memory)
 template <bool WIDE>
-__global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, const Problem* probs,
-                                                        const int* prefix, unsigned* counters) {
+__global__ void __launch_bounds__(256) batch_wta_kernel(const BatchHeader* hd, const GroupDesc* gd,
+                                                        const Problem* probs, const int* prefix,
+                                                        unsigned* counters) {
   extern __shared__ __align__(16) uint8_t wsm[];
-  __shared__ int s_item;
-  const int total = hd->total[kStWta], n = hd->n;
-  for (;;) {
-    // (the barrier inside claim_block also ends the previous item's use of the shared memory)
-    const int item = claim_block(&counters[kStWta], &s_item);
-    if (item >= total) break;
-    const int p = find_slot(prefix, n, item);
-    const Problem pb = probs[p];
-    const int T = wta_staged_px(pb.D, WIDE, hd->tune[tune_bucket(pb.W, pb.H, pb.D)].wta_px);
-    wta_dr_staged<WIDE>(pb, item - prefix[p], wsm, T);
-  }
+  R2T_GROUP_LOOP(kStWta,
+                 wta_dr_staged<WIDE>(pb, item - prefix[p], wsm,
+                                     wta_staged_px(pb.D, WIDE,
+                                                   hd->tune[tune_bucket(pb.W, pb.H, pb.D)].wta_px)))
 }
 
-__global__ void __launch_bounds__(256) batch_median_kernel(const BatchHeader* hd,
+__global__ void __launch_bounds__(256) batch_median_kernel(const GroupDesc* gd,
                                                            const Problem* probs, const int* prefix,
                                                            Method mt, unsigned* counters) {
   __shared__ MedianSmem sm;
-  __shared__ int s_item;
-  const int total = hd->total[kStMedian], n = hd->n;
-  for (;;) {
-    const int item = claim_block(&counters[kStMedian], &s_item);
-    if (item >= total) break;
-    const int p = find_slot(prefix, n, item);
-    const Problem pb = probs[p];
-    lr_median_tile<false, false>(pb, mt, item - prefix[p], sm);
-  }
+  R2T_GROUP_LOOP(kStMedian, (lr_median_tile<false, false>(pb, mt, item - prefix[p], sm)))
 }
+#undef R2T_GROUP_LOOP
 
 struct BatchEngine {
   char* scratch = nullptr;
@@ -99,36 +93,50 @@ struct BatchEngine {
   char* h_desc = nullptr;  // its pinned host image
   size_t desc_bytes = 0;
   int cap_pairs = 0;
-  unsigned* d_counters = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  Fork fork = {nullptr, nullptr, nullptr};
-  cudaGraphExec_t exec = nullptr;
+  unsigned* d_counters = nullptr;  // kCountersPerGroup per group, cap_pairs groups
+  cudaStream_t main[kSlots] = {nullptr, nullptr};  // main[0] is the capture origin
+  cudaStream_t aux[kSlots] = {nullptr, nullptr};   // row-path kernels of each slot
+  cudaEvent_t ev_fork[kSlots] = {nullptr, nullptr}, ev_join[kSlots] = {nullptr, nullptr};
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  // captured graphs by group count (index G), all for graph_method and the shared-memory sizes
+  std::vector<cudaGraphExec_t> execs;
   cudaEvent_t copied = nullptr;  // recorded in the graph after the descriptor upload
   bool copy_pending = false;
   Method graph_method;
   int graph_wta_smem = 0;
   int graph_shear_smem = 0;  // per warp
-  int graph_launches = 0;
   BatchTune tune[kTuneBuckets];
   char err[256];
 };
 
+// Descriptor block: BatchHeader | Problem[cap] | int prefix[4][cap + 1] (cost, wta, median,
+// census items) | for the row and the sheared queue AggSeg[cap], int seg_prefix[cap + 1] |
+// GroupDesc[cap].
 static size_t probs_offset() { return (sizeof(BatchHeader) + 255) / 256 * 256; }
 static size_t prefix_offset(int cap) { return probs_offset() + (size_t)cap * sizeof(Problem); }
-static size_t segs_offset(int cap, int q) {  // q = 0 rows, 1 sheared columns
+static size_t segs_offset(int cap, int q) {  // q = 0 rows, 1 sheared columns, 2 groups
   const size_t base = (prefix_offset(cap) + 4 * sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
   const size_t per = ((size_t)cap * sizeof(AggSeg) + sizeof(int) * (size_t)(cap + 1) + 15) / 16 * 16;
   return base + q * per;
 }
 static size_t seg_prefix_offset(int cap, int q) { return segs_offset(cap, q) + (size_t)cap * sizeof(AggSeg); }
-static size_t desc_size(int cap) { return segs_offset(cap, 2); }
+static size_t groups_offset(int cap) { return segs_offset(cap, 2); }
+static size_t desc_size(int cap) { return groups_offset(cap) + (size_t)cap * sizeof(GroupDesc); }
 
-size_t batch_fixed_bytes(int n) { return desc_size(n) + 4096; }
+size_t batch_fixed_bytes(int n) {
+  return desc_size(n) + (size_t)n * kCountersPerGroup * sizeof(unsigned) + 4096;
+}
 
 static int set_err(BatchEngine* e, cudaError_t c, const char* what) {
   cudaGetLastError();
   snprintf(e->err, sizeof(e->err), "%s: %s", what, cudaGetErrorString(c));
   return c == cudaErrorMemoryAllocation ? -2 : -3;
+}
+
+static void drop_graphs(BatchEngine* e) {
+  for (cudaGraphExec_t& x : e->execs)
+    if (x) cudaGraphExecDestroy(x);
+  e->execs.clear();
 }
 
 static int grow_desc(BatchEngine* e, int n) {
@@ -138,21 +146,22 @@ static int grow_desc(BatchEngine* e, int n) {
   cudaDeviceSynchronize();  // the old descriptor block may still be read by a running batch
   cudaFree(e->d_desc);
   cudaFreeHost(e->h_desc);
+  cudaFree(e->d_counters);
   e->d_desc = nullptr;
   e->h_desc = nullptr;
+  e->d_counters = nullptr;
   e->desc_bytes = desc_size(cap);
   cudaError_t c = cudaMalloc(&e->d_desc, e->desc_bytes);
   if (c == cudaSuccess) c = cudaMallocHost(&e->h_desc, e->desc_bytes);
+  if (c == cudaSuccess)
+    c = cudaMalloc(&e->d_counters, (size_t)cap * kCountersPerGroup * sizeof(unsigned));
   if (c != cudaSuccess) {
     e->cap_pairs = 0;
     return set_err(e, c, "descriptor allocation");
   }
   e->cap_pairs = cap;
   e->copy_pending = false;
-  if (e->exec) {  // the graph holds the old descriptor addresses
-    cudaGraphExecDestroy(e->exec);
-    e->exec = nullptr;
-  }
+  drop_graphs(e);  // the graphs hold the old descriptor addresses
   return 0;
 }
 
@@ -163,14 +172,22 @@ int batch_reserve(BatchEngine** pe, size_t scratch_bytes, int n) {
     e->err[0] = 0;
     memset(&e->graph_method, 0, sizeof(Method));
     *pe = e;
-    cudaError_t c = cudaMalloc(&e->d_counters, 64);
-    if (c == cudaSuccess) c = cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking);
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    cudaError_t c = cudaSuccess;
+    for (int k = 0; k < kSlots && c == cudaSuccess; k++) {
+      c = cudaStreamCreateWithFlags(&e->main[k], cudaStreamNonBlocking);
+      if (c == cudaSuccess) c = cudaStreamCreateWithPriority(&e->aux[k], cudaStreamNonBlocking, hi);
+      if (c == cudaSuccess) c = cudaEventCreateWithFlags(&e->ev_fork[k], cudaEventDisableTiming);
+      if (c == cudaSuccess) c = cudaEventCreateWithFlags(&e->ev_join[k], cudaEventDisableTiming);
+    }
+    if (c == cudaSuccess) c = cudaEventCreateWithFlags(&e->ev_start, cudaEventDisableTiming);
+    if (c == cudaSuccess) c = cudaEventCreateWithFlags(&e->ev_end, cudaEventDisableTiming);
     if (c == cudaSuccess) c = cudaEventCreateWithFlags(&e->copied, cudaEventDisableTiming);
-    if (c == cudaSuccess) c = fork_create(&e->fork);
     if (c != cudaSuccess) return set_err(e, c, "batch engine setup");
   }
   BatchEngine* e = *pe;
-  if (!e->d_counters || !e->fork.aux)
+  if (!e->main[0] || !e->copied)
     return set_err(e, cudaErrorInitializationError, "batch engine setup");
   if (scratch_bytes > e->scratch_cap) {
     // the previous batch may still run on its stream: wait before freeing its scratch
@@ -220,10 +237,16 @@ BatchTune batch_get_tune(BatchEngine* e, int bucket) {
 
 void batch_destroy(BatchEngine* e) {
   if (!e) return;
-  if (e->exec) cudaGraphExecDestroy(e->exec);
+  drop_graphs(e);
   if (e->copied) cudaEventDestroy(e->copied);
-  if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
-  fork_destroy(&e->fork);
+  for (int k = 0; k < kSlots; k++) {
+    if (e->main[k]) cudaStreamDestroy(e->main[k]);
+    if (e->aux[k]) cudaStreamDestroy(e->aux[k]);
+    if (e->ev_fork[k]) cudaEventDestroy(e->ev_fork[k]);
+    if (e->ev_join[k]) cudaEventDestroy(e->ev_join[k]);
+  }
+  if (e->ev_start) cudaEventDestroy(e->ev_start);
+  if (e->ev_end) cudaEventDestroy(e->ev_end);
   cudaFree(e->scratch);
   cudaFree(e->d_desc);
   cudaFreeHost(e->h_desc);
@@ -241,8 +264,11 @@ static int persistent_grid(K kernel, size_t smem) {
   return sms * per_sm;
 }
 
+// Records the graph for G groups: the descriptor upload and the counter reset on main[0], then
+// group g's six stage kernels on slot g % kSlots (its aggregation kernels forked onto the slot's
+// aux stream), and the join of every stream back into main[0].
 template <bool WIDE>
-static int capture_t(BatchEngine* e, const Method& mt, int wta_smem, int warp_smem) {
+static int capture_t(BatchEngine* e, const Method& mt, int wta_smem, int warp_smem, int G) {
   const int cap = e->cap_pairs;
   const BatchHeader* hd = reinterpret_cast<const BatchHeader*>(e->d_desc);
   const Problem* probs = reinterpret_cast<const Problem*>(e->d_desc + probs_offset());
@@ -252,6 +278,7 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem, int warp_sm
   const int* lpre = reinterpret_cast<const int*>(e->d_desc + seg_prefix_offset(cap, 0));
   const AggSeg* bsegs = reinterpret_cast<const AggSeg*>(e->d_desc + segs_offset(cap, 1));
   const int* bpre = reinterpret_cast<const int*>(e->d_desc + seg_prefix_offset(cap, 1));
+  const GroupDesc* groups = reinterpret_cast<const GroupDesc*>(e->d_desc + groups_offset(cap));
   // launch shapes and attributes are settled before the capture starts
   cudaFuncSetAttribute(batch_wta_kernel<WIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        wta_smem);
@@ -267,68 +294,87 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem, int warp_sm
   const int g_med = persistent_grid(batch_median_kernel, 0);
   cudaError_t c = cudaGetLastError();
   if (c != cudaSuccess) return set_err(e, c, "kernel attributes");
-  cudaStream_t cs = e->cap_stream;
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaStream_t cs = e->main[0];
   cudaGraph_t g = nullptr;
   c = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (c != cudaSuccess) return set_err(e, c, "begin capture");
   cudaMemcpyAsync(e->d_desc, e->h_desc, e->desc_bytes, cudaMemcpyHostToDevice, cs);
   // an external record node, so the host can wait for the upload of each replay
   cudaEventRecordWithFlags(e->copied, cs, cudaEventRecordExternal);
-  cudaMemsetAsync(e->d_counters, 0, 64, cs);
-  batch_census_kernel<<<g_census, 256, 0, cs>>>(hd, probs, prefix + 3 * stride, mt, e->d_counters);
-  batch_cost_kernel<<<g_cost, 256, 0, cs>>>(hd, probs, prefix + 0 * stride, mt, e->d_counters);
-  cudaEventRecord(e->fork.fork, cs);
-  cudaStreamWaitEvent(e->fork.aux, e->fork.fork, 0);
-  {
-    int nseg = cap;
-    Method m = mt;
-    unsigned* counters = e->d_counters;
-    int wsm = warp_smem;
-    void* rargs[] = {(void*)&hd, (void*)&probs, (void*)&lsegs, (void*)&lpre, (void*)&nseg,
-                     (void*)&m, (void*)&counters, (void*)&wsm};
-    void* sargs[] = {(void*)&hd, (void*)&probs, (void*)&bsegs, (void*)&bpre, (void*)&nseg,
-                     (void*)&m, (void*)&counters, (void*)&wsm};
-    // the row kernel holds the batch's longest chains: its node keeps the highest priority so
-    // its blocks are dispatched ahead of the sheared kernel's
-    int lo = 0, hi = 0;
-    cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributePriority;
-    attr[0].val.priority = hi;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(g_rows);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = e->fork.aux;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelExC(&cfg, k_rows, rargs);
-    cudaLaunchKernel(k_shear, dim3(g_shear), dim3(256), sargs, shear_smem, cs);
+  cudaMemsetAsync(e->d_counters, 0, (size_t)G * kCountersPerGroup * sizeof(unsigned), cs);
+  cudaEventRecord(e->ev_start, cs);
+  for (int k = 1; k < kSlots; k++) cudaStreamWaitEvent(e->main[k], e->ev_start, 0);
+  for (int gi = 0; gi < G; gi++) {
+    const int sl = gi % kSlots;
+    cudaStream_t m = e->main[sl], a = e->aux[sl];
+    const GroupDesc* gd = groups + gi;
+    unsigned* cnt = e->d_counters + (size_t)gi * kCountersPerGroup;
+    batch_census_kernel<<<g_census, 256, 0, m>>>(gd, probs, prefix + 3 * stride, mt, cnt);
+    batch_cost_kernel<<<g_cost, 256, 0, m>>>(gd, probs, prefix + 0 * stride, mt, cnt);
+    cudaEventRecord(e->ev_fork[sl], m);
+    cudaStreamWaitEvent(a, e->ev_fork[sl], 0);
+    {
+      Method mm = mt;
+      int wsm = warp_smem;
+      void* rargs[] = {(void*)&hd, (void*)&gd, (void*)&probs, (void*)&lsegs, (void*)&lpre,
+                       (void*)&mm, (void*)&cnt, (void*)&wsm};
+      void* sargs[] = {(void*)&hd, (void*)&gd, (void*)&probs, (void*)&bsegs, (void*)&bpre,
+                       (void*)&mm, (void*)&cnt, (void*)&wsm};
+      // the row kernel holds the group's longest chains: its node keeps the highest priority so
+      // its blocks are dispatched ahead of the sheared kernel's
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributePriority;
+      attr[0].val.priority = hi;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(g_rows);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = a;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelExC(&cfg, k_rows, rargs);
+      cudaLaunchKernel(k_shear, dim3(g_shear), dim3(256), sargs, shear_smem, m);
+    }
+    cudaEventRecord(e->ev_join[sl], a);
+    cudaStreamWaitEvent(m, e->ev_join[sl], 0);
+    batch_wta_kernel<WIDE><<<g_wta, 256, wta_smem, m>>>(hd, gd, probs, prefix + 1 * stride, cnt);
+    batch_median_kernel<<<g_med, 256, 0, m>>>(gd, probs, prefix + 2 * stride, mt, cnt);
   }
-  cudaEventRecord(e->fork.join, e->fork.aux);
-  cudaStreamWaitEvent(cs, e->fork.join, 0);
-  batch_wta_kernel<WIDE><<<g_wta, 256, wta_smem, cs>>>(hd, probs, prefix + 1 * stride,
-                                                       e->d_counters);
-  batch_median_kernel<<<g_med, 256, 0, cs>>>(hd, probs, prefix + 2 * stride, mt, e->d_counters);
+  for (int k = 1; k < kSlots; k++) {
+    cudaEventRecord(e->ev_end, e->main[k]);
+    cudaStreamWaitEvent(cs, e->ev_end, 0);
+  }
   c = cudaStreamEndCapture(cs, &g);
   if (c != cudaSuccess) return set_err(e, c, "end capture");
-  c = cudaGraphInstantiate(&e->exec, g, 0);
+  cudaGraphExec_t x = nullptr;
+  c = cudaGraphInstantiate(&x, g, 0);
   cudaGraphDestroy(g);
   if (c != cudaSuccess) return set_err(e, c, "graph instantiate");
-  e->graph_method = mt;
-  e->graph_wta_smem = wta_smem;
-  e->graph_shear_smem = warp_smem;
-  e->graph_launches = 6;
+  if ((int)e->execs.size() <= G) e->execs.resize((size_t)G + 1, nullptr);
+  e->execs[(size_t)G] = x;
   return 0;
 }
 
-static int capture(BatchEngine* e, const Method& mt, int wta_smem, int warp_smem) {
-  if (e->exec) {
-    cudaGraphExecDestroy(e->exec);
-    e->exec = nullptr;
+// The graph for G groups, captured when missing; every cached graph is dropped first when the
+// method or a shared-memory size changes.
+static int graph_for(BatchEngine* e, const Method& mt, int wta_smem, int warp_smem, int G,
+                     cudaGraphExec_t* out) {
+  if (memcmp(&e->graph_method, &mt, sizeof(Method)) != 0 || wta_smem > e->graph_wta_smem ||
+      warp_smem > e->graph_shear_smem) {
+    drop_graphs(e);
+    e->graph_method = mt;
+    e->graph_wta_smem = std::max(wta_smem, e->graph_wta_smem);
+    e->graph_shear_smem = std::max(warp_smem, e->graph_shear_smem);
   }
-  return mt.wide ? capture_t<true>(e, mt, wta_smem, warp_smem)
-                 : capture_t<false>(e, mt, wta_smem, warp_smem);
+  if ((int)e->execs.size() <= G || !e->execs[(size_t)G]) {
+    const int rc = mt.wide ? capture_t<true>(e, mt, e->graph_wta_smem, e->graph_shear_smem, G)
+                           : capture_t<false>(e, mt, e->graph_wta_smem, e->graph_shear_smem, G);
+    if (rc) return rc;
+  }
+  *out = e->execs[(size_t)G];
+  return 0;
 }
 
 struct Keyed {
@@ -336,17 +382,16 @@ struct Keyed {
   int len;
 };
 
-// Writes one queue's segments, sorted by their chain length, and its prefix table.
-static int write_queue(std::vector<Keyed>& kv, AggSeg* segs, int* pre, int cap) {
+// Writes one group's queue segments at segs[0 .. k), sorted by their chain length, with item
+// prefixes continuing from base; returns the queue's item count after the group.
+static int write_queue(std::vector<Keyed>& kv, AggSeg* segs, int* pre, int base) {
   std::stable_sort(kv.begin(), kv.end(), [](const Keyed& a, const Keyed& b) { return a.len > b.len; });
-  int items = 0;
-  const int n = (int)kv.size();
-  for (int i = 0; i < n; i++) {
+  int items = base;
+  for (size_t i = 0; i < kv.size(); i++) {
     segs[i] = kv[i].s;
     pre[i] = items;
     items += (kv[i].s.end - kv[i].s.begin + kv[i].s.group - 1) / kv[i].s.group;
   }
-  for (int i = n; i <= cap; i++) pre[i] = items;  // padding slots never match an item
   return items;
 }
 
@@ -361,41 +406,84 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
     if (c != cudaSuccess) return set_err(e, c, "descriptor upload wait");
     e->copy_pending = false;
   }
+  const size_t bpe = mt.wide ? 4 : 2;
+  // pairs by footprint, largest first, then cut into groups
+  std::vector<int> order((size_t)n);
+  std::iota(order.begin(), order.end(), 0);
+  auto fp = [&](int p) { return (size_t)probs[p].W * probs[p].H * probs[p].D * (1 + bpe); };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return fp(a) > fp(b); });
+  std::vector<int> gstart;
+  for (int i = 0; i < n;) {
+    gstart.push_back(i);
+    size_t bytes = fp(order[i]);
+    int k = 1;
+    i++;
+    while (i < n && k < kGroupMaxPairs && bytes + fp(order[i]) <= kGroupBytes) {
+      bytes += fp(order[i]);
+      k++;
+      i++;
+    }
+  }
+  const int G = (int)gstart.size();
+  gstart.push_back(n);
+
   BatchHeader* hd = reinterpret_cast<BatchHeader*>(e->h_desc);
   memset(hd, 0, sizeof(BatchHeader));
   Problem* hp = reinterpret_cast<Problem*>(e->h_desc + probs_offset());
   int* prefix = reinterpret_cast<int*>(e->h_desc + prefix_offset(cap));
+  AggSeg* lsegs = reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 0));
+  int* lpre = reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 0));
+  AggSeg* bsegs = reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 1));
+  int* bpre = reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 1));
+  GroupDesc* groups = reinterpret_cast<GroupDesc*>(e->h_desc + groups_offset(cap));
   const int stride = cap + 1;
   int tot[4] = {0, 0, 0, 0};
-  int wta_smem = 0, warp_smem = 0;
-  std::vector<Keyed> lk, bk;
-  lk.reserve(n);
-  bk.reserve(n);
-  for (int p = 0; p < n; p++) {
-    const Problem& pb = probs[p];
-    const BatchTune& tn = e->tune[tune_bucket(pb.W, pb.H, pb.D)];
-    hp[p] = pb;
-    prefix[0 * stride + p] = tot[0];
-    prefix[1 * stride + p] = tot[1];
-    prefix[2 * stride + p] = tot[2];
-    prefix[3 * stride + p] = tot[3];
-    tot[0] += cost_items(pb.W, pb.H);
-    tot[3] += 2 * census_items(pb.W, pb.H);
-    const int wt = wta_staged_px(pb.D, mt.wide != 0, tn.wta_px);
-    tot[1] += wta_items(pb.W, pb.H, wt);
-    tot[2] += median_items(pb.W, pb.H);
-    wta_smem = std::max(wta_smem, (int)wta_staged_smem_bytes(pb.D, mt.wide != 0, wt));
-    warp_smem = std::max(warp_smem, shear_smem_bytes(tn.shear_dpl, mt.wide != 0, tn.shear_cpl));
-    lk.push_back(Keyed{AggSeg{p, 0, row_units(pb.H, true), 32 / long_lanes(pb.D, tn.row_dpl)},
-                       pb.W});
-    bk.push_back(Keyed{AggSeg{p, 0, shear_items(pb.W, pb.D, tn.shear_dpl, mt.num_paths,
-                                                tn.shear_cpl), 1}, pb.H});
+  int wta_smem = 0, warp_smem = 0, nrows = 0, nshear = 0;
+  for (int gi = 0; gi < G; gi++) {
+    const int p0 = gstart[gi], p1 = gstart[gi + 1];
+    GroupDesc& gd = groups[gi];
+    memset(&gd, 0, sizeof(gd));
+    gd.p0 = p0;
+    gd.np = p1 - p0;
+    gd.lo[kStCost] = tot[0];
+    gd.lo[kStWta] = tot[1];
+    gd.lo[kStMedian] = tot[2];
+    gd.lo[kStCensus] = tot[3];
+    std::vector<Keyed> lk, bk;
+    for (int i = p0; i < p1; i++) {
+      const Problem& pb = probs[order[i]];
+      const BatchTune& tn = e->tune[tune_bucket(pb.W, pb.H, pb.D)];
+      hp[i] = pb;
+      prefix[0 * stride + i] = tot[0];
+      prefix[1 * stride + i] = tot[1];
+      prefix[2 * stride + i] = tot[2];
+      prefix[3 * stride + i] = tot[3];
+      tot[0] += cost_items(pb.W, pb.H);
+      const int wt = wta_staged_px(pb.D, mt.wide != 0, tn.wta_px);
+      tot[1] += wta_items(pb.W, pb.H, wt);
+      tot[2] += median_items(pb.W, pb.H);
+      tot[3] += 2 * census_items(pb.W, pb.H);
+      wta_smem = std::max(wta_smem, (int)wta_staged_smem_bytes(pb.D, mt.wide != 0, wt));
+      warp_smem = std::max(warp_smem, shear_smem_bytes(tn.shear_dpl, mt.wide != 0, tn.shear_cpl));
+      lk.push_back(Keyed{AggSeg{i, 0, row_units(pb.H, true), 32 / long_lanes(pb.D, tn.row_dpl)},
+                         pb.W});
+      bk.push_back(Keyed{AggSeg{i, 0, shear_items(pb.W, pb.D, tn.shear_dpl, mt.num_paths,
+                                                  tn.shear_cpl), 1}, pb.H});
+    }
+    gd.hi[kStCost] = tot[0];
+    gd.hi[kStWta] = tot[1];
+    gd.hi[kStMedian] = tot[2];
+    gd.hi[kStCensus] = tot[3];
+    gd.lo[kStRows] = nrows;
+    nrows = write_queue(lk, lsegs + p0, lpre + p0, nrows);
+    gd.hi[kStRows] = nrows;
+    gd.lo[kStShear] = nshear;
+    nshear = write_queue(bk, bsegs + p0, bpre + p0, nshear);
+    gd.hi[kStShear] = nshear;
   }
   for (int k = 0; k < 4; k++) prefix[k * stride + n] = tot[k];
-  const int nrows = write_queue(lk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 0)),
-                                reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 0)), cap);
-  const int nshear = write_queue(bk, reinterpret_cast<AggSeg*>(e->h_desc + segs_offset(cap, 1)),
-                                reinterpret_cast<int*>(e->h_desc + seg_prefix_offset(cap, 1)), cap);
+  lpre[n] = nrows;
+  bpre[n] = nshear;
   hd->n = n;
   hd->total[kStCost] = tot[0];
   hd->total[kStRows] = nrows;
@@ -404,16 +492,13 @@ int batch_run(BatchEngine* e, const Problem* probs, int n, const Method& mt, cud
   hd->total[kStMedian] = tot[2];
   hd->total[kStCensus] = tot[3];
   memcpy(hd->tune, e->tune, sizeof(hd->tune));
-  if (!e->exec || memcmp(&e->graph_method, &mt, sizeof(Method)) != 0 ||
-      wta_smem > e->graph_wta_smem || warp_smem > e->graph_shear_smem) {
-    rc = capture(e, mt, std::max(wta_smem, e->graph_wta_smem),
-                 std::max(warp_smem, e->graph_shear_smem));
-    if (rc) return rc;
-  }
-  cudaError_t c = cudaGraphLaunch(e->exec, s);
+  cudaGraphExec_t exec = nullptr;
+  rc = graph_for(e, mt, wta_smem, warp_smem, G, &exec);
+  if (rc) return rc;
+  cudaError_t c = cudaGraphLaunch(exec, s);
   if (c != cudaSuccess) return set_err(e, c, "graph launch");
   e->copy_pending = true;
-  if (launches) *launches = e->graph_launches;
+  if (launches) *launches = 6 * G;
   return 0;
 }
 

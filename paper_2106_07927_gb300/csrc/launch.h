@@ -37,10 +37,10 @@ cudaError_t launch_rows(const Problem& pb, const Method& mt, const Tuning& tn, c
 template <bool WIDE>
 cudaError_t launch_shear(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s);
 // Persistent batch variants of the two kernels, as handles for cudaLaunchKernel. Parameters:
-// (const BatchHeader*, const Problem*, const AggSeg* segs, const int* seg_prefix, int nseg,
-// Method, unsigned* counters, int warp_smem); 256 threads; the sheared one takes 8 warp_smem
-// bytes of dynamic shared memory (warp_smem: the largest shear_smem_bytes of the batch's
-// settings).
+// (const BatchHeader*, const GroupDesc*, const Problem*, const AggSeg* segs,
+// const int* seg_prefix, Method, unsigned* counters, int warp_smem); 256 threads; the sheared
+// one takes 8 warp_smem bytes of dynamic shared memory (warp_smem: the largest shear_smem_bytes
+// of the batch's settings).
 template <bool WIDE>
 const void* batch_row_kernel_fn();
 template <bool WIDE>
