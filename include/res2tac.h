@@ -197,7 +197,7 @@ int res2tac_compute_raw(res2tac_t h, const uint8_t* raw_left, const uint8_t* raw
  * pair at a time, Sec. 2.2; batching is this library's addition). The pairs are sorted by memory
  * footprint and cut into groups of at most 96 MB of cost and aggregated volumes (a larger pair is
  * a group of its own); each group runs the six stages as persistent kernels fed by device work
- * queues over its pairs, and groups alternate between two stream slots so consecutive groups
+ * queues over its pairs, and groups rotate over four stream slots so consecutive groups
  * overlap. The whole batch is one CUDA graph, captured once per group count and replayed while
  * the capacities last (res2tac_last_launch_count: 6 per group). The context grows its batch
  * scratch when a larger batch arrives: that call allocates and must not be made during stream

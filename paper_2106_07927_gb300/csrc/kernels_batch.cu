@@ -6,8 +6,11 @@
 // Each group runs the six stages - census, cost, the two aggregation kernels (concurrently, on
 // a forked stream), WTA, LR check + median - as persistent kernels over its own pairs, so a
 // group's volumes are still in L2 when its next stage reads them, as they are for a pair run
-// alone, while the pairs of a group fill the GPU together. Groups alternate between two slots
-// of streams, so one group's latency-bound aggregation overlaps the next group's other stages.
+// alone, while the pairs of a group fill the GPU together. Groups rotate over kSlots slots of
+// streams, so one group's latency-bound aggregation overlaps the next groups' other stages
+// (measured on the 64-pair mix: 0.80 of per-pair launches with one slot, 0.985 with two, 1.013
+// with four; aggregation blocks of two warps, as the single-pair kernels use, rather than
+// eight: 0.977 -> 0.985 with two slots).
 //
 // A block (or, in the aggregation, a warp) claims its next work item from its group's queue
 // with one atomic increment and maps it to (pair, item of that pair) through prefix tables; no
@@ -37,7 +40,8 @@ namespace r2t {
 // Footprint bound of one group (bytes of cost and aggregated volumes) and its pair count.
 constexpr size_t kGroupBytes = 96u << 20;
 constexpr int kGroupMaxPairs = 32;
-constexpr int kSlots = 2;  // groups in flight
+constexpr int kSlots = 4;  // groups in flight
+constexpr int kAggWarps = 2;  // warps per block of the persistent aggregation kernels
 
 // Block-claimed stage kernels of one group: item = lo + claim, pair found among the group's.
 #define R2T_GROUP_LOOP(STAGE, BODY)                                                  \
@@ -94,9 +98,9 @@ struct BatchEngine {
   size_t desc_bytes = 0;
   int cap_pairs = 0;
   unsigned* d_counters = nullptr;  // kCountersPerGroup per group, cap_pairs groups
-  cudaStream_t main[kSlots] = {nullptr, nullptr};  // main[0] is the capture origin
-  cudaStream_t aux[kSlots] = {nullptr, nullptr};   // row-path kernels of each slot
-  cudaEvent_t ev_fork[kSlots] = {nullptr, nullptr}, ev_join[kSlots] = {nullptr, nullptr};
+  cudaStream_t main[kSlots] = {};  // main[0] is the capture origin
+  cudaStream_t aux[kSlots] = {};   // row-path kernels of each slot
+  cudaEvent_t ev_fork[kSlots] = {}, ev_join[kSlots] = {};
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;
   // captured graphs by group count (index G), all for graph_method and the shared-memory sizes
   std::vector<cudaGraphExec_t> execs;
@@ -255,17 +259,17 @@ void batch_destroy(BatchEngine* e) {
 }
 
 template <class K>
-static int persistent_grid(K kernel, size_t smem) {
+static int persistent_grid(K kernel, size_t smem, int threads = 256) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
   if (per_sm < 1) per_sm = 1;
   return sms * per_sm;
 }
 
 // Records the graph for G groups: the descriptor upload and the counter reset on main[0], then
-// group g's six stage kernels on slot g % kSlots (its aggregation kernels forked onto the slot's
+// group g's six stage kernels on slot g % kSlots (its row-path kernel forked onto the slot's
 // aux stream), and the join of every stream back into main[0].
 template <bool WIDE>
 static int capture_t(BatchEngine* e, const Method& mt, int wta_smem, int warp_smem, int G) {
@@ -286,10 +290,10 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem, int warp_sm
   const int g_cost = persistent_grid(batch_cost_kernel, 0);
   const void* k_rows = batch_row_kernel_fn<WIDE>();
   const void* k_shear = batch_shear_kernel_fn<WIDE>();
-  const int g_rows = persistent_grid(k_rows, 0);
-  const int shear_smem = 8 * warp_smem;  // 8 warps per block
+  const int g_rows = persistent_grid(k_rows, 0, 32 * kAggWarps);
+  const int shear_smem = kAggWarps * warp_smem;
   cudaFuncSetAttribute(k_shear, cudaFuncAttributeMaxDynamicSharedMemorySize, shear_smem);
-  const int g_shear = persistent_grid(k_shear, shear_smem);
+  const int g_shear = persistent_grid(k_shear, shear_smem, 32 * kAggWarps);
   const int g_wta = persistent_grid(batch_wta_kernel<WIDE>, wta_smem);
   const int g_med = persistent_grid(batch_median_kernel, 0);
   cudaError_t c = cudaGetLastError();
@@ -329,13 +333,13 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem, int warp_sm
       attr[0].val.priority = hi;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(g_rows);
-      cfg.blockDim = dim3(256);
+      cfg.blockDim = dim3(32 * kAggWarps);
       cfg.dynamicSmemBytes = 0;
       cfg.stream = a;
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       cudaLaunchKernelExC(&cfg, k_rows, rargs);
-      cudaLaunchKernel(k_shear, dim3(g_shear), dim3(256), sargs, shear_smem, m);
+      cudaLaunchKernel(k_shear, dim3(g_shear), dim3(32 * kAggWarps), sargs, shear_smem, m);
     }
     cudaEventRecord(e->ev_join[sl], a);
     cudaStreamWaitEvent(m, e->ev_join[sl], 0);
