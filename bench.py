@@ -52,7 +52,24 @@ def _args():
     ap.add_argument("--serve-rates", default="200,500,1000,2000,5000")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--pair", type=int, nargs=3, metavar=("W", "H", "D"), default=None,
+                    help="time a seeded road-like pair of this size instead of the 1242x375 "
+                         "workload (9x7, 8 paths, LR + median; for profiling larger pairs)")
     return ap.parse_args()
+
+
+def _workload_pair(args, seed):
+    """(left, right, params, name) of the timed workload: the 1242x375 D=128 pair, or with
+    --pair a seeded road-like scene of the given size with the same method settings."""
+    from paper_2106_07927_gb300 import scenes
+    if args.pair is None:
+        left, right, _, prm = scenes.single_pair(WORKLOAD, seed)
+        return left, right, prm, WORKLOAD
+    W, H, D = args.pair
+    left, right, _ = scenes.make_scene("road", 3 + seed, W, H, D)
+    return (left, right, scenes.params(W, H, D, 9, 7, 10, 120, 8,
+                                        scenes.FLAG_LR_CHECK | scenes.FLAG_MEDIAN),
+            f"{W}x{H}_d{D}_ct9x7_r8")
 
 
 def _traffic(tuning):
@@ -268,7 +285,7 @@ def main():
         replicas.barrier()
         torch.cuda.synchronize()
 
-    left, right, _, prm = scenes.single_pair(WORKLOAD, 0)
+    left, right, prm, workload = _workload_pair(args, 0)
     W, H, D = prm["width"], prm["height"], prm["max_disp"]
     de = W * H * D
     stream = torch.cuda.current_stream()
@@ -282,6 +299,7 @@ def main():
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
 
     int_peak = binding.res2tac_probe_int_peak(2000, sh)  # lane-ops/s, packed u16 min + add
+    popc_rate = binding.res2tac_probe_popc_rate(2000, sh)  # 32-bit POPC per second
     # bytes/s of TMA bulk add-reductions into a buffer the size of the aggregated volume
     red_peak = binding.res2tac_probe_red_peak(2 * W * H * D, 16, sh)
 
@@ -412,7 +430,7 @@ def main():
         # res2tac_compute).
         e2e_pairs = []
         for sd in range(4):
-            l_, r_, _, _ = scenes.single_pair(WORKLOAD, sd)
+            l_, r_, _, _ = _workload_pair(args, sd)
             e2e_pairs.append((torch.from_numpy(l_).pin_memory(), torch.from_numpy(r_).pin_memory(),
                               torch.empty((H, W), dtype=torch.int16).pin_memory()))
         dL = torch.empty((H, W), dtype=torch.uint8, device="cuda")
@@ -566,7 +584,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u8/u16 (integer)", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "W": W, "H": H, "D": D, "census": "9x7", "paths": 8,
+        "config": {"workload": workload, "W": W, "H": H, "D": D, "census": "9x7", "paths": 8,
                    "P1": 10, "P2": 120, "post": "LR check (1 px) + 3x3 median",
                    "l2": "flushed between steps (256 MB write outside the step events)",
                    "parallelism": f"replicas x{ws}"},
@@ -583,7 +601,8 @@ def main():
                      "peak_source": "measured packed-u16 min+add probe on this GPU",
                      "hbm_achieved_gbs": round(bytes_agg / (agg_ms / 1e3) / 1e9, 1),
                      "hbm_peak_gbs": hbm,
-                     "traffic": _traffic(binding.res2tac_get_tuning(ctx.handle)),
+                     "traffic": (_traffic(binding.res2tac_get_tuning(ctx.handle))
+                                 if args.pair is None else None),
                      "ops_per_launch": ops_agg, "algorithmic_bytes_per_launch": bytes_agg,
                      "dominant_stage": dominant,
                      # the accumulation into S: every path adds 2 bytes per DE (read-modify-write
@@ -594,6 +613,14 @@ def main():
                          "peak_gbs": round(red_peak / 1e9, 1),
                          "frac": round(2 * de * prm["num_paths"] / (agg_ms / 1e3) / red_peak, 3),
                          "peak_source": "measured TMA bulk add-reduction probe, S-sized buffer"}},
+        # recomputing the cost inside each path walk instead of reading the volume: two 32-bit
+        # POPC per DE and path at the measured POPC rate, against the aggregation's own time
+        "cost_recompute_bound": {
+            "popc_per_s": round(popc_rate, 0),
+            "popc_per_step": 2 * prm["num_paths"] * de,
+            "popc_us_per_step": round(2 * prm["num_paths"] * de / popc_rate * 1e6, 1),
+            "aggregate_us_per_step": round(agg_ms * 1e3, 1),
+            "cost_bytes_read_per_step": prm["num_paths"] * de},
         "e2e": {"value": round(ws * de * args.steps / e2e_s / 1e6, 1), "unit": "MDE/s",
                 "h2d_bytes_per_step": 2 * W * H, "d2h_bytes_per_step": 2 * W * H,
                 "ms_per_step": round(1e3 * e2e_s / args.steps, 4), "matches_device_path": e2e_ok,
@@ -610,7 +637,7 @@ def main():
         "clocks": clocks,
         "wall_s_timed_plain": round(t_wall, 3),
     }
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and args.pair is None:
         t = [_oracle_band(left, right, prm, H) for _ in range(3)]
         model, ncpu = _cpu_info()
         result["cpu_baseline"] = {

@@ -29,6 +29,12 @@ int res2tac_probe_int_peak(int iters, res2tac_stream_t s, double* lane_ops_per_s
  * *bytes_per_s. Synchronises s. RES2TAC_ENOMEM if the buffer does not fit. */
 int res2tac_probe_red_peak(int64_t bytes, int32_t passes, res2tac_stream_t s, double* bytes_per_s);
 
+/* POPC-throughput probe (measurement aid): independent chains of 32-bit population counts on
+ * every SM for about `iters` iterations on stream s; returns the sustained rate in POPC per second
+ * through *popc_per_s (the bound on recomputing the census cost inside the aggregation, which
+ * needs two per disparity estimate and path). Synchronises s. */
+int res2tac_probe_popc_rate(int iters, res2tac_stream_t s, double* popc_per_s);
+
 /* Range checks of the debug build. libres2tac_check.so is the same library compiled with
  * RES2TAC_CHECK_BOUNDS: before each global access of the path-aggregation and WTA kernels it
  * tests that the bytes lie inside their buffer (the cost volume, the aggregated volume, D^L),

@@ -37,7 +37,8 @@ EXPORTS = (
     "res2tac_set_batch_tuning", "res2tac_get_batch_tuning", "res2tac_autotune_batch",
 )
 # Every symbol include/res2tac_measure.h declares (measurement aids of the benchmark).
-MEASURE_EXPORTS = ("res2tac_probe_int_peak", "res2tac_probe_red_peak", "res2tac_bounds_status")
+MEASURE_EXPORTS = ("res2tac_probe_int_peak", "res2tac_probe_red_peak", "res2tac_probe_popc_rate",
+                   "res2tac_bounds_status")
 RES2TAC_STATIC_SCRATCH_BYTES = 80 << 20
 STAGES = ("census_cost", "aggregate", "wta_dr", "lr_median")
 
@@ -124,6 +125,8 @@ def load(path: str | None = None):
         "res2tac_set_rectification": (ctypes.c_int, [P, P, P, P, P, I64, I32, I32, P]),
         "res2tac_compute_raw": (ctypes.c_int, [P, P, P, I64, P, I64, P]),
         "res2tac_set_batch_tuning": (ctypes.c_int, [P, ctypes.POINTER(res2tac_batch_tuning), I32]),
+        "res2tac_probe_popc_rate": (ctypes.c_int, [ctypes.c_int, P,
+                                                   ctypes.POINTER(ctypes.c_double)]),
         "res2tac_bounds_status": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I32),
                                                  ctypes.POINTER(I64)]),
         "res2tac_get_batch_tuning": (ctypes.c_int, [P, ctypes.POINTER(res2tac_batch_tuning)]),
@@ -313,6 +316,12 @@ def res2tac_probe_red_peak(nbytes: int, passes: int = 16, stream: int = 0) -> fl
 def res2tac_probe_int_peak(iters: int = 20000, stream: int = 0) -> float:
     v = ctypes.c_double()
     _check(load().res2tac_probe_int_peak(iters, stream, ctypes.byref(v)))
+    return v.value
+
+
+def res2tac_probe_popc_rate(iters: int = 20000, stream: int = 0) -> float:
+    v = ctypes.c_double()
+    _check(load().res2tac_probe_popc_rate(iters, stream, ctypes.byref(v)))
     return v.value
 
 

@@ -99,6 +99,7 @@ struct res2tac_ctx {
   r2t::Fork fork;     // second stream for the concurrent aggregation kernels
 };
 
+
 extern "C" {
 
 const char* res2tac_strerror(int code) {
@@ -496,6 +497,13 @@ int res2tac_probe_red_peak(int64_t bytes, int32_t passes, res2tac_stream_t s, do
   if (bytes < 1024 || passes < 1 || !bytes_per_s) return fail(RES2TAC_EINVAL, "bad probe arguments");
   cudaError_t e = r2t::probe_red_peak(bytes, passes, (cudaStream_t)s, bytes_per_s);
   if (e != cudaSuccess) return fail_cuda(e, "res2tac_probe_red_peak");
+  return RES2TAC_OK;
+}
+
+int res2tac_probe_popc_rate(int iters, res2tac_stream_t s, double* popc_per_s) {
+  if (iters < 1 || !popc_per_s) return fail(RES2TAC_EINVAL, "bad probe arguments");
+  cudaError_t e = r2t::probe_popc_rate(iters, (cudaStream_t)s, popc_per_s);
+  if (e != cudaSuccess) return fail_cuda(e, "res2tac_probe_popc_rate");
   return RES2TAC_OK;
 }
 

@@ -273,6 +273,49 @@ cudaError_t probe_int_peak(int iters, cudaStream_t s, double* lane_ops_per_s) {
   return cudaStreamSynchronize(s);
 }
 
+// Independent chains of 32-bit POPC (each fed by an XOR and an integer multiply-add), 16 per
+// thread: the rate at which the cost could be recomputed from census descriptors.
+__global__ void __launch_bounds__(256) popc_probe_kernel(uint32_t* sink, int iters, uint32_t seed) {
+  uint32_t a[16];
+#pragma unroll
+  for (int k = 0; k < 16; k++) a[k] = seed * (threadIdx.x + 7 * k + 1);
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int k = 0; k < 16; k++) a[k] = __popc(a[k] ^ (uint32_t)i) + a[k] * 3u;
+  }
+  uint32_t r = 0;
+#pragma unroll
+  for (int k = 0; k < 16; k++) r ^= a[k];
+  if (r == 0x12345678u) sink[blockIdx.x] = r;
+}
+
+cudaError_t probe_popc_rate(int iters, cudaStream_t s, double* popc_per_s) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, popc_probe_kernel, 256, 0);
+  const int grid = sms * (per_sm > 0 ? per_sm : 1);
+  uint32_t* sink = nullptr;
+  cudaError_t e = cudaMallocAsync(&sink, grid * sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  popc_probe_kernel<<<grid, 256, 0, s>>>(sink, iters / 8 + 1, 3u);  // warm-up
+  cudaEventRecord(e0, s);
+  popc_probe_kernel<<<grid, 256, 0, s>>>(sink, iters, 5u);
+  cudaEventRecord(e1, s);
+  e = cudaEventSynchronize(e1);
+  float ms = 0;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(sink, s);
+  if (e != cudaSuccess) return e;
+  *popc_per_s = (double)grid * 256.0 * (double)iters * 16.0 / (ms * 1e-3);
+  return cudaStreamSynchronize(s);
+}
+
 // Reduction-throughput probe: every warp stages 1 KB of 32-bit ones in shared memory once, then
 // adds it into the buffer's 1 KB runs with TMA bulk reductions (4 per group, at most two groups
 // reading shared memory at a time), the way the sheared aggregation kernel adds its runs into S.

@@ -85,6 +85,9 @@ int report_error(int code, const char* msg);
 // Packed-u16 integer throughput probe: lane operations per second.
 cudaError_t probe_int_peak(int iters, cudaStream_t s, double* lane_ops_per_s);
 
+// POPC-throughput probe: 32-bit population counts per second on every SM.
+cudaError_t probe_popc_rate(int iters, cudaStream_t s, double* popc_per_s);
+
 // Reduction-throughput probe: bytes per second that TMA bulk add-reductions achieve into a buffer
 // of `bytes` bytes, `passes` passes.
 cudaError_t probe_red_peak(int64_t bytes, int passes, cudaStream_t s, double* bytes_per_s);
