@@ -1,4 +1,6 @@
 // Plain single-pair launches of the SGM stages (one kernel per stage, all on the caller's stream).
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 
 #include "aggregate.cuh"
@@ -127,18 +129,26 @@ static cudaError_t launch_aggregate(const Problem& pb, const Method& mt, const T
 static cudaError_t run_pass(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
                             cudaEvent_t* ev, const Fork* fork, int* n) {
   cudaError_t e;
+  nvtxRangePushA("res2tac census + cost");
   if (mt.flags & 8) {
-    if ((e = launch_ncc_cost(pb, mt, s)) != cudaSuccess) return e;
+    e = launch_ncc_cost(pb, mt, s);
+    nvtxRangePop();
+    if (e != cudaSuccess) return e;
     *n += 3;
   } else {
     census_kernel<<<2 * census_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
     cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
+    nvtxRangePop();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *n += 2;
   }
   if (ev) cudaEventRecord(ev[0], s);
-  if ((e = launch_aggregate(pb, mt, tn, s, fork)) != cudaSuccess) return e;
+  nvtxRangePushA("res2tac aggregation");
+  e = launch_aggregate(pb, mt, tn, s, fork);
+  nvtxRangePop();
+  if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], s);
+  nvtxRangePushA("res2tac wta + right-disparity keys");
   // pixels per block of 256 threads, capped so that the staged sums take at most 64 KB
   const int T = wta_staged_px(pb.D, mt.wide != 0, tn.wta_chunk);
   const size_t smem = wta_staged_smem_bytes(pb.D, mt.wide != 0, T);
@@ -152,6 +162,7 @@ static cudaError_t run_pass(const Problem& pb, const Method& mt, const Tuning& t
                          (int)smem);
     wta_dr_staged_kernel<false><<<nw, 256, smem, s>>>(pb, T);
   }
+  nvtxRangePop();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[2], s);
   *n += 3;
@@ -199,12 +210,14 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
       cudaSuccess)
     return e;
   const int nm = median_items(pb.W, pb.H);
+  nvtxRangePushA("res2tac lr check + median");
   if (pb.disp_f == nullptr)  // uint16 map
     lr_median_kernel<false, false><<<nm, 256, 0, s>>>(pb, mt);
   else if (mt.wide)          // sub-pixel float map
     lr_median_kernel<true, true><<<nm, 256, 0, s>>>(pb, mt);
   else
     lr_median_kernel<true, false><<<nm, 256, 0, s>>>(pb, mt);
+  nvtxRangePop();
   n++;
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[exact ? 7 : 4], s);
