@@ -7,8 +7,9 @@
 // 9x7 gives 62 bits, both kept as uint64.
 // Cost (Eq. image_matching): C(x, y, d) = popcount(CT_L(x, y) ^ CT_R(x - d, y)), 255 if x < d.
 //
-// census_tile: 32 x 8 pixels of one image; the window rows around them are staged in shared
-// memory (zero outside the image) and each thread computes one descriptor, stored to the pair's
+// census_tile: 128 x 8 pixels of one image; the window rows around them are staged in shared
+// memory as 4-byte words (zero outside the image) and each thread computes the descriptors of four
+// neighbouring pixels at once, four byte comparisons per 32-bit operation, stored to the pair's
 // descriptor map (8 B per pixel and image; 16 B per pixel for both, which stays in L2).
 // cost_tile: kCostTX pixels of one row, all D disparities. It stages the row's kCostTX left
 // descriptors and the kCostTX + D right ones it reads (x0 - D .. x0 + kCostTX - 1) in shared
@@ -23,7 +24,7 @@
 namespace r2t {
 
 constexpr int kCostTX = 128;  // cost tile: 128 pixels of one row, all D disparities
-constexpr int kCtTX = 32, kCtTY = 8;  // census tile: 32 x 8 pixels of one image
+constexpr int kCtTX = 128, kCtTY = 8;  // census tile: 128 x 8 pixels of one image
 
 __host__ __device__ inline int cost_items(int W, int H) { return H * ((W + kCostTX - 1) / kCostTX); }
 // Census tiles of one image; a pair has twice as many (left image first).
@@ -32,7 +33,9 @@ __host__ __device__ inline int census_items(int W, int H) {
 }
 
 struct CensusSmem {
-  uint8_t win[kCtTY + 6][kCtTX + 8];  // rows y0 - ry .. y0 + 7 + ry, columns x0 - rx .. x0 + 31 + rx
+  // window rows y0 - ry .. y0 + 7 + ry, columns x0 - 4 .. x0 + 131, as 4-byte words (word w holds
+  // columns x0 - 4 + 4 w .. + 3, lowest address in the low byte)
+  uint32_t win[kCtTY + 6][kCtTX / 4 + 2];
 };
 // CT_R(x0 - D + i) sits at r[i & 3][i >> 2]: the lanes of a warp read i, i - 4, i - 8, ... (their
 // words are 4 disparities apart), which this split keeps on consecutive words (no bank conflict).
@@ -41,38 +44,86 @@ struct CostSmem {
   uint64_t r[4][(kCostTX + 256) / 4]; // CT_R(x0 - D + i), i < kCostTX + D (0 outside the image)
 };
 
-// Census descriptor of the pixel whose window's top-left byte is win[0][i] (row stride kCtTX + 8).
-// Bits are accumulated from the last neighbour to the first, each as the sign of
-// (neighbour - centre) shifted in from the right, so bit k ends at position k (first 32
-// neighbours in the low word).
+// Bytewise unsigned a < b of four byte lanes, in bit 7 of each byte (other bits undefined).
+// t = (a | 0x80) - (b & 0x7F) per byte lies in 1 .. 255, so no borrow crosses a byte, and its bit 7
+// says a_low >= b_low (the low seven bits); with the top bits a7, b7:
+// a < b = (!a7 & b7) | (a7 == b7 & !(a_low >= b_low)).
+__device__ __forceinline__ uint32_t bytes_lt(uint32_t a, uint32_t b_low, uint32_t b) {
+  const uint32_t t = (a | 0x80808080u) - b_low;
+  return (~a & b) | (~(a ^ b) & ~t);
+}
+
+// Census descriptors of the four pixels x .. x + 3 of one row, x = x0 + 4 lane, from the window
+// words of rows r0 .. r0 + ch - 1 (r0 = the pixels' row - ry + ry = tile row). The four pixels'
+// comparisons with neighbour k run in one word: the neighbour bytes of offset dx are the window
+// bytes 4 + dx .. 7 + dx of the three words lane, lane + 1, lane + 2. Neighbour k's four result
+// bits (bit 7 of each byte) are shifted into byte lane p of the accumulator of group k / 8, which
+// after eight neighbours holds bit k % 8 of pixel p's descriptor byte k / 8 at position k % 8; a
+// byte transpose of the accumulators gives the four descriptors.
 template <int CW, int CH>
-__device__ __forceinline__ uint64_t census_at(const uint8_t (*win)[kCtTX + 8], int i) {
+__device__ __forceinline__ void census_x4(const uint32_t (*win)[kCtTX / 4 + 2], int lane,
+                                          uint64_t* out) {
   constexpr int RX = CW / 2, RY = CH / 2;
-  const int c = win[RY][i + RX];
-  uint32_t lo = 0, hi = 0;
+  constexpr int NB = CW * CH - 1;     // descriptor bits
+  constexpr int NG = (NB + 7) / 8;    // groups of eight neighbours
+  constexpr int centre = RY * CW + RX;
+  const uint32_t c = win[RY][lane + 1];
+  const uint32_t c_low = c & 0x7F7F7F7Fu;
+  uint32_t acc[8];
 #pragma unroll
-  for (int j = CH - 1; j >= 0; j--) {
+  for (int g = 0; g < 8; g++) acc[g] = 0;
 #pragma unroll
-    for (int ii = CW - 1; ii >= 0; ii--) {
-      constexpr int centre = RY * CW + RX;
-      const int n = j * CW + ii;  // window position, compile time after unrolling
+  for (int j = 0; j < CH; j++) {
+    const uint32_t w0 = win[j][lane], w1 = win[j][lane + 1], w2 = win[j][lane + 2];
+#pragma unroll
+    for (int i = 0; i < CW; i++) {
+      const int n = j * CW + i;  // window position, compile time after unrolling
       if (n == centre) continue;
-      const int k = n < centre ? n : n - 1;          // bit of this neighbour
-      const uint32_t dlt = (uint32_t)((int)win[j][i + ii] - c);  // sign bit: 1 iff darker
-      if (k >= 32)
-        hi = __funnelshift_l(dlt, hi, 1);  // (hi << 1) | (dlt >> 31)
+      const int k = n < centre ? n : n - 1;
+      const int o = 4 + i - RX;  // byte offset of the neighbour word in w0 w1 w2
+      uint32_t nb;
+      if (o == 4)
+        nb = w1;
+      else if (o == 8)
+        nb = w2;
+      else if (o < 4)
+        nb = __byte_perm(w0, w1, (o) | ((o + 1) << 4) | ((o + 2) << 8) | ((o + 3) << 12));
       else
-        lo = __funnelshift_l(dlt, lo, 1);
+        nb = __byte_perm(w1, w2, (o - 4) | ((o - 3) << 4) | ((o - 2) << 8) | ((o - 1) << 12));
+      acc[k >> 3] = (acc[k >> 3] >> 1) | (bytes_lt(nb, c_low, c) & 0x80808080u);
     }
   }
-  return (uint64_t)lo | ((uint64_t)hi << 32);
+  if (NB % 8) acc[NG - 1] >>= 8 - NB % 8;  // a last group of fewer than eight bits
+  // 4 x 4 byte transposes: descriptor byte g of pixel p = byte p of acc[g]
+  uint32_t lo[4], hi[4];
+  {
+    const uint32_t u0 = __byte_perm(acc[0], acc[1], 0x5140), u1 = __byte_perm(acc[0], acc[1], 0x7362);
+    const uint32_t u2 = __byte_perm(acc[2], acc[3], 0x5140), u3 = __byte_perm(acc[2], acc[3], 0x7362);
+    lo[0] = __byte_perm(u0, u2, 0x5410);
+    lo[1] = __byte_perm(u0, u2, 0x7632);
+    lo[2] = __byte_perm(u1, u3, 0x5410);
+    lo[3] = __byte_perm(u1, u3, 0x7632);
+  }
+  if (NG > 4) {
+    const uint32_t u0 = __byte_perm(acc[4], acc[5], 0x5140), u1 = __byte_perm(acc[4], acc[5], 0x7362);
+    const uint32_t u2 = __byte_perm(acc[6], acc[7], 0x5140), u3 = __byte_perm(acc[6], acc[7], 0x7362);
+    hi[0] = __byte_perm(u0, u2, 0x5410);
+    hi[1] = __byte_perm(u0, u2, 0x7632);
+    hi[2] = __byte_perm(u1, u3, 0x5410);
+    hi[3] = __byte_perm(u1, u3, 0x7632);
+  } else {
+    hi[0] = hi[1] = hi[2] = hi[3] = 0;
+  }
+#pragma unroll
+  for (int p = 0; p < 4; p++) out[p] = (uint64_t)lo[p] | ((uint64_t)hi[p] << 32);
 }
 
 // Census tile `item` of the pair (items [0, census_items) the left image, then the right one)
-// into pb.ct: left descriptors at [0, W H), right ones at [W H, 2 W H).
+// into pb.ct: left descriptors at [0, W H), right ones at [W H, 2 W H). Warp w computes row
+// y0 + w; lane l the pixels x0 + 4 l .. + 3.
 template <int CW, int CH>
 __device__ __forceinline__ void census_tile(const Problem& pb, int item, CensusSmem& sm) {
-  constexpr int RX = CW / 2, RY = CH / 2, NR = kCtTY + 2 * RY, NC = kCtTX + 2 * RX;
+  constexpr int RY = CH / 2, NR = kCtTY + 2 * RY, NWD = kCtTX / 4 + 2;
   const int W = pb.W, H = pb.H;
   const int per = census_items(W, H);
   const int img = item >= per ? 1 : 0;
@@ -80,18 +131,33 @@ __device__ __forceinline__ void census_tile(const Problem& pb, int item, CensusS
   const int ntx = (W + kCtTX - 1) / kCtTX;
   const int x0 = (it % ntx) * kCtTX, y0 = (it / ntx) * kCtTY;
   const uint8_t* src = img ? pb.right : pb.left;
-  for (int k = threadIdx.x; k < NR * NC; k += blockDim.x) {
-    const int r = k / NC, c = k - r * NC;
-    const int gy = y0 - RY + r, gx = x0 - RX + c;
-    sm.win[r][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? __ldg(src + (int64_t)gy * pb.in_pitch + gx)
-                                                           : (uint8_t)0;
+  for (int k = threadIdx.x; k < NR * NWD; k += blockDim.x) {
+    const int r = k / NWD, cw = k - r * NWD;
+    const int gy = y0 - RY + r, gx = x0 - 4 + 4 * cw;
+    uint32_t v = 0;
+    if (gy >= 0 && gy < H) {
+      const uint8_t* row = src + (int64_t)gy * pb.in_pitch;
+      if (gx >= 0 && gx + 3 < W && ((reinterpret_cast<uintptr_t>(row + gx) & 3) == 0)) {
+        v = __ldg(reinterpret_cast<const uint32_t*>(row + gx));
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+          if (gx + b >= 0 && gx + b < W) v |= (uint32_t)__ldg(row + gx + b) << (8 * b);
+      }
+    }
+    sm.win[r][cw] = v;
   }
   __syncthreads();
-  const int lx = threadIdx.x % kCtTX, ly = threadIdx.x / kCtTX;
-  const int x = x0 + lx, y = y0 + ly;
-  if (x < W && y < H)
-    pb.ct[(int64_t)img * W * H + (int64_t)y * W + x] =
-        census_at<CW, CH>(reinterpret_cast<const uint8_t(*)[kCtTX + 8]>(&sm.win[ly][0]), lx);
+  const int ly = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int x = x0 + 4 * lane, y = y0 + ly;
+  if (ly < kCtTY && x < W && y < H) {
+    uint64_t d[4];
+    census_x4<CW, CH>(reinterpret_cast<const uint32_t(*)[NWD]>(&sm.win[ly][0]), lane, d);
+    uint64_t* o = pb.ct + (int64_t)img * W * H + (int64_t)y * W + x;
+#pragma unroll
+    for (int p = 0; p < 4; p++)
+      if (x + p < W) o[p] = d[p];
+  }
   __syncthreads();  // the block may take another tile into the same shared memory
 }
 
