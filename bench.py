@@ -394,6 +394,21 @@ def main():
         exact_cc = variant(binding.RES2TAC_EXACT_CC)
         exact_cc["valid_fraction_approximate_check"] = round(
             float((binding.u16(out) != binding.RES2TAC_INVALID).mean()), 4)
+        # the same step with the cost volume computed on the tensor cores (tuning cost_mode 2:
+        # a dot product over the census bits, tcgen05): its timing and bit-identity of the map
+        tensor_cost = None
+        if prm["census_w"] == 9 and D in (64, 128):
+            tctx = binding.Stereo(prm)
+            t = binding.res2tac_get_tuning(tctx.handle)
+            t.cost_mode = 2
+            binding.res2tac_set_tuning(tctx.handle, t)
+            o = torch.empty((H, W), dtype=torch.int16, device="cuda")
+            ms, st = time_variant(tctx.handle, lambda: binding.res2tac_compute(
+                tctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, o.data_ptr(), 2 * W, sh))
+            tensor_cost = {"value": round(ws * de / (ms / 1e3) / 1e6, 1), "unit": "MDE/s",
+                           "ms_per_step": round(ms, 4), "stage_ms": st,
+                           "bit_identical_to_default": bool(torch.equal(o, out))}
+            tctx.close()
         # rectification of the raw pair (Sec. 2.1.1) in front of the same step, through seeded
         # calibration-like maps kept in the context
         rmaps = [torch.from_numpy(m).cuda() for sd in (10, 11)
@@ -592,6 +607,7 @@ def main():
         "stage_ms": {k: round(v / args.steps, 4) for k, v in stage.items()},
         "subpixel": subpixel,
         "exact_cc": exact_cc,
+        "tensor_core_cost": tensor_cost,
         "ncc": ncc,
         "rectify": rectify,
         "roofline": {"kernel": "aggregate (SGM paths)", "bound": "alu",

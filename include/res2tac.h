@@ -104,8 +104,12 @@ typedef struct res2tac_pair {
  *   D % shear_dpl == 0.
  * row_mode: 1 = both directions of a row in one lane group, 2 = one direction per group.
  * shear_cpl: chains per lane of the column / diagonal path kernel (1 or 2).
+ * cost_mode: kernel of the Hamming cost of the 9 x 7 census, Eq. (image_matching): 1 = population
+ *   counts on the CUDA cores, 2 = the same integers as a dot product over the descriptor bits on
+ *   the tensor cores (tcgen05, fp8 operands, exact fp32 accumulation; D = 64 or 128 only, other
+ *   shapes and the 5 x 5 census use the population-count kernel).
  * Automatic values: agg_dpl 2 for D <= 64, 4 for D <= 128, else 8; agg_warps 2; wta_chunk 128;
- * shear_dpl 16; row_mode 2; shear_cpl 2 at D = 128, else 1. */
+ * shear_dpl 16; row_mode 2; shear_cpl 2 at D = 128, else 1; cost_mode 1 (measured faster). */
 typedef struct res2tac_tuning {
   int32_t agg_dpl;
   int32_t agg_warps;
@@ -113,6 +117,7 @@ typedef struct res2tac_tuning {
   int32_t shear_dpl;
   int32_t row_mode;
   int32_t shear_cpl;
+  int32_t cost_mode;
 } res2tac_tuning;
 
 /* Validates *p, allocates the context's device scratch for a W x H x D pair on the current
@@ -232,8 +237,9 @@ int res2tac_batch_reserve(res2tac_t h, size_t scratch_bytes, int32_t max_pairs);
 
 /* Reads / sets the kernel configuration (RES2TAC_EINVAL for a setting the context's D cannot
  * use). res2tac_autotune times every valid setting on the given device pair (left, right,
- * in_pitch as for res2tac_compute, output into disp), keeps the fastest in the context and
- * returns it in *best; it synchronises s. */
+ * in_pitch as for res2tac_compute, output into disp), then the fastest one with the other cost
+ * kernel where the shape has two, keeps the fastest in the context and returns it in *best; it
+ * synchronises s. */
 int res2tac_get_tuning(res2tac_t h, res2tac_tuning* t);
 int res2tac_set_tuning(res2tac_t h, const res2tac_tuning* t);
 int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int64_t in_pitch,

@@ -23,7 +23,7 @@ CHECK_OBJDIR = os.path.join(HERE, "_build_check")
 CHECK_LIB = os.path.join(HERE, "libres2tac_check.so")
 UNITS = ("abi.cu", "kernels_plain.cu", "kernels_batch.cu", "noalloc.cu", "agg_rows_narrow.cu",
          "agg_rows_wide.cu", "agg_shear_narrow.cu", "agg_shear_wide.cu", "agg_shear_batch_narrow.cu",
-         "agg_shear_batch_wide.cu", "ncc.cu", "rectify.cu")
+         "agg_shear_batch_wide.cu", "ncc.cu", "rectify.cu", "cost_mma.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -377,6 +377,7 @@ int res2tac_get_tuning(res2tac_t h, res2tac_tuning* t) {
   t->shear_dpl = h->tuning.shear_dpl;
   t->row_mode = h->tuning.row_split ? 2 : 1;
   t->shear_cpl = h->tuning.shear_cpl;
+  t->cost_mode = h->tuning.cost_mode + 1;
   return RES2TAC_OK;
 }
 
@@ -389,12 +390,13 @@ int res2tac_set_tuning(res2tac_t h, const res2tac_tuning* t) {
   if (t->shear_dpl) n.shear_dpl = t->shear_dpl;
   if (t->row_mode) n.row_split = t->row_mode == 2 ? 1 : (t->row_mode == 1 ? 0 : -1);
   if (t->shear_cpl) n.shear_cpl = t->shear_cpl;
+  if (t->cost_mode) n.cost_mode = t->cost_mode - 1;
   if (!r2t::tuning_valid(n, h->p.max_disp))
     return fail(RES2TAC_EINVAL,
-                "tuning (dpl %d, warps %d, chunk %d, shear dpl %d, row mode %d, shear cpl %d) "
-                "invalid for D = %d",
+                "tuning (dpl %d, warps %d, chunk %d, shear dpl %d, row mode %d, shear cpl %d, "
+                "cost mode %d) invalid for D = %d",
                 n.agg_dpl, n.agg_warps, n.wta_chunk, n.shear_dpl, t->row_mode, n.shear_cpl,
-                h->p.max_disp);
+                t->cost_mode, h->p.max_disp);
   h->tuning = n;
   return RES2TAC_OK;
 }
@@ -414,7 +416,7 @@ int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int
         for (int sd : sdpls)
           for (int split = 0; split < 2; split++)
             for (int cpl = 1; cpl <= 2; cpl++) {
-              r2t::Tuning t{a, w, c, sd, split, cpl};
+              r2t::Tuning t{a, w, c, sd, split, cpl, 0};
               if (r2t::tuning_valid(t, h->p.max_disp)) cands.push_back(t);
             }
   if (cands.empty()) return fail(RES2TAC_EINVAL, "no valid tuning");
@@ -424,22 +426,21 @@ int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int
   const r2t::Tuning keep = h->tuning;
   float best_ms = 1e30f;
   r2t::Tuning best_t = keep;
-  for (const r2t::Tuning& t : cands) {
+  // times t (two warm-up calls, then 5 calls) and keeps it when it is the fastest so far
+  auto try_tuning = [&](const r2t::Tuning& t) {
     h->tuning = t;
-    for (int rep = 0; rep < 2; rep++) {  // warm-up
+    for (int rep = 0; rep < 2 && !rc; rep++)  // warm-up
       rc = res2tac_compute(h, left, right, in_pitch, disp, out_pitch, s);
-      if (rc) break;
-    }
-    if (rc) break;
+    if (rc) return;
     cudaEventRecord(e0, st);
     const int reps = 5;
     for (int rep = 0; rep < reps && !rc; rep++)
       rc = res2tac_compute(h, left, right, in_pitch, disp, out_pitch, s);
     cudaEventRecord(e1, st);
-    if (rc) break;
+    if (rc) return;
     if (cudaEventSynchronize(e1) != cudaSuccess) {
       rc = fail(RES2TAC_ECUDA, "autotune synchronisation failed");
-      break;
+      return;
     }
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
@@ -447,6 +448,17 @@ int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int
       best_ms = ms;
       best_t = t;
     }
+  };
+  for (const r2t::Tuning& t : cands) {
+    try_tuning(t);
+    if (rc) break;
+  }
+  r2t::Problem shape{};
+  shape.D = h->p.max_disp;
+  if (!rc && r2t::cost_mma_ok(shape, h->method)) {  // the other cost kernel with the best setting
+    r2t::Tuning t = best_t;
+    t.cost_mode = 1 - t.cost_mode;
+    try_tuning(t);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

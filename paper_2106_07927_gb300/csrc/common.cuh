@@ -49,6 +49,8 @@ struct Problem {
 // constant true and compiles away.
 // Sites: 1 row-kernel cost load, 2 row-kernel add into S, 3 sheared-kernel cost copy, 4 / 5
 // sheared-kernel bulk add (run before / after a wrap), 6 WTA staging copy of S, 7 WTA store of D^L.
+// Site 8 is recorded in every build: a block of the tensor-core cost kernel whose MMAs did not
+// complete within its poll limit (it stores no cost).
 #ifdef RES2TAC_CHECK_BOUNDS
 static __device__ __noinline__ bool check_range(unsigned* fault, const void* p, int64_t bytes,
                                                 const void* lo, int64_t size, int site) {

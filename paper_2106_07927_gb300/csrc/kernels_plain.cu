@@ -68,6 +68,7 @@ Tuning default_tuning(int D) {
   t.shear_dpl = shear_dpl_default(D);
   t.shear_cpl = shear_cpl_default(D);
   t.row_split = 1;  // one row direction per lane group (measured 2 % faster at D = 128)
+  t.cost_mode = 0;  // population counts: measured faster than the tensor-core kernel
   return t;
 }
 
@@ -81,6 +82,7 @@ bool tuning_valid(const Tuning& t, int D) {
   if (t.shear_cpl != 1 && t.shear_cpl != 2) return false;
   if (D % t.shear_dpl != 0) return false;
   if (t.row_split != 0 && t.row_split != 1) return false;
+  if (t.cost_mode != 0 && t.cost_mode != 1) return false;
   return true;
 }
 
@@ -137,7 +139,11 @@ static cudaError_t run_pass(const Problem& pb, const Method& mt, const Tuning& t
     *n += 3;
   } else {
     census_kernel<<<2 * census_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
-    cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
+    if (tn.cost_mode == 1 && cost_mma_ok(pb, mt)) {
+      if ((e = launch_cost_mma(pb, mt, s)) != cudaSuccess) return e;
+    } else {
+      cost_kernel<<<cost_items(pb.W, pb.H), 256, 0, s>>>(pb, mt);
+    }
     nvtxRangePop();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     *n += 2;

@@ -14,6 +14,7 @@ struct Tuning {
   int shear_dpl;  // disparities per lane of the sheared-column kernel (16 or 32)
   int shear_cpl;  // chains per lane of the sheared-column kernel (1 or 2)
   int row_split;  // 1: one row direction per lane group, 0: both directions in one group
+  int cost_mode;  // 0: population-count cost kernel, 1: tensor-core cost kernel (cost_mma_ok)
 };
 
 // A second stream and two events that let the two aggregation kernels run concurrently: the
@@ -58,6 +59,12 @@ const void* batch_shear_kernel_fn();
 // fork: NULL runs the two aggregation kernels one after the other on s.
 cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, cudaStream_t s,
                          int* launches, cudaEvent_t* ev = nullptr, const Fork* fork = nullptr);
+
+// Cost volume of the 9 x 7 census on the tensor cores (tcgen05), with the clearing of the
+// aggregated sums; the descriptor map pb.ct must be filled. cost_mma_ok: the shapes it covers
+// (9 x 7 census, D = 64 or 128).
+bool cost_mma_ok(const Problem& pb, const Method& mt);
+cudaError_t launch_cost_mma(const Problem& pb, const Method& mt, cudaStream_t s);
 
 // NCC matching cost (mt.flags & 8, patch mt.cw x mt.cw, pb.nst set): patch statistics
 // of both images, then the cost volume with the clearing of the aggregated sums; 3 launches.

@@ -122,6 +122,49 @@ def test_every_tuning_is_bit_identical():
     assert n == 144
 
 
+# The cost volume on the tensor cores (tuning cost_mode 2): the same integers as the
+# population counts, on shapes with one and several tiles per row, a ragged last tile, images
+# narrower than a tile, padded pitches, wide sums and the exact check; 5 x 5 and D = 256 fall back
+# to the population-count kernel.
+TC = dict(cost_mode=2)
+
+
+@pytest.mark.parametrize("W,H,D,cw,ch,p2,flags,pads", [
+    (1242, 60, 128, 9, 7, 120, 3, (0, 0)),
+    (300, 40, 64, 9, 7, 120, 3, (13, 3)),
+    (1, 1, 64, 9, 7, 120, 0, (0, 0)),
+    (5, 3, 128, 9, 7, 120, 3, (0, 0)),
+    (127, 17, 128, 9, 7, 120, 2, (1, 1)),
+    (257, 33, 128, 9, 7, 16384, 3, (0, 0)),
+    (200, 30, 64, 9, 7, 120, 3 | 4, (0, 0)),  # exact consistency check
+    (97, 21, 256, 9, 7, 120, 3, (0, 0)),
+    (130, 20, 128, 5, 5, 120, 3, (0, 0)),
+])
+def test_tensor_core_cost_is_bit_exact(W, H, D, cw, ch, p2, flags, pads):
+    left, right, _ = scenes.make_scene("road", W + 7 * H, W, H, D)
+    prm = scenes.params(W, H, D, cw, ch, 10, p2, 8, flags)
+    t = binding.res2tac_tuning(cost_mode=2)
+    _assert_same(left, right, prm, tuning=t, in_pad=pads[0], out_pad=pads[1])
+
+
+def test_tensor_core_cost_setting_and_autotune():
+    import torch
+    left, right, _ = scenes.make_scene("road", 5, 160, 48, 64)
+    prm = scenes.params(160, 48, 64, 9, 7, 10, 120, 8, 3)
+    st = binding.Stereo(prm)
+    assert binding.res2tac_get_tuning(st.handle).cost_mode == 1  # population counts by default
+    with pytest.raises(binding.Res2tacError):
+        binding.res2tac_set_tuning(st.handle, binding.res2tac_tuning(cost_mode=3))
+    L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
+    o = torch.empty((48, 160), dtype=torch.int16, device="cuda")
+    best = binding.res2tac_autotune(st.handle, L.data_ptr(), R.data_ptr(), 160, o.data_ptr(),
+                                    320, torch.cuda.current_stream().cuda_stream)
+    assert best.cost_mode in (1, 2)
+    out = st.compute(L, R)
+    assert np.array_equal(binding.u16(out), oracle.sgm(left, right, 64, 9, 7, 10, 120, 8, 3))
+    st.close()
+
+
 @pytest.mark.parametrize("D", [48, 80, 96, 144, 160, 256])
 def test_partial_lane_groups_every_mode(D):
     # D that leaves lanes of a group without disparities, in both row modes and both sheared
