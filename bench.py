@@ -55,6 +55,11 @@ def _args():
     ap.add_argument("--pair", type=int, nargs=3, metavar=("W", "H", "D"), default=None,
                     help="time a seeded road-like pair of this size instead of the 1242x375 "
                          "workload (9x7, 8 paths, LR + median; for profiling larger pairs)")
+    ap.add_argument("--profile-steps", type=int, default=0, metavar="N",
+                    help="only run N plain steps of the workload and exit, printing nothing "
+                         "(the command that ncu captures kernels of)")
+    ap.add_argument("--cost-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="with --profile-steps: the tuning's cost_mode (0 = default)")
     return ap.parse_args()
 
 
@@ -294,6 +299,17 @@ def main():
     Ld = torch.from_numpy(left).cuda()
     Rd = torch.from_numpy(right).cuda()
     out = torch.empty((H, W), dtype=torch.int16, device="cuda")
+    if args.profile_steps > 0:  # a bare run of plain steps for a profiler, no timing
+        if args.cost_mode:
+            t = binding.res2tac_get_tuning(ctx.handle)
+            t.cost_mode = args.cost_mode
+            binding.res2tac_set_tuning(ctx.handle, t)
+        for _ in range(args.profile_steps):
+            binding.res2tac_compute(ctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, out.data_ptr(),
+                                    2 * W, sh)
+        torch.cuda.synchronize()
+        ctx.close()
+        return
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
