@@ -42,6 +42,11 @@ constexpr size_t kGroupBytes = 96u << 20;
 constexpr int kGroupMaxPairs = 32;
 constexpr int kSlots = 4;  // groups in flight
 constexpr int kAggWarps = 2;  // warps per block of the persistent aggregation kernels
+// Blocks per SM of the persistent aggregation kernels. Their warps claim chains with atomics;
+// a grid of every block that fits lets the SMs that start first take most of a group's long row
+// chains, which then share their schedulers while other SMs idle (a single 1242x375 pair: row
+// kernel 228 us against 121 us for the single-pair launch, whose blocks the hardware spreads).
+constexpr int kRowBlocksPerSM = 3, kShearBlocksPerSM = 8;
 
 // Block-claimed stage kernels of one group: item = lo + claim, pair found among the group's.
 #define R2T_GROUP_LOOP(STAGE, BODY)                                                  \
@@ -63,7 +68,8 @@ __global__ void __launch_bounds__(256) batch_census_kernel(const GroupDesc* gd,
   R2T_GROUP_LOOP(kStCensus, census_tile_dispatch(pb, mt, item - prefix[p], sm))
 }
 
-__global__ void __launch_bounds__(256) batch_cost_kernel(const GroupDesc* gd,
+// (at least 5 blocks per SM: the population counts need the warps to hide their pipe's queue)
+__global__ void __launch_bounds__(256, 5) batch_cost_kernel(const GroupDesc* gd,
                                                          const Problem* probs, const int* prefix,
                                                          Method mt, unsigned* counters) {
   __shared__ CostSmem sm;
@@ -258,6 +264,13 @@ void batch_destroy(BatchEngine* e) {
   delete e;
 }
 
+static int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
 template <class K>
 static int persistent_grid(K kernel, size_t smem, int threads = 256) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -290,10 +303,11 @@ static int capture_t(BatchEngine* e, const Method& mt, int wta_smem, int warp_sm
   const int g_cost = persistent_grid(batch_cost_kernel, 0);
   const void* k_rows = batch_row_kernel_fn<WIDE>();
   const void* k_shear = batch_shear_kernel_fn<WIDE>();
-  const int g_rows = persistent_grid(k_rows, 0, 32 * kAggWarps);
+  const int g_rows = std::min(persistent_grid(k_rows, 0, 32 * kAggWarps), sm_count() * kRowBlocksPerSM);
   const int shear_smem = kAggWarps * warp_smem;
   cudaFuncSetAttribute(k_shear, cudaFuncAttributeMaxDynamicSharedMemorySize, shear_smem);
-  const int g_shear = persistent_grid(k_shear, shear_smem, 32 * kAggWarps);
+  const int g_shear = std::min(persistent_grid(k_shear, shear_smem, 32 * kAggWarps),
+                               sm_count() * kShearBlocksPerSM);
   const int g_wta = persistent_grid(batch_wta_kernel<WIDE>, wta_smem);
   const int g_med = persistent_grid(batch_median_kernel, 0);
   cudaError_t c = cudaGetLastError();
