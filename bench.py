@@ -60,6 +60,9 @@ def _args():
                          "(the command that ncu captures kernels of)")
     ap.add_argument("--cost-mode", type=int, default=0, choices=[0, 1, 2],
                     help="with --profile-steps: the tuning's cost_mode (0 = default)")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="with --profile-steps: each step is res2tac_compute_batch of the pair "
+                         "alone, followed by the same pair through res2tac_compute")
     return ap.parse_args()
 
 
@@ -304,7 +307,11 @@ def main():
             t = binding.res2tac_get_tuning(ctx.handle)
             t.cost_mode = args.cost_mode
             binding.res2tac_set_tuning(ctx.handle, t)
+        pair = binding.res2tac_pair(Ld.data_ptr(), Rd.data_ptr(), W, out.data_ptr(), 2 * W, W,
+                                    H, D, 0)
         for _ in range(args.profile_steps):
+            if args.profile_batch:
+                binding.res2tac_compute_batch(ctx.handle, [pair], sh)
             binding.res2tac_compute(ctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, out.data_ptr(),
                                     2 * W, sh)
         torch.cuda.synchronize()
