@@ -107,7 +107,9 @@ typedef struct res2tac_pair {
  * cost_mode: kernel of the Hamming cost of the 9 x 7 census, Eq. (image_matching): 1 = population
  *   counts on the CUDA cores, 2 = the same integers as a dot product over the descriptor bits on
  *   the tensor cores (tcgen05, fp8 operands, exact fp32 accumulation; D = 64 or 128 only, other
- *   shapes and the 5 x 5 census use the population-count kernel).
+ *   shapes and the 5 x 5 census use the population-count kernel). Its blocks take all of their
+ *   SM's tensor memory, so they wait for tensor-core kernels of other libraries running
+ *   concurrently on other streams.
  * Automatic values: agg_dpl 2 for D <= 64, 4 for D <= 128, else 8; agg_warps 2; wta_chunk 128;
  * shear_dpl 16; row_mode 2; shear_cpl 2 at D = 128, else 1; cost_mode 1 (measured faster). */
 typedef struct res2tac_tuning {

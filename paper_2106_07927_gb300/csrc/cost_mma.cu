@@ -27,7 +27,9 @@
 // The hand-offs are mbarriers: stage full (producers -> MMA), stage empty and accumulator full
 // (MMA completion, tcgen05.commit), accumulator empty (epilogue -> MMA). Every wait polls at most
 // kSpinLimit times; a wait that gives up records fault site 8 and makes the block stop taking
-// tiles, so the kernel always ends.
+// tiles, so the kernel always ends. The block holds all 512 tensor-memory columns of its SM: when
+// a kernel of another library (a tensor-core GEMM on another stream) holds columns on that SM,
+// the allocation waits until that kernel frees them.
 #include <stdint.h>
 
 #include <algorithm>
