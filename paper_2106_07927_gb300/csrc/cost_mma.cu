@@ -117,7 +117,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 }
 
 // Polls the mbarrier at `bar` until the phase of parity `par` has completed; false after
-// kSpinLimit polls, or earlier once another role has given up (*abort set).
+// kSpinLimit polls, or earlier once another role has given up (*abort set; abort == nullptr: no
+// early end).
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t par, volatile int* abort) {
   for (uint32_t it = 0; it < kSpinLimit; it++) {
     uint32_t done;
@@ -128,7 +129,7 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t par, volatile in
         : "r"(bar), "r"(par), "r"(kSuspendNs)
         : "memory");
     if (done) return true;
-    if (*abort) return false;
+    if (abort && *abort) return false;
   }
   return false;
 }
@@ -256,6 +257,7 @@ __global__ void __launch_bounds__(MmaWarps<D>::kThreads, 1) cost_mma_kernel(Prob
   } else if (warp == kMmaWarp) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
+      int issued = 0;  // tiles whose MMAs were issued
       for (int t = t0, i = 0; t < t1; t++, i++) {
         const int s = i & 1;
         const uint32_t par = (i >> 1) & 1;
@@ -278,7 +280,12 @@ __global__ void __launch_bounds__(MmaWarps<D>::kThreads, 1) cost_mma_kernel(Prob
         asm volatile(
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 tfull(s)));
+        issued = i + 1;
       }
+      // the tensor memory is freed below: wait for the last MMAs to complete, also when another
+      // role gave up before reading them (their phase has completed already otherwise)
+      if (issued > 0 && !bar_wait(tfull((issued - 1) & 1), ((issued - 1) >> 1) & 1, nullptr))
+        give_up(pb, abort);
     }
     __syncwarp();
   } else {
