@@ -432,6 +432,21 @@ def main():
                            "ms_per_step": round(ms, 4), "stage_ms": st,
                            "bit_identical_to_default": bool(torch.equal(o, out))}
             tctx.close()
+        # the same step with the row-path kernel recomputing its costs from the census
+        # descriptors (tuning row_cost 2) instead of reading the cost volume
+        row_recompute = None
+        if prm["census_w"] in (5, 9) and D % 32 == 0 and D <= 256:
+            rctx = binding.Stereo(prm)
+            t = binding.res2tac_get_tuning(rctx.handle)
+            t.agg_dpl, t.row_mode, t.row_cost = D // 32, 2, 2
+            binding.res2tac_set_tuning(rctx.handle, t)
+            o = torch.empty((H, W), dtype=torch.int16, device="cuda")
+            ms, st = time_variant(rctx.handle, lambda: binding.res2tac_compute(
+                rctx.handle, Ld.data_ptr(), Rd.data_ptr(), W, o.data_ptr(), 2 * W, sh))
+            row_recompute = {"value": round(ws * de / (ms / 1e3) / 1e6, 1), "unit": "MDE/s",
+                             "ms_per_step": round(ms, 4), "stage_ms": st,
+                             "bit_identical_to_default": bool(torch.equal(o, out))}
+            rctx.close()
         # rectification of the raw pair (Sec. 2.1.1) in front of the same step, through seeded
         # calibration-like maps kept in the context
         rmaps = [torch.from_numpy(m).cuda() for sd in (10, 11)
@@ -631,6 +646,7 @@ def main():
         "subpixel": subpixel,
         "exact_cc": exact_cc,
         "tensor_core_cost": tensor_cost,
+        "row_recompute": row_recompute,
         "ncc": ncc,
         "rectify": rectify,
         "roofline": {"kernel": "aggregate (SGM paths)", "bound": "alu",

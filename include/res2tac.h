@@ -110,8 +110,12 @@ typedef struct res2tac_pair {
  *   shapes and the 5 x 5 census use the population-count kernel). Its blocks take all of their
  *   SM's tensor memory, so they wait for tensor-core kernels of other libraries running
  *   concurrently on other streams.
+ * row_cost: costs of the row-path kernel: 1 = read from the cost volume, 2 = recomputed from the
+ *   census descriptors inside the walk (popcount of the XOR per step; census cost with
+ *   row_mode 2 and D = 32 agg_dpl only, other settings read the volume).
  * Automatic values: agg_dpl 2 for D <= 64, 4 for D <= 128, else 8; agg_warps 2; wta_chunk 128;
- * shear_dpl 16; row_mode 2; shear_cpl 2 at D = 128, else 1; cost_mode 1 (measured faster). */
+ * shear_dpl 16; row_mode 2; shear_cpl 2 at D = 128, else 1; cost_mode 1 (measured faster);
+ * row_cost 1. */
 typedef struct res2tac_tuning {
   int32_t agg_dpl;
   int32_t agg_warps;
@@ -120,6 +124,7 @@ typedef struct res2tac_tuning {
   int32_t row_mode;
   int32_t shear_cpl;
   int32_t cost_mode;
+  int32_t row_cost;
 } res2tac_tuning;
 
 /* Validates *p, allocates the context's device scratch for a W x H x D pair on the current

@@ -58,7 +58,8 @@ class res2tac_pair(ctypes.Structure):
 
 class res2tac_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("agg_dpl", "agg_warps", "wta_chunk", "shear_dpl",
-                                               "row_mode", "shear_cpl", "cost_mode")]
+                                               "row_mode", "shear_cpl", "cost_mode",
+                                               "row_cost")]
 
 
 class res2tac_batch_tuning(ctypes.Structure):

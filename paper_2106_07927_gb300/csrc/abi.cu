@@ -378,6 +378,7 @@ int res2tac_get_tuning(res2tac_t h, res2tac_tuning* t) {
   t->row_mode = h->tuning.row_split ? 2 : 1;
   t->shear_cpl = h->tuning.shear_cpl;
   t->cost_mode = h->tuning.cost_mode + 1;
+  t->row_cost = h->tuning.row_cost + 1;
   return RES2TAC_OK;
 }
 
@@ -391,6 +392,7 @@ int res2tac_set_tuning(res2tac_t h, const res2tac_tuning* t) {
   if (t->row_mode) n.row_split = t->row_mode == 2 ? 1 : (t->row_mode == 1 ? 0 : -1);
   if (t->shear_cpl) n.shear_cpl = t->shear_cpl;
   if (t->cost_mode) n.cost_mode = t->cost_mode - 1;
+  if (t->row_cost) n.row_cost = t->row_cost - 1;
   if (!r2t::tuning_valid(n, h->p.max_disp))
     return fail(RES2TAC_EINVAL,
                 "tuning (dpl %d, warps %d, chunk %d, shear dpl %d, row mode %d, shear cpl %d, "
@@ -416,7 +418,7 @@ int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int
         for (int sd : sdpls)
           for (int split = 0; split < 2; split++)
             for (int cpl = 1; cpl <= 2; cpl++) {
-              r2t::Tuning t{a, w, c, sd, split, cpl, 0};
+              r2t::Tuning t{a, w, c, sd, split, cpl, 0, 0};
               if (r2t::tuning_valid(t, h->p.max_disp)) cands.push_back(t);
             }
   if (cands.empty()) return fail(RES2TAC_EINVAL, "no valid tuning");
@@ -459,6 +461,11 @@ int res2tac_autotune(res2tac_t h, const uint8_t* left, const uint8_t* right, int
     r2t::Tuning t = best_t;
     t.cost_mode = 1 - t.cost_mode;
     try_tuning(t);
+  }
+  {  // the row kernel recomputing its costs, with the best setting so far
+    r2t::Tuning t = best_t;
+    t.row_cost = 1;
+    if (!rc && r2t::rows_recompute_ok(shape, h->method, t)) try_tuning(t);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

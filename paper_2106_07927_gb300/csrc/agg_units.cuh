@@ -15,6 +15,13 @@ __global__ void __launch_bounds__(512) agg_row_kernel(Problem pb, Method mt) {
   agg_rows<DPL, LPL, WIDE, FULL, SPLIT>(pb, mt, warp * (32 / LPL), 0x7FFFFFFF);
 }
 
+// The row kernel with the costs recomputed from the descriptor map (one direction per warp).
+template <int DPL, bool WIDE, bool FULL>
+__global__ void __launch_bounds__(512) agg_row_rc_kernel(Problem pb, Method mt) {
+  const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  agg_rows_recompute<DPL, 32, WIDE, FULL>(pb, mt, warp, 0x7FFFFFFF);
+}
+
 template <int DPL, int WD, int CPL, bool WIDE, bool FULL>
 __global__ void __launch_bounds__(256) agg_shear_kernel(Problem pb, Method mt, int items) {
   extern __shared__ __align__(16) uint8_t shm[];
@@ -54,9 +61,26 @@ static cudaError_t launch_rows_s(const Problem& pb, const Method& mt, const Tuni
   }
 }
 
+// Recomputed costs (tuning row_cost 1): one row direction per warp of 32 lanes (D = 32 dpl),
+// census cost only (the NCC cost has no descriptor map).
+template <int DPL, bool WIDE>
+static cudaError_t launch_rows_rc(const Problem& pb, const Method& mt, int warps, cudaStream_t s) {
+  const int nu = row_units(pb.H, true);
+  const int grid = (nu + warps - 1) / warps;
+  agg_row_rc_kernel<DPL, WIDE, true><<<grid, warps * 32, 0, s>>>(pb, mt);
+  return cudaGetLastError();
+}
+
 template <bool WIDE>
 cudaError_t launch_rows(const Problem& pb, const Method& mt, const Tuning& tn,
                                cudaStream_t s) {
+  if (rows_recompute_ok(pb, mt, tn)) {
+    switch (tn.agg_dpl) {
+      case 2: return launch_rows_rc<2, WIDE>(pb, mt, tn.agg_warps, s);
+      case 4: return launch_rows_rc<4, WIDE>(pb, mt, tn.agg_warps, s);
+      default: return launch_rows_rc<8, WIDE>(pb, mt, tn.agg_warps, s);
+    }
+  }
   return tn.row_split ? launch_rows_s<WIDE, true>(pb, mt, tn, s)
                       : launch_rows_s<WIDE, false>(pb, mt, tn, s);
 }

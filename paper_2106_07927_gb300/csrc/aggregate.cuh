@@ -376,6 +376,100 @@ __device__ __forceinline__ void agg_rows(const Problem& pb, const Method& mt, in
   }
 }
 
+// The row walk of agg_rows (one direction per lane group) with the costs recomputed from the
+// census descriptor map instead of read from the cost volume: for the lane's disparities
+// d0 + j at pixel x, C = popcount(CT_L(x) ^ CT_R(x - d0 - j)), Eq. (image_matching), and 255 where
+// x < d0 + j. CT_L(x) and the one right descriptor that enters the lane's window of DPL right
+// descriptors at pixel x (CT_R(x - d0) going right, CT_R(x - d0 - DPL + 1) going left) are loaded
+// UR steps ahead; the window slides by one descriptor per step.
+template <int DPL, int LPL, bool WIDE, bool FULL>
+__device__ __forceinline__ void agg_rows_recompute(const Problem& pb, const Method& mt, int unit0,
+                                                   int unit_end) {
+  constexpr int NP = DPL / 2, UR = 8;
+  const int lane = threadIdx.x & 31;
+  const int lig = lane % LPL;
+  const int W = pb.W, H = pb.H, D = pb.D;
+  const int nu = min(row_units(H, true), unit_end);
+  const int ui = unit0 + lane / LPL;
+  if (LPL == 32 && ui >= nu) return;  // one unit per warp: uniform
+  const bool valid = ui < nu;
+  const int y = valid ? ui >> 1 : 0;
+  const bool active = FULL ? valid : (valid && lig * DPL < D);
+  const int d0 = active ? lig * DPL : 0;
+  const bool back = (ui & 1) != 0;
+  const int step = back ? -1 : 1;
+  const uint64_t* cl = pb.ct + (int64_t)y * W;
+  const uint64_t* cr = pb.ct + (int64_t)W * H + (int64_t)y * W;
+  const int enter = back ? d0 + DPL - 1 : d0;  // the entering right descriptor is CT_R(x - enter)
+  const uint32_t P1P1 = (uint32_t)mt.P1 * 0x10001u, P2P2 = (uint32_t)mt.P2 * 0x10001u;
+  const int64_t nde = (int64_t)W * H * D;  // extent of the volumes (range checks)
+  (void)nde;
+  constexpr int BPE = WIDE ? 4 : 2;
+  const int64_t estride = back ? -(int64_t)D : (int64_t)D;
+  int64_t e = ((int64_t)y * W + (back ? W - 1 : 0)) * D + d0;
+  uint64_t sl[UR], sr[UR];
+  int xf = back ? W - 1 : 0;  // pixel of the next load
+#pragma unroll
+  for (int u = 0; u < UR; u++) {
+    sl[u] = 0;
+    sr[u] = 0;
+    if (active && u < W) {
+      sl[u] = cl[xf];
+      const int xr = xf - enter;
+      if (xr >= 0) sr[u] = cr[xr];
+    }
+    if (u + 1 < W) xf += step;
+  }
+  // the window of the pixel before the first: going right every entry lies left of the image
+  // (cost 255 anyway); going left win[j] = CT_R(W - d0 - j), j >= 1
+  uint64_t win[DPL];
+#pragma unroll
+  for (int j = 0; j < DPL; j++) {
+    win[j] = 0;
+    const int xr = W - d0 - j;
+    if (back && active && j >= 1 && xr >= 0 && xr < W) win[j] = cr[xr];
+  }
+  uint32_t L[NP];
+#pragma unroll
+  for (int k = 0; k < NP; k++) L[k] = active ? 0u : kSent * 0x10001u;
+  uint32_t mm = 0;
+  for (int t0 = 0; t0 < W; t0 += UR) {
+#pragma unroll
+    for (int u = 0; u < UR; u++) {
+      const int t = t0 + u;
+      if (t >= W) break;
+      const int x = back ? W - 1 - t : t;
+      if (back) {
+#pragma unroll
+        for (int j = 0; j + 1 < DPL; j++) win[j] = win[j + 1];
+        win[DPL - 1] = sr[u];
+      } else {
+#pragma unroll
+        for (int j = DPL - 1; j > 0; j--) win[j] = win[j - 1];
+        win[0] = sr[u];
+      }
+      uint32_t cv[DPL];
+#pragma unroll
+      for (int j = 0; j < DPL; j++)
+        cv[j] = x < d0 + j ? (uint32_t)kCostOutside : (uint32_t)__popcll(sl[u] ^ win[j]);
+      uint32_t c[NP];
+#pragma unroll
+      for (int k = 0; k < NP; k++) c[k] = cv[2 * k] | (cv[2 * k + 1] << 16);
+      long_step<DPL, LPL, FULL>(L, mm, c, active, lig, P1P1, P2P2);
+      if (active && t + UR < W) {  // refill this slot with step t + UR (pixel xf)
+        sl[u] = cl[xf];
+        const int xr = xf - enter;
+        sr[u] = xr >= 0 ? cr[xr] : 0ull;
+      }
+      if (t + UR + 1 < W) xf += step;
+      if (active && R2T_CHECKED(pb, reinterpret_cast<uint8_t*>(pb.agg) + e * BPE, DPL * BPE,
+                                pb.agg, nde * BPE, 2))
+        add_lane<DPL, WIDE>(pb.agg, e, L);
+      e += estride;
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------- sheared columns
 // Kinds of sheared chain: 0 TB, 1 BT, 2 TLBR, 3 BRTL, 4 TRBL, 5 BLTR. Chain j of a kind with shear
 // s (0 for kinds 0-1, +1 for 2-3, -1 for 4-5) visits pixel x = (j + s y) mod W of every row y,

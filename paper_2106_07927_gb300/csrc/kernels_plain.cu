@@ -69,6 +69,7 @@ Tuning default_tuning(int D) {
   t.shear_cpl = shear_cpl_default(D);
   t.row_split = 1;  // one row direction per lane group (measured 2 % faster at D = 128)
   t.cost_mode = 0;  // population counts: measured faster than the tensor-core kernel
+  t.row_cost = 0;   // the row kernel reads the cost volume
   return t;
 }
 
@@ -83,7 +84,12 @@ bool tuning_valid(const Tuning& t, int D) {
   if (D % t.shear_dpl != 0) return false;
   if (t.row_split != 0 && t.row_split != 1) return false;
   if (t.cost_mode != 0 && t.cost_mode != 1) return false;
+  if (t.row_cost != 0 && t.row_cost != 1) return false;
   return true;
+}
+
+bool rows_recompute_ok(const Problem& pb, const Method& mt, const Tuning& tn) {
+  return tn.row_cost == 1 && tn.row_split == 1 && !(mt.flags & 8) && pb.D == 32 * tn.agg_dpl;
 }
 
 cudaError_t fork_create(Fork* f) {

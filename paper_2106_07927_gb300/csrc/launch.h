@@ -15,6 +15,7 @@ struct Tuning {
   int shear_cpl;  // chains per lane of the sheared-column kernel (1 or 2)
   int row_split;  // 1: one row direction per lane group, 0: both directions in one group
   int cost_mode;  // 0: population-count cost kernel, 1: tensor-core cost kernel (cost_mma_ok)
+  int row_cost;   // 0: the row kernel reads the cost volume, 1: recomputes (rows_recompute_ok)
 };
 
 // A second stream and two events that let the two aggregation kernels run concurrently: the
@@ -64,6 +65,10 @@ cudaError_t run_pipeline(const Problem& pb, const Method& mt, const Tuning& tn, 
 // aggregated sums; the descriptor map pb.ct must be filled. cost_mma_ok: the shapes it covers
 // (9 x 7 census, D = 64 or 128).
 bool cost_mma_ok(const Problem& pb, const Method& mt);
+// The row kernel recomputes its costs (tn.row_cost 1) when it runs one direction per warp with 32
+// lanes of tn.agg_dpl disparities (D = 32 agg_dpl, one row direction per lane group) on the
+// census cost; otherwise it reads the cost volume.
+bool rows_recompute_ok(const Problem& pb, const Method& mt, const Tuning& tn);
 cudaError_t launch_cost_mma(const Problem& pb, const Method& mt, cudaStream_t s);
 
 // NCC matching cost (mt.flags & 8, patch mt.cw x mt.cw, pb.nst set): patch statistics

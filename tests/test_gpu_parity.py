@@ -147,6 +147,27 @@ def test_tensor_core_cost_is_bit_exact(W, H, D, cw, ch, p2, flags, pads):
     _assert_same(left, right, prm, tuning=t, in_pad=pads[0], out_pad=pads[1])
 
 
+# The row kernel recomputing its costs from the census descriptors (tuning row_cost 2): every
+# D it covers (agg_dpl 2, 4, 8 with 32 lanes), images narrower than its 8-step prefetch, both
+# census windows, wide sums, the exact check (its flipped pass recomputes from the flipped
+# pair's descriptors) and padded pitches; other settings and the NCC cost read the volume.
+@pytest.mark.parametrize("W,H,D,dpl,cw,ch,p2,flags", [
+    (300, 40, 128, 4, 9, 7, 120, 3),
+    (257, 21, 64, 2, 9, 7, 120, 3),
+    (97, 13, 256, 8, 9, 7, 120, 3),
+    (5, 9, 64, 2, 9, 7, 120, 3),
+    (1, 3, 128, 4, 9, 7, 120, 0),
+    (200, 30, 128, 4, 5, 5, 120, 3 | 4),
+    (150, 40, 128, 4, 5, 5, 16384, 3),
+    (130, 20, 128, 8, 9, 7, 120, 3),
+])
+def test_row_recompute_is_bit_exact(W, H, D, dpl, cw, ch, p2, flags):
+    left, right, _ = scenes.make_scene("road", W + 3 * H, W, H, D)
+    prm = scenes.params(W, H, D, cw, ch, 10, p2, 8, flags)
+    t = binding.res2tac_tuning(agg_dpl=dpl, row_mode=2, row_cost=2)
+    _assert_same(left, right, prm, tuning=t, in_pad=3, out_pad=1)
+
+
 def test_tensor_core_cost_setting_and_autotune():
     import torch
     left, right, _ = scenes.make_scene("road", 5, 160, 48, 64)
