@@ -174,13 +174,16 @@ def test_tensor_core_cost_setting_and_autotune():
     prm = scenes.params(160, 48, 64, 9, 7, 10, 120, 8, 3)
     st = binding.Stereo(prm)
     assert binding.res2tac_get_tuning(st.handle).cost_mode == 1  # population counts by default
+    assert binding.res2tac_get_tuning(st.handle).row_cost == 1  # the row kernel reads the volume
     with pytest.raises(binding.Res2tacError):
         binding.res2tac_set_tuning(st.handle, binding.res2tac_tuning(cost_mode=3))
+    with pytest.raises(binding.Res2tacError):
+        binding.res2tac_set_tuning(st.handle, binding.res2tac_tuning(row_cost=3))
     L, R = torch.from_numpy(left).cuda(), torch.from_numpy(right).cuda()
     o = torch.empty((48, 160), dtype=torch.int16, device="cuda")
     best = binding.res2tac_autotune(st.handle, L.data_ptr(), R.data_ptr(), 160, o.data_ptr(),
                                     320, torch.cuda.current_stream().cuda_stream)
-    assert best.cost_mode in (1, 2)
+    assert best.cost_mode in (1, 2) and best.row_cost in (1, 2)
     out = st.compute(L, R)
     assert np.array_equal(binding.u16(out), oracle.sgm(left, right, 64, 9, 7, 10, 120, 8, 3))
     st.close()
